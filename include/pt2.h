@@ -1,0 +1,162 @@
+/*
+ * libpt2 -- deterministic, sort-based Epstein-Nesbet PT2 on one GB300 (sm_103a).
+ *
+ * The library computes the second-order Epstein-Nesbet correction of a
+ * selected-CI reference wavefunction psi = sum_i c_i |D_i> (Eq. 3 of Tubman
+ * et al., arXiv:1808.02049, "Overview of ASCI"):
+ *
+ *     E2 = sum_{a not in psi} ( sum_i <D_a|H|D_i> c_i )^2 / (E0 - H_aa)
+ *
+ * where a runs over every determinant one single or double excitation away
+ * from some reference determinant (Algorithm 1; the sum is split into
+ * non-overlapping, complete constraint classes as in Algorithm 2).
+ *
+ * Conventions used by every entry point:
+ *  - orbitals are numbered 0..n_orb-1, n_orb <= 64;
+ *  - a determinant is a 128-bit key held as two 64-bit words, the alpha word
+ *    (bit p set = alpha spin-orbital p occupied) and the beta word; the alpha
+ *    word is the more significant half ("Triplet constraints" section);
+ *  - key arrays interleave the words: keys[2 i] = alpha, keys[2 i + 1] = beta;
+ *  - the determinant's sign convention is alpha creators in ascending order,
+ *    then beta creators in ascending order, acting on the vacuum;
+ *  - integrals are real, chemist notation: h[p*n + q] = h_pq (symmetric) and
+ *    eri[((p*n + q)*n + r)*n + s] = (pq|rs) with 8-fold symmetry.
+ *
+ * Memory and ownership: every pointer argument is a HOST pointer.  Input arrays
+ * are copied into device memory the library owns during the call and are
+ * never retained; output arrays are written before the call returns.  The
+ * context owns all device memory and one CUDA stream; nothing is allocated by
+ * the caller on the device.
+ *
+ * Errors: every int-returning call returns PT2_OK (0) or a negative
+ * pt2_status; pt2_last_error() then holds a message.  No call aborts or
+ * exits.  A context is not thread-safe: one host thread at a time.
+ */
+#ifndef PT2_H
+#define PT2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt2_ctx pt2_ctx;
+
+typedef enum {
+    PT2_OK = 0,
+    PT2_ERR_INVALID = -1,     /* bad argument or inconsistent input data */
+    PT2_ERR_OOM = -2,         /* device memory budget or capacity exceeded */
+    PT2_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    PT2_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+    PT2_ERR_BUSY = -5,        /* a submitted request has not finished */
+    PT2_ERR_NOT_FOUND = -6,   /* unknown system, reference or ticket id */
+    PT2_ERR_UNSUPPORTED = -7  /* e.g. n_orb > 64 */
+} pt2_status;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the context may hold (0 = 80% of the free memory at creation).
+ * On success *out receives the context. */
+int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes);
+
+/* Release every device resource of the context.  NULL is ignored. */
+void pt2_destroy(pt2_ctx *ctx);
+
+/* Message of the last failed call on this context (or of the last failed
+ * pt2_create when ctx is NULL).  Valid until the next call on the context. */
+const char *pt2_last_error(const pt2_ctx *ctx);
+
+/* Load the integrals of one system (the Hamiltonian of Eq. 3).
+ * h: n_orb*n_orb doubles, symmetric to 1e-12; eri: n_orb^4 doubles with
+ * (pq|rs) = (qp|rs) = (pq|sr) = (rs|pq) to 1e-12.  All values finite.
+ * Errors: PT2_ERR_UNSUPPORTED for n_orb > 64, PT2_ERR_INVALID otherwise. */
+int pt2_load_system(pt2_ctx *ctx, int n_orb, const double *h, const double *eri,
+                    uint32_t *system_id);
+
+/* Load a reference wavefunction {D_i, c_i} and its variational energy E0
+ * (E_ASCI of Eq. 3) for a loaded system.  keys: 2*n_det words as described
+ * above; coef: n_det finite doubles.  Every determinant must have the same
+ * alpha and the same beta electron count, no bit at or above n_orb, and no
+ * determinant may repeat (PT2_ERR_INVALID otherwise).  The reference is kept
+ * resident on the device until pt2_unload. */
+int pt2_load_reference(pt2_ctx *ctx, uint32_t system_id, uint64_t n_det, const uint64_t *keys,
+                       const double *coef, double e0, uint32_t *ref_id);
+
+/* Free a loaded system or reference (a system may only be unloaded once no
+ * reference uses it). */
+int pt2_unload(pt2_ctx *ctx, uint32_t id);
+
+/* Direct diagonal H_kk (Slater-Condon, the denominator term of Eq. 3) of n
+ * determinants of a loaded system, computed on the device.  keys: 2*n words;
+ * out: n doubles.  Used e.g. to set E0 = min_i H_ii - shift. */
+int pt2_diagonal(pt2_ctx *ctx, uint32_t system_id, uint64_t n, const uint64_t *keys, double *out);
+
+/* Run options.  Zero-initialise and set what you need. */
+typedef struct {
+    uint64_t constraint_mod;  /* 0 or 1: no constraint.  Otherwise only excited
+                                 determinants with alpha % constraint_mod ==
+                                 constraint_rem are summed: one class of a
+                                 non-overlapping, complete partition
+                                 (Algorithm 2). */
+    uint64_t constraint_rem;
+    uint64_t pass_budget_bytes; /* device bytes for one pass of generated
+                                   terms (0 = derived from the context budget);
+                                   smaller values mean more passes */
+    uint32_t tile_target;       /* mean terms per hash tile (0 = default 1024) */
+    uint32_t flags;             /* PT2_FLAG_* below */
+} pt2_opts;
+
+#define PT2_FLAG_PROFILE 1u  /* record per-phase device times (pt2_phase_times) */
+
+typedef struct {
+    double e2;                /* the PT2 energy, Hartree */
+    uint64_t n_terms;         /* generated (key, H_ai c_i) pairs */
+    uint64_t n_unique;        /* distinct generated determinants */
+    uint64_t n_in_ref;        /* distinct generated determinants that are in psi */
+    uint64_t n_external;      /* |connected external set| */
+    uint64_t digest_sum;      /* sum over the external set of mix1(key) mod 2^64 */
+    uint64_t digest_xor;      /* xor over the external set of mix2(key) */
+    double min_abs_denom;     /* min |E0 - H_aa| over the external set */
+    uint64_t n_pos_denom;     /* external determinants with E0 - H_aa > 0 */
+    uint32_t n_passes;        /* memory-bounded passes used */
+    uint32_t n_tiles;         /* hash tiles over all passes */
+    uint32_t n_oversize;      /* tiles handled by the chunked path */
+    uint32_t reserved;
+    double seconds;           /* device time of the run (CUDA events) */
+} pt2_result;
+
+/* Compute E2 for a loaded reference (blocking).  opts may be NULL.  The
+ * result is bit-identical across runs for the same inputs and options. */
+int pt2_run(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, pt2_result *out);
+
+/* Like pt2_run, and also write the connected external set: for each of its
+ * determinants the key (2 words), the summed numerator sum_i H_ai c_i and the
+ * diagonal H_aa.  Order is unspecified.  At most cap entries are written;
+ * *n_out receives |S| (PT2_ERR_OOM if it exceeds cap).  Parity aid. */
+int pt2_dump_external(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, uint64_t *keys,
+                      double *num, double *haa, uint64_t cap, uint64_t *n_out);
+
+/* Generate the terms of one reference determinant (index in the caller's
+ * original order): every single and double excitation D_a with its numerator
+ * <D_a|H|D_i> c_i and diagonal H_aa, as the generation kernel emits them
+ * (Algorithm 1, first step).  Order is unspecified; *n_out receives the count
+ * (PT2_ERR_OOM if it exceeds cap).  Parity aid. */
+int pt2_det_terms(pt2_ctx *ctx, uint32_t ref_id, uint64_t det_index, uint64_t *keys,
+                  double *val, double *haa, uint64_t cap, uint64_t *n_out);
+
+/* Per-phase device milliseconds of the last run made with PT2_FLAG_PROFILE:
+ * out[0] class count, [1] tile count, [2] scan, [3] generate/emit,
+ * [4] reference partition, [5] tile sort-reduce, [6] oversize tiles,
+ * [7] pass reduction.  n = number of slots in out (at most 8 written).
+ * launches (may be NULL) receives the number of kernel launches. */
+int pt2_phase_times(pt2_ctx *ctx, double *out, int n, uint64_t *launches);
+
+/* The context's CUDA stream (a cudaStream_t), for callers that want to
+ * order or time their own work against the library's. */
+void *pt2_stream(pt2_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT2_H */

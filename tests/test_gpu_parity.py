@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerance: |dE2| <= 1e-10 Ha absolute or 1e-10 relative; the connected
+external set (count and order-independent digest, and the full key list where
+the oracle can enumerate it) must match bit-exactly; per-key numerators agree
+to 1e-13 absolute (they are sums of FP64 products, summed in a different
+order) and diagonals to 1e-11 absolute (incremental on the GPU, direct in the
+oracle).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import brute
+import oracle
+from paper_1808_02049_gb300 import inputs, pt2
+
+pytestmark = pytest.mark.gpu
+
+E2_TOL = 1e-10
+
+
+def e2_close(a, b):
+    return abs(a - b) <= max(E2_TOL, E2_TOL * abs(b))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1808_02049_gb300 import build
+
+    build.build_library()
+    c = pt2.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def cfg0(ctx):
+    s, r = inputs.make_config(0)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    sid = ctx.load_system(s.h, s.eri)
+    rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
+    return dict(s=s, r=r, e0=e0, sid=sid, rid=rid, ref=ref)
+
+
+def assert_same_result(got, ref):
+    assert got["n_terms"] == ref["n_terms"]
+    assert got["n_external"] == ref["n_external"]
+    assert got["n_in_ref"] == ref["n_in_ref"]
+    assert got["n_unique"] == ref["n_unique"]
+    assert (got["digest_sum"], got["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
+    assert got["n_pos_denom"] == ref["n_pos_denom"]
+    if ref["n_external"]:
+        assert abs(got["min_abs_denom"] - ref["min_abs_denom"]) < 1e-10
+    assert e2_close(got["e2"], ref["e2"]), (got["e2"], ref["e2"])
+
+
+def sort_keys(k, *vals):
+    order = np.lexsort((k[:, 1], k[:, 0]))
+    return (k[order],) + tuple(v[order] for v in vals)
+
+
+def test_diagonal_matches_oracle(ctx, cfg0):
+    s, r = cfg0["s"], cfg0["r"]
+    got = ctx.diagonal(cfg0["sid"], r.keys)
+    np.testing.assert_allclose(got, oracle.diagonals(s.h, s.eri, r.keys), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("det", [0, 1, 123, 999])
+def test_det_terms_match_oracle(ctx, cfg0, det):
+    s, r = cfg0["s"], cfg0["r"]
+    k, v, d = ctx.det_terms(cfg0["rid"], det, 4000)
+    ok, ov, od = oracle.det_terms(s.h, s.eri, r.keys[2 * det], r.keys[2 * det + 1], r.coef[det])
+    assert k.shape == ok.shape == (3192, 2)
+    k, v, d = sort_keys(k, v, d)
+    ok, ov, od = sort_keys(ok, ov, od)
+    assert np.array_equal(k, ok)
+    np.testing.assert_allclose(v, ov, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(d, od, rtol=0, atol=1e-11)
+
+
+def test_e2_config0_matches_oracle(ctx, cfg0):
+    got = ctx.run(cfg0["rid"])
+    assert_same_result(got, cfg0["ref"])
+
+
+def test_external_set_dump_matches_oracle(ctx, cfg0):
+    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
+    k, num, haa = ctx.dump_external(cfg0["rid"], cfg0["ref"]["n_external"] + 10)
+    ok, onum, ohaa, _ = oracle.dump_external(s.h, s.eri, r.keys, r.coef, e0)
+    k, num, haa = sort_keys(k, num, haa)
+    assert np.array_equal(k, ok)
+    np.testing.assert_allclose(num, onum, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(haa, ohaa, rtol=0, atol=1e-11)
+
+
+def test_run_is_bit_identical_across_runs(ctx, cfg0):
+    a = ctx.run(cfg0["rid"])
+    b = ctx.run(cfg0["rid"])
+    assert a["e2"] == b["e2"]
+    assert a == {**b, "seconds": a["seconds"]}
+
+
+@pytest.mark.parametrize("tile_target", [16, 256, 2048])
+def test_tile_sizes_and_oversize_path(ctx, cfg0, tile_target):
+    got = ctx.run(cfg0["rid"], tile_target=tile_target)
+    assert_same_result(got, cfg0["ref"])
+    if tile_target == 2048:
+        assert got["n_oversize"] > 0  # tiles above shared-memory capacity took the chunked path
+
+
+def test_many_passes(ctx, cfg0):
+    # a 12 MB pass budget forces several memory-bounded passes
+    got = ctx.run(cfg0["rid"], pass_budget_bytes=12 << 20)
+    assert got["n_passes"] >= 5
+    assert_same_result(got, cfg0["ref"])
+
+
+def test_constraint_classes(ctx, cfg0):
+    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
+    m = 5
+    tot = 0.0
+    for k in range(m):
+        got = ctx.run(cfg0["rid"], constraint=(m, k))
+        ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=(m, k))
+        assert_same_result(got, ref)
+        tot += got["e2"]
+    assert e2_close(tot, cfg0["ref"]["e2"])
+
+
+def test_permutation_invariance_is_bit_exact(ctx, cfg0):
+    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
+    perm = np.random.default_rng(11).permutation(r.n_det)
+    pk = np.empty_like(r.keys)
+    pk[0::2], pk[1::2] = r.keys[0::2][perm], r.keys[1::2][perm]
+    rid = ctx.load_reference(cfg0["sid"], pk, r.coef[perm], e0)
+    try:
+        a = ctx.run(cfg0["rid"])
+        b = ctx.run(rid)
+    finally:
+        ctx.unload(rid)
+    assert a["e2"] == b["e2"]
+    assert (a["digest_sum"], a["digest_xor"]) == (b["digest_sum"], b["digest_xor"])
+
+
+def test_scaling_and_spin_swap(ctx, cfg0):
+    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
+    base = ctx.run(cfg0["rid"])["e2"]
+    rid = ctx.load_reference(cfg0["sid"], r.keys, 2.0 * r.coef, e0)
+    try:
+        dbl = ctx.run(rid)["e2"]
+    finally:
+        ctx.unload(rid)
+    assert abs(dbl - 4.0 * base) <= 1e-14 * abs(base)
+    sw = r.keys.copy()
+    sw[0::2], sw[1::2] = r.keys[1::2], r.keys[0::2]
+    rid = ctx.load_reference(cfg0["sid"], sw, r.coef, e0)
+    try:
+        swp = ctx.run(rid)["e2"]
+    finally:
+        ctx.unload(rid)
+    assert abs(swp - base) <= 1e-12 * abs(base)
+
+
+def _keys_of(dets):
+    k = np.empty(2 * len(dets), dtype=np.uint64)
+    k[0::2] = [d[0] for d in dets]
+    k[1::2] = [d[1] for d in dets]
+    return k
+
+
+@pytest.mark.parametrize("n_orb,na,nb,n_ref,seed", [(4, 2, 2, 3, 1), (5, 2, 1, 4, 3), (6, 3, 3, 5, 5),
+                                                    (6, 3, 2, 1, 6)])
+def test_tiny_systems_match_brute_force(ctx, n_orb, na, nb, n_ref, seed):
+    from test_oracle_pins import strong_integrals
+
+    h, eri = strong_integrals(n_orb, seed)
+    dets = brute.basis(n_orb, na, nb)
+    H = brute.hamiltonian(h, eri, dets)
+    rng = np.random.default_rng(100 + seed)
+    idx = sorted(rng.choice(len(dets), size=n_ref, replace=False).tolist())
+    coef = rng.normal(0, 1, n_ref)
+    e0 = float(min(H[i, i] for i in idx) - 0.37)
+    bf = brute.pt2(h, eri, dets, H, idx, coef, e0)
+    sid = ctx.load_system(h, eri)
+    rid = ctx.load_reference(sid, _keys_of([dets[i] for i in idx]), coef, e0)
+    try:
+        got = ctx.run(rid)
+        k, num, haa = ctx.dump_external(rid, len(dets))
+    finally:
+        ctx.unload(rid)
+        ctx.unload(sid)
+    k, num, haa = sort_keys(k, num, haa)
+    assert np.array_equal(k, bf["keys"])
+    np.testing.assert_allclose(num, bf["num"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(haa, bf["haa"], rtol=0, atol=1e-12)
+    assert abs(got["e2"] - bf["e2"]) <= 1e-12 * max(1.0, abs(bf["e2"]))
+
+
+def test_edge_cases(ctx):
+    # no excitations at all: one orbital, one alpha electron, no beta electron
+    h = np.array([[-1.0]])
+    eri = np.array([[[[0.5]]]])
+    sid = ctx.load_system(h, eri)
+    rid = ctx.load_reference(sid, np.array([1, 0], dtype=np.uint64), np.array([1.0]), -2.0)
+    got = ctx.run(rid)
+    ctx.unload(rid)
+    ctx.unload(sid)
+    assert got["n_terms"] == 0 and got["n_external"] == 0 and got["e2"] == 0.0
+    # a filled alpha shell (no alpha virtuals), single-determinant reference
+    s = inputs.make_integrals(6, 5)
+    keys = np.array([0b111111, 0b000011], dtype=np.uint64)
+    e0 = float(oracle.diagonals(s.h, s.eri, keys)[0] - 0.2)
+    ref = oracle.pt2(s.h, s.eri, keys, np.array([1.0]), e0)
+    sid = ctx.load_system(s.h, s.eri)
+    rid = ctx.load_reference(sid, keys, np.array([1.0]), e0)
+    got = ctx.run(rid)
+    ctx.unload(rid)
+    ctx.unload(sid)
+    assert_same_result(got, ref)
+
+
+def test_64_orbitals_top_bit(ctx):
+    # n_orb = 64 exercises bit 63 of both words
+    s = inputs.make_integrals(64, 77)
+    r = inputs.make_reference(64, 2, 6, 2, 78)
+    # move one electron of each spin to orbital 63 in one determinant
+    keys = r.keys.copy()
+    keys[2] = np.uint64((1 << 63) | 1)
+    keys[3] = np.uint64((1 << 63) | 2)
+    e0 = oracle.e0_of(s.h, s.eri, keys)
+    ref = oracle.pt2(s.h, s.eri, keys, r.coef, e0)
+    sid = ctx.load_system(s.h, s.eri)
+    rid = ctx.load_reference(sid, keys, r.coef, e0)
+    got = ctx.run(rid)
+    ctx.unload(rid)
+    ctx.unload(sid)
+    assert_same_result(got, ref)
+
+
+def test_invalid_inputs_are_rejected(ctx, cfg0):
+    s, r = cfg0["s"], cfg0["r"]
+    bad = r.keys.copy()
+    bad[2], bad[3] = bad[0], bad[1]
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.load_reference(cfg0["sid"], bad, r.coef, -1.0)
+    assert e.value.code == pt2.PT2_ERR_INVALID
+    bad = r.keys.copy()
+    bad[0] = np.uint64(bad[0]) | np.uint64(1 << 40)
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.load_reference(cfg0["sid"], bad, r.coef, -1.0)
+    assert e.value.code == pt2.PT2_ERR_INVALID
+    coef = r.coef.copy()
+    coef[3] = np.nan
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.load_reference(cfg0["sid"], r.keys, coef, -1.0)
+    assert e.value.code == pt2.PT2_ERR_INVALID
+    hb = s.h.copy()
+    hb[0, 1] += 1e-6
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.load_system(hb, s.eri)
+    assert e.value.code == pt2.PT2_ERR_INVALID
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.load_system(np.eye(65), np.zeros((65,) * 4))
+    assert e.value.code == pt2.PT2_ERR_UNSUPPORTED
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.run(987654)
+    assert e.value.code == pt2.PT2_ERR_NOT_FOUND
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.run(cfg0["rid"], constraint=(3, 5))
+    assert e.value.code == pt2.PT2_ERR_INVALID
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.unload(cfg0["sid"])  # still used by a reference
+    assert e.value.code == pt2.PT2_ERR_INVALID
+
+
+def T(n, v):
+    return 2 * n * v + 2 * math.comb(n, 2) * math.comb(v, 2) + (n * v) ** 2
