@@ -172,6 +172,7 @@ def run_gpu(args):
     sid = ctx.load_system(s.h, s.eri)
     e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
     rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    print(f"[bench] device memory: {ctx.memory_info()}", file=sys.stderr)
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
 

@@ -151,6 +151,12 @@ int pt2_det_terms(pt2_ctx *ctx, uint32_t ref_id, uint64_t det_index, uint64_t *k
  * launches (may be NULL) receives the number of kernel launches. */
 int pt2_phase_times(pt2_ctx *ctx, double *out, int n, uint64_t *launches);
 
+/* Device memory accounting of the context: *budget is the byte budget fixed
+ * at creation, *used what the context holds now (systems, references and the
+ * grow-only run workspace), *device_free what the device reports free.  Any
+ * pointer may be NULL. */
+int pt2_memory_info(pt2_ctx *ctx, uint64_t *budget, uint64_t *used, uint64_t *device_free);
+
 /* The context's CUDA stream (a cudaStream_t), for callers that want to
  * order or time their own work against the library's. */
 void *pt2_stream(pt2_ctx *ctx);

@@ -284,14 +284,22 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     uint64_t scratch_cap = 1ull << 20;
     const int big_ctas = 16;
     if (!pass_budget) {
+        // the pass workspace a previous run left allocated is reused, so it counts as available
+        const DevBuf *ws[] = {&c->tile_counts, &c->tile_off, &c->cursor, &c->scan_tmp, &c->parts, &c->ref_count,
+                              &c->ref_off, &c->ref_cursor, &c->big_list, &c->scratch, &c->recs};
+        uint64_t held = 0;
+        for (const DevBuf *b : ws) held += b->bytes;
+        const uint64_t fixed = c->used - held;
         uint64_t reserve = (uint64_t)big_ctas * 2 * scratch_cap * sizeof(Rec48) + (64ull << 20);
-        uint64_t avail = c->budget > c->used + reserve ? c->budget - c->used - reserve : 0;
+        uint64_t avail = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
         // tile arrays for the pass cost about 100 bytes per tile
         pass_budget = avail;
     }
     const double per_rec = sizeof(Rec32) + 100.0 / (double)tile_target;
     uint64_t max_rec = (uint64_t)((double)pass_budget / per_rec);
-    if (max_rec < 1024) return fail(c, PT2_ERR_OOM, "pass budget of %llu bytes is too small", (unsigned long long)pass_budget);
+    if (max_rec < 1024)
+        return fail(c, PT2_ERR_OOM, "pass budget of %llu bytes is too small (context budget %llu, in use %llu)",
+                    (unsigned long long)pass_budget, (unsigned long long)c->budget, (unsigned long long)c->used);
     std::vector<Pass> passes;
     {
         Pass cur{0, 0, 0, 0};
@@ -493,7 +501,8 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
     auto c = std::make_unique<pt2_ctx>();
     c->device = device;
     size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e));
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(0.8 * (double)fr);
     e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
@@ -776,6 +785,20 @@ int pt2_phase_times(pt2_ctx *c, double *out, int n, uint64_t *launches)
     if (!c || (!out && n > 0)) return PT2_ERR_INVALID;
     for (int i = 0; i < n && i < kPhases; ++i) out[i] = c->phase_ms[i];
     if (launches) *launches = c->launches;
+    return PT2_OK;
+}
+
+int pt2_memory_info(pt2_ctx *c, uint64_t *budget, uint64_t *used, uint64_t *device_free)
+{
+    if (!c) return PT2_ERR_INVALID;
+    if (budget) *budget = c->budget;
+    if (used) *used = c->used;
+    if (device_free) {
+        cudaSetDevice(c->device);
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+        *device_free = fr;
+    }
     return PT2_OK;
 }
 

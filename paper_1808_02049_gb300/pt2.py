@@ -28,7 +28,7 @@ PT2_FLAG_PROFILE = 1
 
 EXPORTS = ["pt2_create", "pt2_destroy", "pt2_last_error", "pt2_load_system", "pt2_load_reference",
            "pt2_unload", "pt2_diagonal", "pt2_run", "pt2_dump_external", "pt2_det_terms",
-           "pt2_phase_times", "pt2_stream"]
+           "pt2_phase_times", "pt2_memory_info", "pt2_stream"]
 
 PHASES = ["class_count", "tile_count", "scan", "emit", "ref_partition", "tile_sort_reduce",
           "oversize_tiles", "pass_reduce"]
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "pt2_dump_external": (i32, [P, u32, ctypes.POINTER(pt2_opts), P, P, P, u64, pu64]),
         "pt2_det_terms": (i32, [P, u32, u64, P, P, P, u64, pu64]),
         "pt2_phase_times": (i32, [P, P, i32, pu64]),
+        "pt2_memory_info": (i32, [P, pu64, pu64, pu64]),
         "pt2_stream": (P, [P]),
     }
     for name, (res, args) in sig.items():
@@ -199,6 +200,12 @@ def pt2_phase_times(ctx):
     return dict(zip(PHASES, out.tolist())), launches.value
 
 
+def pt2_memory_info(ctx) -> dict:
+    b, u, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, load_library().pt2_memory_info(ctx, ctypes.byref(b), ctypes.byref(u), ctypes.byref(f)))
+    return {"budget": b.value, "used": u.value, "device_free": f.value}
+
+
 def pt2_stream(ctx) -> int:
     return load_library().pt2_stream(ctx) or 0
 
@@ -249,6 +256,9 @@ class Context:
 
     def phase_times(self):
         return pt2_phase_times(self.handle)
+
+    def memory_info(self):
+        return pt2_memory_info(self.handle)
 
     @property
     def stream(self):
