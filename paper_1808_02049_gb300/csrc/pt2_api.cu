@@ -27,7 +27,7 @@ struct DevBuf {
 
 struct SystemRes {
     int n = 0;
-    DevBuf h, eri, J, WS;
+    DevBuf h, eri, J, WS, Jx, WSx, hdx;
     int refs = 0;  // references using this system
 };
 
@@ -36,7 +36,7 @@ struct RefRes {
     uint64_t n_det = 0;
     int na = 0, nb = 0;
     double e0 = 0.0;
-    DevBuf keys, coef, hii;
+    DevBuf keys, coef, hii, d0;
 };
 
 constexpr int kPhases = 8;
@@ -45,6 +45,7 @@ constexpr int kPhases = 8;
 
 struct pt2_ctx {
     int device = 0;
+    int sm_count = 0;
     cudaStream_t stream = nullptr;
     uint64_t budget = 0, used = 0;
     std::string err;
@@ -53,9 +54,8 @@ struct pt2_ctx {
     std::map<uint32_t, std::unique_ptr<RefRes>> refs;
     DevBuf hash;
     // run workspace (grow-only)
-    DevBuf class_counts, tile_counts, tile_off, cursor, scan_tmp, recs, parts, chunk_tmp, ref_tile, ref_count,
-        ref_off, ref_cursor, ref_keys, big_list, big_count, scratch, acc, err_word, dump_keys, dump_num, dump_haa,
-        dump_count;
+    DevBuf class_counts, tile_counts, tile_off, cursor, scan_tmp, recs, ref_tile, ref_count, ref_off, ref_cursor,
+        ref_keys, big_list, scratch, acc, err_word, dump_keys, dump_num, dump_haa, dump_count;
     cudaEvent_t ev[2 * kPhases + 2] = {};
     double phase_ms[kPhases] = {};
     uint64_t launches = 0;
@@ -122,6 +122,18 @@ int ensure(pt2_ctx *c, DevBuf &b, size_t bytes, const char *what)
     return dev_alloc(c, b, bytes, what);
 }
 
+void free_system(pt2_ctx *c, SystemRes &s)
+{
+    DevBuf *b[] = {&s.h, &s.eri, &s.J, &s.WS, &s.Jx, &s.WSx, &s.hdx};
+    for (DevBuf *x : b) dev_free(c, *x);
+}
+
+void free_ref(pt2_ctx *c, RefRes &r)
+{
+    DevBuf *b[] = {&r.keys, &r.coef, &r.hii, &r.d0};
+    for (DevBuf *x : b) dev_free(c, *x);
+}
+
 uint64_t splitmix64(uint64_t &s)
 {
     uint64_t z = (s += 0x9e3779b97f4a7c15ull);
@@ -154,6 +166,9 @@ SysDev sys_dev(const SystemRes &s)
     d.eri = (const double *)s.eri.ptr;
     d.J = (const double *)s.J.ptr;
     d.WS = (const double *)s.WS.ptr;
+    d.Jx = (const int64_t *)s.Jx.ptr;
+    d.WSx = (const int64_t *)s.WSx.ptr;
+    d.hdx = (const int64_t *)s.hdx.ptr;
     return d;
 }
 
@@ -165,7 +180,8 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.hash = (const HashTables *)c->hash.ptr;
     p.keys = (const uint64_t *)r.keys.ptr;
     p.coef = (const double *)r.coef.ptr;
-    p.hii = (const double *)r.hii.ptr;
+    p.d0 = (const int64_t *)r.d0.ptr;
+    p.e0 = r.e0;
     p.n_det = r.n_det;
     p.na = r.na;
     p.nb = r.nb;
@@ -243,8 +259,6 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     // fixed workspace
     if ((rc = ensure(c, c->class_counts, kNumClasses * 8, "class counts"))) return rc;
     if ((rc = ensure(c, c->acc, sizeof(RunAcc), "accumulator"))) return rc;
-    if ((rc = ensure(c, c->chunk_tmp, 256 * 64, "reduction chunks"))) return rc;
-    if ((rc = ensure(c, c->big_count, 16, "oversize count"))) return rc;
     if ((rc = ensure(c, c->ref_tile, r.n_det * 4, "reference tiles"))) return rc;
     if ((rc = ensure(c, c->ref_keys, r.n_det * 16, "reference slices"))) return rc;
     if (dump) {
@@ -254,10 +268,12 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
         if ((rc = ensure(c, c->dump_haa, std::max<uint64_t>(dump->cap, 1) * 8, "dump haa"))) return rc;
         CK(cudaMemsetAsync(c->dump_count.ptr, 0, 8, st), "memset");
     }
+    RunAcc *acc = (RunAcc *)c->acc.ptr;
+    uint32_t *errw = (uint32_t *)c->err_word.ptr;
 
     CK(cudaEventRecord(c->ev[0], st), "event");
-    CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, st), "memset");
-    CK(launch_acc_init((RunAcc *)c->acc.ptr, st), "acc init");
+    CK(cudaMemsetAsync(errw, 0, 4, st), "memset");
+    CK(launch_acc_init(acc, st), "acc init");
     c->launches++;
 
     // ---- work list: terms per alpha-hash class
@@ -281,21 +297,18 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     uint64_t total = 0;
     for (auto x : cls) total += x;
     uint64_t pass_budget = o.pass_budget_bytes;
-    uint64_t scratch_cap = 1ull << 20;
-    const int big_ctas = 16;
     if (!pass_budget) {
         // the pass workspace a previous run left allocated is reused, so it counts as available
-        const DevBuf *ws[] = {&c->tile_counts, &c->tile_off, &c->cursor, &c->scan_tmp, &c->parts, &c->ref_count,
-                              &c->ref_off, &c->ref_cursor, &c->big_list, &c->scratch, &c->recs};
+        const DevBuf *ws[] = {&c->tile_counts, &c->tile_off, &c->cursor,   &c->scan_tmp, &c->ref_count,
+                              &c->ref_off,     &c->ref_cursor, &c->big_list, &c->scratch,  &c->recs};
         uint64_t held = 0;
         for (const DevBuf *b : ws) held += b->bytes;
         const uint64_t fixed = c->used - held;
-        uint64_t reserve = (uint64_t)big_ctas * 2 * scratch_cap * sizeof(Rec48) + (64ull << 20);
-        uint64_t avail = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
-        // tile arrays for the pass cost about 100 bytes per tile
-        pass_budget = avail;
+        const uint64_t reserve = (2ull << 30) + (64ull << 20);  // oversize scratch and slack
+        pass_budget = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
     }
-    const double per_rec = sizeof(Rec32) + 100.0 / (double)tile_target;
+    // per record: 32 bytes plus about 60 bytes of tile bookkeeping per tile
+    const double per_rec = sizeof(Rec32) + 60.0 / (double)tile_target;
     uint64_t max_rec = (uint64_t)((double)pass_budget / per_rec);
     if (max_rec < 1024)
         return fail(c, PT2_ERR_OOM, "pass budget of %llu bytes is too small (context budget %llu, in use %llu)",
@@ -325,21 +338,19 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
         max_records = std::max(max_records, p.records);
     }
     if (max_tiles >= 0xFFFFFFFFull) return fail(c, PT2_ERR_INVALID, "too many tiles in one pass");
-    scratch_cap = std::min<uint64_t>(scratch_cap, max_records);
     if ((rc = ensure(c, c->tile_counts, max_tiles * 4, "tile counts"))) return rc;
     if ((rc = ensure(c, c->tile_off, (max_tiles + 1) * 8, "tile offsets"))) return rc;
     if ((rc = ensure(c, c->cursor, max_tiles * 8, "tile cursors"))) return rc;
     if ((rc = ensure(c, c->scan_tmp, scan_tmp_elems(max_tiles) * 8 * 2, "scan scratch"))) return rc;
-    if ((rc = ensure(c, c->parts, max_tiles * sizeof(TilePart), "tile partials"))) return rc;
     if ((rc = ensure(c, c->ref_count, max_tiles * 4, "reference counts"))) return rc;
     if ((rc = ensure(c, c->ref_off, (max_tiles + 1) * 8, "reference offsets"))) return rc;
     if ((rc = ensure(c, c->ref_cursor, max_tiles * 8, "reference cursors"))) return rc;
     if ((rc = ensure(c, c->big_list, max_tiles * 4, "oversize list"))) return rc;
-    if ((rc = ensure(c, c->scratch, (size_t)big_ctas * 2 * scratch_cap * sizeof(Rec48), "oversize scratch"))) return rc;
     if ((rc = ensure(c, c->recs, max_records * sizeof(Rec32), "term records"))) return rc;
 
     uint64_t n_tiles_total = 0;
     uint32_t n_big_total = 0;
+    const int tile_ctas = 2 * c->sm_count;
     for (size_t pi = 0; pi < passes.size(); ++pi) {
         const Pass &P = passes[pi];
         n_tiles_total += P.n_tiles;
@@ -399,12 +410,9 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
         tp.ref_keys = (const uint64_t *)c->ref_keys.ptr;
         tp.n_tiles = P.n_tiles;
         tp.e0 = r.e0;
-        tp.parts = (TilePart *)c->parts.ptr;
+        tp.acc = acc;
         tp.big_list = (uint32_t *)c->big_list.ptr;
-        tp.big_count = (unsigned int *)c->big_count.ptr;
-        tp.err = (uint32_t *)c->err_word.ptr;
-        tp.scratch = (Rec48 *)c->scratch.ptr;
-        tp.scratch_cap = scratch_cap;
+        tp.err = errw;
         if (dump) {
             tp.dump_keys = (uint64_t *)c->dump_keys.ptr;
             tp.dump_num = (double *)c->dump_num.ptr;
@@ -412,56 +420,71 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
             tp.dump_count = (unsigned long long *)c->dump_count.ptr;
             tp.dump_cap = dump->cap;
         }
-        CK(cudaMemsetAsync(c->big_count.ptr, 0, 4, st), "memset");
-        CK(launch_tiles(tp, st), "tile kernel");
+        CK(launch_tiles(tp, tile_ctas, st), "tile kernel");
+        c->launches++;
         if (prof) CK(cudaEventRecord(E[5], st), "event");
-        CK(launch_big_tiles(tp, big_ctas, st), "oversize tile kernel");
+        // oversize tiles: size the scratch from what the tile kernel found
+        struct {
+            unsigned int n_big;
+            unsigned int pad;
+            unsigned long long big_max;
+        } bi;
+        CK(cudaMemcpyAsync(&bi, &acc->n_big, sizeof bi, cudaMemcpyDeviceToHost, st), "copy");
+        CK(cudaStreamSynchronize(st), "sync");
+        n_big_total += bi.n_big;
+        if (bi.n_big) {
+            uint64_t cap = bi.big_max;
+            int ctas = (int)std::min<uint64_t>(bi.n_big, (uint64_t)c->sm_count);
+            // keep the scratch within 2 GB (or what a single tile needs)
+            while (ctas > 1 && (uint64_t)ctas * 2 * cap * sizeof(Rec48) > (2ull << 30)) ctas /= 2;
+            if ((rc = ensure(c, c->scratch, (size_t)ctas * 2 * cap * sizeof(Rec48), "oversize scratch"))) return rc;
+            tp.scratch = (Rec48 *)c->scratch.ptr;
+            tp.scratch_cap = cap;
+            CK(launch_big_tiles(tp, ctas, st), "oversize tile kernel");
+            c->launches++;
+        }
         if (prof) CK(cudaEventRecord(E[6], st), "event");
-        CK(launch_pass_reduce(tp.parts, P.n_tiles, (TilePart *)c->chunk_tmp.ptr, tp.tile_off, P.records,
-                              (RunAcc *)c->acc.ptr, st),
-           "pass reduce");
-        c->launches += 4;
+        CK(launch_pass_finish(tp.tile_off, P.n_tiles, P.records, acc, errw, st), "pass finish");
+        c->launches++;
         if (prof) {
             CK(cudaEventRecord(E[7], st), "event");
             CK(cudaEventSynchronize(E[7]), "sync");
             float ms;
-            const int map[7] = {1, 2, 3, 4, 5, 6, 7};
             for (int k = 0; k < 7; ++k) {
                 cudaEventElapsedTime(&ms, E[k], E[k + 1]);
-                c->phase_ms[map[k]] += ms;
+                c->phase_ms[k + 1] += ms;
             }
         }
-        unsigned int nb = 0;
-        CK(cudaMemcpyAsync(&nb, c->big_count.ptr, 4, cudaMemcpyDeviceToHost, st), "copy");
-        CK(cudaStreamSynchronize(st), "sync");
-        n_big_total += nb;
     }
-    RunAcc acc;
+    CK(launch_acc_finalize(acc, st), "finalize");
+    c->launches++;
+    RunAcc h;
     uint32_t err = 0;
-    CK(cudaMemcpyAsync(&acc, c->acc.ptr, sizeof acc, cudaMemcpyDeviceToHost, st), "copy");
-    CK(cudaMemcpyAsync(&err, c->err_word.ptr, 4, cudaMemcpyDeviceToHost, st), "copy");
+    CK(cudaMemcpyAsync(&h, acc, sizeof h, cudaMemcpyDeviceToHost, st), "copy");
+    CK(cudaMemcpyAsync(&err, errw, 4, cudaMemcpyDeviceToHost, st), "copy");
     CK(cudaEventRecord(c->ev[1], st), "event");
     CK(cudaStreamSynchronize(st), "sync");
     float ms = 0;
     cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-    err |= acc.err;
+    err |= h.err;
     if ((rc = status_of_err(c, err))) return rc;
     memset(out, 0, sizeof *out);
-    out->e2 = acc.e2_s + acc.e2_c;
-    out->n_terms = acc.n_terms;
-    out->n_unique = acc.n_unique;
-    out->n_in_ref = acc.n_in_ref;
-    out->n_external = acc.n_ext;
-    out->digest_sum = acc.dsum;
-    out->digest_xor = acc.dxor;
-    out->min_abs_denom = acc.n_ext ? acc.min_den : INFINITY;
-    out->n_pos_denom = acc.n_pos;
+    out->e2 = h.e2;
+    out->n_terms = h.n_terms;
+    out->n_unique = h.n_unique;
+    out->n_in_ref = h.n_in_ref;
+    out->n_external = h.n_ext;
+    out->digest_sum = h.dsum;
+    out->digest_xor = h.dxor;
+    out->min_abs_denom = h.min_abs_den;
+    out->n_pos_denom = h.n_pos;
     out->n_passes = (uint32_t)passes.size();
     out->n_tiles = (uint32_t)std::min<uint64_t>(n_tiles_total, 0xFFFFFFFFull);
     out->n_oversize = n_big_total;
     out->seconds = ms * 1e-3;
-    if (acc.n_terms != total) return fail(c, PT2_ERR_CUDA, "generated %llu terms, planned %llu",
-                                          (unsigned long long)acc.n_terms, (unsigned long long)total);
+    if (h.n_terms != total)
+        return fail(c, PT2_ERR_CUDA, "generated %llu terms, planned %llu", (unsigned long long)h.n_terms,
+                    (unsigned long long)total);
     if (dump) {
         unsigned long long nd = 0;
         CK(cudaMemcpy(&nd, c->dump_count.ptr, 8, cudaMemcpyDeviceToHost), "copy");
@@ -500,6 +523,7 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
                     prop.major, prop.minor);
     auto c = std::make_unique<pt2_ctx>();
     c->device = device;
+    c->sm_count = prop.multiProcessorCount;
     size_t fr = 0, tot = 0;
     e = cudaMemGetInfo(&fr, &tot);
     if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e));
@@ -536,21 +560,12 @@ void pt2_destroy(pt2_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (auto &kv : c->refs) {
-        dev_free(c, kv.second->keys);
-        dev_free(c, kv.second->coef);
-        dev_free(c, kv.second->hii);
-    }
-    for (auto &kv : c->systems) {
-        dev_free(c, kv.second->h);
-        dev_free(c, kv.second->eri);
-        dev_free(c, kv.second->J);
-        dev_free(c, kv.second->WS);
-    }
-    DevBuf *bufs[] = {&c->hash, &c->class_counts, &c->tile_counts, &c->tile_off, &c->cursor, &c->scan_tmp,
-                      &c->recs, &c->parts, &c->chunk_tmp, &c->ref_tile, &c->ref_count, &c->ref_off,
-                      &c->ref_cursor, &c->ref_keys, &c->big_list, &c->big_count, &c->scratch, &c->acc,
-                      &c->err_word, &c->dump_keys, &c->dump_num, &c->dump_haa, &c->dump_count};
+    for (auto &kv : c->refs) free_ref(c, *kv.second);
+    for (auto &kv : c->systems) free_system(c, *kv.second);
+    DevBuf *bufs[] = {&c->hash,      &c->class_counts, &c->tile_counts, &c->tile_off, &c->cursor,
+                      &c->scan_tmp,  &c->recs,         &c->ref_tile,    &c->ref_count, &c->ref_off,
+                      &c->ref_cursor, &c->ref_keys,    &c->big_list,    &c->scratch,  &c->acc,
+                      &c->err_word,  &c->dump_keys,    &c->dump_num,    &c->dump_haa, &c->dump_count};
     for (DevBuf *b : bufs) dev_free(c, *b);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
@@ -582,24 +597,44 @@ int pt2_load_system(pt2_ctx *c, int n_orb, const double *h, const double *eri, u
                         return fail(c, PT2_ERR_INVALID, "eri lacks 8-fold symmetry at (%zu %zu|%zu %zu)", p, q, r, s);
                 }
     cudaSetDevice(c->device);
+    // Coulomb and same-spin pair energies, as doubles for the direct diagonal and
+    // as exact 2^-48 Ha integers for the incremental diagonal of the generator
     std::vector<double> J(n2), WS(n2);
-    for (size_t p = 0; p < n; ++p)
+    std::vector<int64_t> Jx(n2), WSx(n2), hdx(n);
+    double gbound = 0.0;
+    for (size_t p = 0; p < n; ++p) {
+        double row = std::fabs(h[p * n + p]);
         for (size_t q = 0; q < n; ++q) {
             J[p * n + q] = E(p, p, q, q);
             WS[p * n + q] = E(p, p, q, q) - E(p, q, q, p);
+            row += std::max(std::fabs(J[p * n + q]), std::fabs(WS[p * n + q]));
+            Jx[p * n + q] = std::llrint(J[p * n + q] * kDenScale);
+            WSx[p * n + q] = std::llrint(WS[p * n + q] * kDenScale);
         }
+        hdx[p] = std::llrint(h[p * n + p] * kDenScale);
+        gbound = std::max(gbound, row);
+    }
+    if (gbound >= kDenRange)
+        return fail(c, PT2_ERR_UNSUPPORTED,
+                    "orbital energy bound %.1f Ha exceeds the %.0f Ha range of the fixed-point diagonal", gbound,
+                    kDenRange);
     auto s = std::make_unique<SystemRes>();
     s->n = n_orb;
     int rc;
     if ((rc = dev_alloc(c, s->h, n2 * 8, "h")) || (rc = dev_alloc(c, s->eri, n4 * 8, "eri")) ||
-        (rc = dev_alloc(c, s->J, n2 * 8, "J")) || (rc = dev_alloc(c, s->WS, n2 * 8, "WS"))) {
-        dev_free(c, s->h), dev_free(c, s->eri), dev_free(c, s->J), dev_free(c, s->WS);
+        (rc = dev_alloc(c, s->J, n2 * 8, "J")) || (rc = dev_alloc(c, s->WS, n2 * 8, "WS")) ||
+        (rc = dev_alloc(c, s->Jx, n2 * 8, "Jx")) || (rc = dev_alloc(c, s->WSx, n2 * 8, "WSx")) ||
+        (rc = dev_alloc(c, s->hdx, n * 8, "hdx"))) {
+        free_system(c, *s);
         return rc;
     }
     CK(cudaMemcpy(s->h.ptr, h, n2 * 8, cudaMemcpyHostToDevice), "copy h");
     CK(cudaMemcpy(s->eri.ptr, eri, n4 * 8, cudaMemcpyHostToDevice), "copy eri");
     CK(cudaMemcpy(s->J.ptr, J.data(), n2 * 8, cudaMemcpyHostToDevice), "copy J");
     CK(cudaMemcpy(s->WS.ptr, WS.data(), n2 * 8, cudaMemcpyHostToDevice), "copy WS");
+    CK(cudaMemcpy(s->Jx.ptr, Jx.data(), n2 * 8, cudaMemcpyHostToDevice), "copy Jx");
+    CK(cudaMemcpy(s->WSx.ptr, WSx.data(), n2 * 8, cudaMemcpyHostToDevice), "copy WSx");
+    CK(cudaMemcpy(s->hdx.ptr, hdx.data(), n * 8, cudaMemcpyHostToDevice), "copy hdx");
     uint32_t id = c->next_id++;
     c->systems[id] = std::move(s);
     *system_id = id;
@@ -640,15 +675,28 @@ int pt2_load_reference(pt2_ctx *c, uint32_t system_id, uint64_t n_det, const uin
     r->e0 = e0;
     int rc;
     if ((rc = dev_alloc(c, r->keys, n_det * 16, "reference keys")) ||
-        (rc = dev_alloc(c, r->coef, n_det * 8, "coefficients")) || (rc = dev_alloc(c, r->hii, n_det * 8, "diagonals"))) {
-        dev_free(c, r->keys), dev_free(c, r->coef), dev_free(c, r->hii);
+        (rc = dev_alloc(c, r->coef, n_det * 8, "coefficients")) ||
+        (rc = dev_alloc(c, r->hii, n_det * 8, "diagonals")) || (rc = dev_alloc(c, r->d0, n_det * 8, "denominators"))) {
+        free_ref(c, *r);
         return rc;
     }
     CK(cudaMemcpyAsync(r->keys.ptr, keys, n_det * 16, cudaMemcpyHostToDevice, c->stream), "copy keys");
     CK(cudaMemcpyAsync(r->coef.ptr, coef, n_det * 8, cudaMemcpyHostToDevice, c->stream), "copy coef");
     CK(launch_diag(sys_dev(s), (const uint64_t *)r->keys.ptr, n_det, (double *)r->hii.ptr, c->stream),
        "diagonal kernel");
-    CK(cudaStreamSynchronize(c->stream), "sync");
+    CK(launch_ref_d0((const double *)r->hii.ptr, n_det, e0, (int64_t *)r->d0.ptr, c->stream), "denominator kernel");
+    {
+        // E0 - H_ii must lie inside the fixed-point range of the diagonal
+        std::vector<double> hii(n_det);
+        CK(cudaMemcpyAsync(hii.data(), r->hii.ptr, n_det * 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        for (uint64_t i = 0; i < n_det; ++i)
+            if (!(std::fabs(e0 - hii[i]) < kDenRange)) {
+                free_ref(c, *r);
+                return fail(c, PT2_ERR_UNSUPPORTED, "|E0 - H_ii| = %g Ha for determinant %llu exceeds %.0f Ha",
+                            std::fabs(e0 - hii[i]), (unsigned long long)i, kDenRange);
+            }
+    }
     s.refs++;
     uint32_t id = c->next_id++;
     c->refs[id] = std::move(r);
@@ -664,9 +712,7 @@ int pt2_unload(pt2_ctx *c, uint32_t id)
     auto ri = c->refs.find(id);
     if (ri != c->refs.end()) {
         RefRes &r = *ri->second;
-        dev_free(c, r.keys);
-        dev_free(c, r.coef);
-        dev_free(c, r.hii);
+        free_ref(c, r);
         c->systems.at(r.system)->refs--;
         c->refs.erase(ri);
         return PT2_OK;
@@ -674,11 +720,7 @@ int pt2_unload(pt2_ctx *c, uint32_t id)
     auto si = c->systems.find(id);
     if (si != c->systems.end()) {
         if (si->second->refs > 0) return fail(c, PT2_ERR_INVALID, "system %u is still used by a reference", id);
-        SystemRes &s = *si->second;
-        dev_free(c, s.h);
-        dev_free(c, s.eri);
-        dev_free(c, s.J);
-        dev_free(c, s.WS);
+        free_system(c, *si->second);
         c->systems.erase(si);
         return PT2_OK;
     }
@@ -775,7 +817,9 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
         keys[2 * i] = h[i].a;
         keys[2 * i + 1] = h[i].b;
         val[i] = h[i].num;
-        haa[i] = h[i].haa;
+        double d;
+        memcpy(&d, &h[i].den, 8);  // this mode stores H_aa itself
+        haa[i] = d;
     }
     return PT2_OK;
 }

@@ -12,25 +12,38 @@ constexpr int kMaxOrb = 64;
 constexpr int kClassBits = 12;               // alpha-hash classes used to form passes
 constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
+constexpr int kGenBatch = 4;                 // terms a lane prepares before issuing their atomics
 constexpr int kTileThreads = 512;            // tile sort-reduce CTA
-constexpr int kTileCap = 2048;               // records a tile CTA groups in shared memory
+constexpr int kTileCap = 1536;               // records a tile CTA groups in shared memory
+constexpr int kTileBuckets = 1024;           // hash buckets of the in-tile counting sort (>= kTileCap / 2)
 constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
 constexpr int kBigThreads = 512;
 constexpr int kBigCap = 2048;                // Rec48 records grouped per chunk (oversize path)
+constexpr int kBigBuckets = 2048;
 
-// Device error bits (OR-ed into RunAcc::err).
-constexpr uint32_t kErrFixedRange = 1u;      // |numerator| beyond the fixed-point range
+// Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is
+// assembled from) are int64 multiples of 2^-48 Ha; numerator and energy sums
+// are int128 multiples of 2^-90.  Integer sums are exact and associative, so
+// results do not depend on the order in which terms meet.
+constexpr int kDenShift = 48;
+constexpr double kDenScale = 281474976710656.0;  // 2^48
+constexpr double kDenRange = 2048.0;             // |component| bound validated at load (2^11 Ha)
+constexpr int kFxShift = 90;
+
+// Device error bits (OR-ed into the run's error word).
+constexpr uint32_t kErrFixedRange = 1u;      // |numerator| or |term| beyond the fixed-point range
 constexpr uint32_t kErrWaitTimeout = 2u;     // a bounded mbarrier wait ran out
 constexpr uint32_t kErrScratch = 4u;         // oversize tile larger than its scratch
 constexpr uint32_t kErrNoProgress = 8u;      // chunked grouping could not shrink a tile
 constexpr uint32_t kErrCount = 16u;          // emitted terms differ from the plan
-constexpr uint32_t kErrDump = 32u;           // dump capacity exceeded
 
 // One generated term: the excited determinant, its numerator H_ai c_i and
-// its diagonal H_aa (computed incrementally from the parent determinant).
+// its denominator E0 - H_aa in units of 2^-48 Ha (from the parent's diagonal
+// plus the exact incremental change, see the appendix on fast diagonals).
 struct __align__(32) Rec32 {
     uint64_t a, b;
-    double num, haa;
+    double num;
+    int64_t den;
 };
 
 // A partially reduced key (oversize path): exact fixed-point numerator sum.
@@ -38,16 +51,19 @@ struct __align__(16) Rec48 {
     uint64_t a, b;
     uint64_t fx_lo;
     int64_t fx_hi;
-    double haa;
+    int64_t den;
     uint64_t pad;
 };
 
 struct SysDev {
     int n;
-    const double *h;    // n*n
-    const double *eri;  // n^4
-    const double *J;    // n*n: (pp|qq)
-    const double *WS;   // n*n: (pp|qq) - (pq|qp), same-spin pair energy
+    const double *h;     // n*n
+    const double *eri;   // n^4
+    const int64_t *Jx;   // n*n: (pp|qq) * 2^48
+    const int64_t *WSx;  // n*n: ((pp|qq) - (pq|qp)) * 2^48, same-spin pair energy
+    const int64_t *hdx;  // n: h_pp * 2^48
+    const double *J;     // n*n (direct diagonal kernel)
+    const double *WS;    // n*n
 };
 
 struct HashTables {
@@ -63,7 +79,8 @@ struct GenParams {
     const HashTables *hash;
     const uint64_t *keys;  // 2 * n_det
     const double *coef;
-    const double *hii;
+    const int64_t *d0;     // (E0 - H_ii) * 2^48 per determinant
+    double e0;
     uint64_t n_det;
     uint64_t det_begin;    // first determinant of this launch
     int na, nb;            // electrons per spin (same for all determinants)
@@ -83,19 +100,17 @@ struct GenParams {
     int n_sa, n_sb;                    // singles per determinant: na*(n-na), nb*(n-nb)
 };
 
-struct TilePart {
-    double e2;
-    double min_den;
-    uint64_t dsum, dxor;
-    uint32_t n_unique, n_in_ref, n_ext, n_pos;
-};
-
+// Run accumulator: every field is an exact integer reduction.
 struct RunAcc {
-    double e2_s, e2_c;  // Neumaier-compensated pass sums
-    double min_den;
-    unsigned long long n_terms, n_unique, n_in_ref, n_ext, dsum, dxor, n_pos;
+    unsigned long long e2_lo;  // E2 * 2^90 as a 128-bit two's-complement integer
+    long long e2_hi;
+    unsigned long long n_terms, n_unique, n_in_ref, n_ext, n_pos, dsum, dxor;
+    unsigned long long min_den;  // min |E0 - H_aa| * 2^48
+    double e2;                   // filled by the finalize kernel
+    double min_abs_den;
     unsigned int err;
     unsigned int n_big;
+    unsigned long long big_max;  // largest oversize tile of the last pass
 };
 
 struct TileParams {
@@ -105,9 +120,8 @@ struct TileParams {
     const uint64_t *ref_keys;            // 2 * (refs in pass), grouped by tile, sorted per tile
     uint64_t n_tiles;
     double e0;
-    TilePart *parts;
+    RunAcc *acc;
     uint32_t *big_list;
-    unsigned int *big_count;
     uint32_t *err;
     // dump of the external set (optional)
     uint64_t *dump_keys;
@@ -137,19 +151,19 @@ struct RefPartParams {
 void gen_layout(GenParams &p, GenMode mode);  // fills the smem_* fields from n_sa, n_sb
 cudaError_t launch_gen(GenMode mode, const GenParams &p, uint64_t n_dets, cudaStream_t s);
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s);
+cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s);
 cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint64_t n,
                                    unsigned long long *tmp, cudaStream_t s);
 size_t scan_tmp_elems(uint64_t n);
 cudaError_t launch_ref_partition(const RefPartParams &p, int phase, cudaStream_t s);
 cudaError_t launch_sort_slices(const unsigned long long *ref_off, uint64_t *ref_keys, uint64_t n_tiles,
                                cudaStream_t s);
-cudaError_t launch_tiles(const TileParams &p, cudaStream_t s);
+cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s);
 cudaError_t launch_big_tiles(const TileParams &p, int n_ctas, cudaStream_t s);
-cudaError_t launch_pass_reduce(const TilePart *parts, uint64_t n_tiles, TilePart *chunk_tmp,
-                               const unsigned long long *tile_off, unsigned long long expected_terms,
-                               RunAcc *acc, cudaStream_t s);
+cudaError_t launch_pass_finish(const unsigned long long *tile_off, uint64_t n_tiles,
+                               unsigned long long expected_terms, RunAcc *acc, uint32_t *err, cudaStream_t s);
 cudaError_t launch_acc_init(RunAcc *acc, cudaStream_t s);
-int big_grid();
+cudaError_t launch_acc_finalize(RunAcc *acc, cudaStream_t s);
 size_t tile_smem_bytes();
 size_t big_smem_bytes();
 

@@ -7,15 +7,21 @@
 //     scan            tile offsets
 //     gen<Emit>       every single/double of every reference determinant whose
 //                     alpha word falls in the pass: key, H_ai c_i (Slater-Condon,
-//                     fermionic phase) and H_aa (incremental diagonal), written
-//                     into its tile
+//                     fermionic phase) and E0 - H_aa (exact incremental diagonal),
+//                     written into its tile
 //     ref partition   reference keys of the pass, grouped by tile and sorted
-//     tile            per tile, in shared memory: bucket sort by key hash then
+//     tile            per tile, in shared memory: counting sort by key hash then
 //                     insertion sort by the 128-bit key (equal keys adjacent),
 //                     reduce_by_key, explicit filter of reference keys by binary
-//                     search, num^2 / (E0 - H_aa), fixed-order block reduction
+//                     search, num^2 / (E0 - H_aa) accumulated exactly
 //     big tile        tiles larger than shared memory, grouped in chunks
-//     pass reduce     fixed-order sum of tile partials into the run total
+//
+// FP64 is the scarce unit on this GPU, so every quantity with a natural exact
+// integer form is kept as one: the diagonal difference (int64, 2^-48 Ha), the
+// per-key numerator sum and the energy sum (int128, 2^-90).  FP64 is used for
+// the Slater-Condon products, the square and the reciprocal of the
+// denominator.  Integer sums are associative, so the energy is bit-identical
+// for any tiling, pass plan, reference order or atomic interleaving.
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
@@ -70,29 +76,42 @@ __device__ __forceinline__ uint32_t bucket_hash(uint64_t a, uint64_t b)
     return (uint32_t)h;
 }
 
-// Exact fixed-point accumulation of numerators: value * 2^90 as a 128-bit
-// two's-complement integer.  Integer addition is associative, so the sum of
-// the duplicates of a key does not depend on the order in which the tile
-// received them; it is rounded to FP64 once.  |value| must stay below 2^36.
-constexpr int kFxShift = 90;
+__device__ __forceinline__ bool key_less(uint64_t a0, uint64_t b0, uint64_t a1, uint64_t b1)
+{
+    return a0 < a1 || (a0 == a1 && b0 < b1);
+}
 
+// ---------------------------------------------------- exact fixed point
+
+// Add value * 2^90 (rounded half away from zero) to the 128-bit integer
+// (lo, hi).  |value| must stay below 2^36, else the range bit is set.
 __device__ __forceinline__ void fx_add_double(uint64_t &lo, int64_t &hi, double v, uint32_t &err)
 {
     uint64_t bits = (uint64_t)__double_as_longlong(v);
     int e = (int)((bits >> 52) & 0x7FF);
-    if (e == 0) return;                  // zero / subnormal: below the resolution
-    if (e >= 1023 + 36) { err |= kErrFixedRange; return; }
+    if (e == 0) return;  // zero / subnormal: below the resolution
+    if (e >= 1023 + 36) {
+        err |= kErrFixedRange;
+        return;
+    }
     uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    int sh = e - 1075 + kFxShift;        // value = m * 2^(e - 1075)
+    int sh = e - 1075 + kFxShift;  // value = m * 2^(e - 1075)
     uint64_t ml, mh;
     if (sh >= 0) {
-        if (sh == 0) { ml = m; mh = 0; }
-        else if (sh < 64) { ml = m << sh; mh = m >> (64 - sh); }
-        else { ml = 0; mh = m << (sh - 64); }
+        if (sh == 0) {
+            ml = m;
+            mh = 0;
+        } else if (sh < 64) {
+            ml = m << sh;
+            mh = m >> (64 - sh);
+        } else {
+            ml = 0;
+            mh = m << (sh - 64);
+        }
     } else {
         int r = -sh;
         if (r > 63) return;
-        ml = (m + (1ull << (r - 1))) >> r;  // round half away from zero on |value|
+        ml = (m + (1ull << (r - 1))) >> r;
         mh = 0;
     }
     if (bits >> 63) {
@@ -116,6 +135,39 @@ __device__ __forceinline__ void fx_add_fx(uint64_t &lo, int64_t &hi, uint64_t bl
     lo = nlo;
 }
 
+// Round a 128-bit magnitude times 2^-scale to the nearest double (ties to
+// even), by assembling the IEEE bits with integer operations.
+__device__ __forceinline__ double u128_to_double(uint64_t ulo, uint64_t uhi, int scale, bool neg)
+{
+    if ((ulo | uhi) == 0) return neg ? -0.0 : 0.0;
+    int msb = uhi ? 127 - __clzll((long long)uhi) : 63 - __clzll((long long)ulo);
+    uint64_t mant;
+    int ex = msb - scale;
+    if (msb <= 52) {
+        mant = ulo << (52 - msb);
+    } else {
+        int sh = msb - 52;  // 1..75
+        uint64_t lo2 = sh < 64 ? (ulo >> sh) | (uhi << (64 - sh)) : (uhi >> (sh - 64));
+        int rb = sh - 1;
+        uint64_t round = rb < 64 ? (ulo >> rb) & 1ull : (uhi >> (rb - 64)) & 1ull;
+        bool sticky;
+        if (rb == 0) sticky = false;
+        else if (rb < 64) sticky = (ulo & ((1ull << rb) - 1ull)) != 0;
+        else if (rb == 64) sticky = ulo != 0;
+        else sticky = ulo != 0 || (uhi & ((1ull << (rb - 64)) - 1ull)) != 0;
+        mant = lo2;
+        if (round && (sticky || (mant & 1ull))) {
+            ++mant;
+            if (mant >> 53) {
+                mant >>= 1;
+                ++ex;
+            }
+        }
+    }
+    uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)(ex + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ double fx_to_double(uint64_t lo, int64_t hi)
 {
     bool neg = hi < 0;
@@ -124,14 +176,32 @@ __device__ __forceinline__ double fx_to_double(uint64_t lo, int64_t hi)
         ulo = ~ulo + 1ull;
         uhi = ~uhi + (ulo == 0 ? 1ull : 0ull);
     }
-    double d = __fma_rn(__ull2double_rn(uhi), 0x1p64, __ull2double_rn(ulo));
-    d *= 0x1p-90;
-    return neg ? -d : d;
+    return u128_to_double(ulo, uhi, kFxShift, neg);
 }
 
-__device__ __forceinline__ bool key_less(uint64_t a0, uint64_t b0, uint64_t a1, uint64_t b1)
+__device__ __forceinline__ double den_to_double(int64_t d)
 {
-    return a0 < a1 || (a0 == a1 && b0 < b1);
+    bool neg = d < 0;
+    uint64_t m = neg ? (uint64_t)(-d) : (uint64_t)d;
+    return u128_to_double(m, 0, kDenShift, neg);
+}
+
+// Reciprocal of d: a single-precision hardware estimate refined by one
+// Newton-Raphson step, x1 = x0 (2 - d x0) (relative error about 2^-46).
+__device__ __forceinline__ double recip(double d, int64_t dfx)
+{
+    float f = __ll2float_rn((long long)dfx) * 0x1p-48f;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
+    uint32_t fb = __float_as_uint(rf);
+    uint32_t fe = (fb >> 23) & 0xFF;
+    uint64_t db;
+    if (fe == 0) db = (uint64_t)(fb >> 31) << 63;
+    else if (fe == 0xFF) db = ((uint64_t)(fb >> 31) << 63) | (0x7FFull << 52) | ((uint64_t)(fb & 0x7FFFFF) << 29);
+    else db = ((uint64_t)(fb >> 31) << 63) | ((uint64_t)(fe + 896) << 52) | ((uint64_t)(fb & 0x7FFFFF) << 29);
+    double x = __longlong_as_double((long long)db);
+    double e = __fma_rn(-d, x, 1.0);
+    return __fma_rn(x, e, x);
 }
 
 // ------------------------------------------------- mbarrier + TMA bulk copy
@@ -246,10 +316,11 @@ __device__ void block_scan_excl_u32(uint32_t *a, int n, uint32_t *warp_tot)
 
 struct GenFixed {
     uint64_t zc[kMaxOrb], zta[kMaxOrb], ztb[kMaxOrb];
-    double gA[kMaxOrb], gB[kMaxOrb];
+    int64_t gA[kMaxOrb], gB[kMaxOrb];  // (h_xx + p(x)) * 2^48 for alpha / beta spin-orbital x
     int occA[kMaxOrb], virA[kMaxOrb], occB[kMaxOrb], virB[kMaxOrb];
     uint64_t A, B, ZcA, ZtaA, ZtbB;
-    double c, hii;
+    double c;
+    int64_t d0;
     int n_sa_pass, a_in_pass;
 };
 
@@ -263,70 +334,90 @@ __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
     j1 = t - k * (k - 1) / 2;
 }
 
+// A lane's batch of up to kGenBatch terms: all tiles and slots are requested
+// before any record is stored, so the atomics of a batch are in flight together.
 template <int MODE>
-__device__ __forceinline__ void sink(const GenParams &p, uint64_t a, uint64_t b, uint64_t zt, double num,
-                                     double haa)
-{
-    if constexpr (MODE == kModeTileCount) {
-        uint64_t t = __umul64hi(zt, p.n_tiles);
-        atomicAdd(&p.tile_counts[t], 1u);
-    } else if constexpr (MODE == kModeEmit) {
-        uint64_t t = __umul64hi(zt, p.n_tiles);
-        unsigned long long slot = atomicAdd(&p.cursor[t], 1ull);
-        if (slot >= p.rec_cap) {  // emission disagrees with the tile counts
-            atomicOr(p.err, kErrCount);
-            return;
-        }
-        double2 *dst = reinterpret_cast<double2 *>(p.recs + slot);
-        dst[0] = make_double2(__longlong_as_double((long long)a), __longlong_as_double((long long)b));
-        dst[1] = make_double2(num, haa);
-    } else if constexpr (MODE == kModeDetTerms) {
-        unsigned long long slot = atomicAdd(&p.cursor[0], 1ull);
-        if (slot < p.rec_cap) {
-            Rec32 r;
-            r.a = a;
-            r.b = b;
-            r.num = num;
-            r.haa = haa;
-            p.recs[slot] = r;
+struct Batch {
+    uint64_t a[kGenBatch], b[kGenBatch], zt[kGenBatch];
+    double num[kGenBatch];
+    int64_t den[kGenBatch];
+    bool ok[kGenBatch];
+
+    __device__ __forceinline__ void flush(const GenParams &p)
+    {
+        if constexpr (MODE == kModeTileCount) {
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u)
+                if (ok[u]) atomicAdd(&p.tile_counts[__umul64hi(zt[u], p.n_tiles)], 1u);
+        } else if constexpr (MODE == kModeEmit) {
+            unsigned long long slot[kGenBatch];
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u)
+                slot[u] = ok[u] ? atomicAdd(&p.cursor[__umul64hi(zt[u], p.n_tiles)], 1ull) : 0ull;
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u) {
+                if (!ok[u]) continue;
+                if (slot[u] >= p.rec_cap) {  // emission disagrees with the tile counts
+                    atomicOr(p.err, kErrCount);
+                    continue;
+                }
+                double2 *dst = reinterpret_cast<double2 *>(p.recs + slot[u]);
+                dst[0] = make_double2(__longlong_as_double((long long)a[u]), __longlong_as_double((long long)b[u]));
+                dst[1] = make_double2(num[u], __longlong_as_double((long long)den[u]));
+            }
+        } else if constexpr (MODE == kModeDetTerms) {
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u) {
+                if (!ok[u]) continue;
+                unsigned long long slot = atomicAdd(&p.cursor[0], 1ull);
+                if (slot < p.rec_cap) {
+                    Rec32 r;
+                    r.a = a[u];
+                    r.b = b[u];
+                    r.num = num[u];
+                    // this mode reports H_aa itself (as double bits) for parity checks
+                    r.den = __double_as_longlong(p.e0 - den_to_double(den[u]));
+                    p.recs[slot] = r;
+                }
+            }
         }
     }
-}
+};
 
 template <int MODE>
-__global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
+__global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     GenFixed &F = *reinterpret_cast<GenFixed *>(smem);
-    double *sa_delta = reinterpret_cast<double *>(smem + p.smem_sa);
+    int64_t *sa_delta = reinterpret_cast<int64_t *>(smem + p.smem_sa);
     uint64_t *sa_zt = reinterpret_cast<uint64_t *>(sa_delta + p.n_sa);
     uint32_t *sa_info = reinterpret_cast<uint32_t *>(sa_zt + p.n_sa);
     uint16_t *sa_pass = reinterpret_cast<uint16_t *>(sa_info + p.n_sa);
-    double *sb_delta = reinterpret_cast<double *>(smem + p.smem_sb);
+    int64_t *sb_delta = reinterpret_cast<int64_t *>(smem + p.smem_sb);
     uint64_t *sb_zt = reinterpret_cast<uint64_t *>(sb_delta + p.n_sb);
     uint32_t *sb_info = reinterpret_cast<uint32_t *>(sb_zt + p.n_sb);
     uint16_t *pairs = reinterpret_cast<uint16_t *>(smem + p.smem_pairs);
-    double *vec_all = reinterpret_cast<double *>(smem + p.smem_vec);
+    int64_t *vec_all = reinterpret_cast<int64_t *>(smem + p.smem_vec);
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + p.smem_hist);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nw = kGenThreads / 32;
+    constexpr bool kVal = MODE == kModeEmit || MODE == kModeDetTerms;
     const int N = p.sys.n;
     const int na = p.na, nb = p.nb, nva = N - na, nvb = N - nb;
     const uint64_t det = p.det_begin + blockIdx.x;
     const double *__restrict__ eri = p.sys.eri;
-    const double *__restrict__ Jt = p.sys.J;
-    const double *__restrict__ WSt = p.sys.WS;
+    const int64_t *__restrict__ Jx = p.sys.Jx;
+    const int64_t *__restrict__ WSx = p.sys.WSx;
     const double *__restrict__ ht = p.sys.h;
-    double *vec = vec_all + warp * kMaxOrb;
+    int64_t *vec = vec_all + warp * kMaxOrb;
 
     for (int i = tid; i < kMaxOrb; i += kGenThreads) {
         F.zc[i] = p.hash->zc[i];
         F.zta[i] = p.hash->zta[i];
         F.ztb[i] = p.hash->ztb[i];
     }
-    const int max_m = N;  // pairs over at most N items
-    for (int t = tid; t < max_m * (max_m - 1) / 2; t += kGenThreads) {
+    for (int t = tid; t < N * (N - 1) / 2; t += kGenThreads) {
         int j1, j2;
         pair_of(t, j1, j2);
         pairs[t] = (uint16_t)(j1 | (j2 << 8));
@@ -338,17 +429,22 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
         F.A = A;
         F.B = B;
         F.c = p.coef[det];
-        F.hii = p.hii[det];
+        F.d0 = p.d0[det];
         int ia = 0, iva = 0, ib = 0, ivb = 0;
         for (int q = 0; q < N; ++q) {
-            if ((A >> q) & 1ull) F.occA[ia++] = q; else F.virA[iva++] = q;
-            if ((B >> q) & 1ull) F.occB[ib++] = q; else F.virB[ivb++] = q;
+            if ((A >> q) & 1ull) F.occA[ia++] = q;
+            else F.virA[iva++] = q;
+            if ((B >> q) & 1ull) F.occB[ib++] = q;
+            else F.virB[ivb++] = q;
         }
     }
     __syncthreads();
     if (warp == 0) {
         uint64_t zc = 0, za = 0, zb = 0;
-        for (int i = lane; i < na; i += 32) { zc ^= F.zc[F.occA[i]]; za ^= F.zta[F.occA[i]]; }
+        for (int i = lane; i < na; i += 32) {
+            zc ^= F.zc[F.occA[i]];
+            za ^= F.zta[F.occA[i]];
+        }
         for (int i = lane; i < nb; i += 32) zb ^= F.ztb[F.occB[i]];
 #pragma unroll
         for (int off = 16; off; off >>= 1) {
@@ -362,23 +458,24 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
             F.ZtbB = zb;
         }
     } else if (warp == 1 || warp == 2) {
-        // g(x) = h_xx + p(x), p(x) = sum over occupied j of <xj||xj>
+        // g(x) = h_xx + p(x), p(x) = sum over occupied j of <xj||xj>, exact in 2^-48 units
         const int spin = warp - 1;  // 0: alpha x, 1: beta x
         const int *os = spin ? F.occB : F.occA;
         const int *oo = spin ? F.occA : F.occB;
         const int ns = spin ? nb : na, no = spin ? na : nb;
         for (int x = lane; x < N; x += 32) {
-            double g = ht[x * N + x];
-            for (int k = 0; k < ns; ++k) g += WSt[x * N + os[k]];
-            for (int k = 0; k < no; ++k) g += Jt[x * N + oo[k]];
+            int64_t g = p.sys.hdx[x];
+            for (int k = 0; k < ns; ++k) g += WSx[x * N + os[k]];
+            for (int k = 0; k < no; ++k) g += Jx[x * N + oo[k]];
             (spin ? F.gB : F.gA)[x] = g;
         }
     }
     __syncthreads();
     const uint64_t A = F.A, B = F.B;
-    const double c = F.c, hii = F.hii;
+    const double c = F.c;
+    const int64_t d0 = F.d0;
 
-    // singles lists (alpha: with pass flag)
+    // singles lists; delta = H_aa - H_ii of the single, exact
     for (int s = tid; s < p.n_sa; s += kGenThreads) {
         int i = s / nva, j = s - (s / nva) * nva;
         int r = F.occA[i], a = F.virA[j];
@@ -392,7 +489,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
             uint32_t cl = class_of(zc);
             inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, a2);
         }
-        sa_delta[s] = F.gA[a] - F.gA[r] - WSt[r * N + a];
+        sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
         sa_zt[s] = (MODE == kModeClassCount) ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
         sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17);
     }
@@ -400,7 +497,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
         int i = s / nvb, j = s - (s / nvb) * nvb;
         int r = F.occB[i], a = F.virB[j];
         uint32_t sg = __popcll(B & between_mask(r, a)) & 1;
-        sb_delta[s] = F.gB[a] - F.gB[r] - WSt[r * N + a];
+        sb_delta[s] = F.gB[a] - F.gB[r] - WSx[r * N + a];
         sb_zt[s] = F.ZtbB ^ F.ztb[r] ^ F.ztb[a];
         sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16);
     }
@@ -435,8 +532,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
     if constexpr (MODE == kModeClassCount) {
         // work list (the paper's first pass over the wavefunction): terms per class
         if (tid == 0 && a_in)
-            atomicAdd(&hist[class_of(F.ZcA)],
-                      (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
+            atomicAdd(&hist[class_of(F.ZcA)], (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
         for (int k = tid; k < n_sa_pass; k += kGenThreads) {
             int s = sa_pass[k];
             atomicAdd(&hist[class_of(sa_zt[s])], (uint32_t)(1 + p.n_sb));
@@ -459,51 +555,67 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
             if (hist[i]) atomicAdd(&p.class_counts[i], (unsigned long long)hist[i]);
         return;
     } else {
-        constexpr bool kVal = MODE != kModeTileCount;
         const uint64_t ZtaA = F.ZtaA, ZtbB = F.ZtbB;
+        Batch<MODE> bt;
 
-        // ---- alpha singles
-        for (int k = tid; k < n_sa_pass; k += kGenThreads) {
-            int s = sa_pass[k];
-            uint32_t info = sa_info[s];
-            int r = info & 0xFF, a = (info >> 8) & 0xFF;
-            double num = 0.0, haa = 0.0;
-            if constexpr (kVal) {
-                double v = ht[a * N + r];
-                for (int q = 0; q < na; ++q) {
-                    int j = F.occA[q];
-                    v += eri[(((size_t)a * N + r) * N + j) * N + j] - eri[(((size_t)a * N + j) * N + j) * N + r];
+        // ---- alpha singles (few per determinant: O(n) element each)
+        for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch) {
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u) {
+                int k = k0 + u * kGenThreads;
+                bt.ok[u] = k < n_sa_pass;
+                if (!bt.ok[u]) continue;
+                int s = sa_pass[k];
+                uint32_t info = sa_info[s];
+                int r = info & 0xFF, a = (info >> 8) & 0xFF;
+                bt.a[u] = A ^ (1ull << r) ^ (1ull << a);
+                bt.b[u] = B;
+                bt.zt[u] = sa_zt[s] ^ ZtbB;
+                if constexpr (kVal) {
+                    double v = ht[a * N + r];
+                    for (int q = 0; q < na; ++q) {
+                        int j = F.occA[q];
+                        v += eri[(((size_t)a * N + r) * N + j) * N + j] - eri[(((size_t)a * N + j) * N + j) * N + r];
+                    }
+                    for (int q = 0; q < nb; ++q) {
+                        int j = F.occB[q];
+                        v += eri[(((size_t)a * N + r) * N + j) * N + j];
+                    }
+                    bt.num[u] = flip_sign(c * v, info >> 16);
+                    bt.den[u] = d0 - sa_delta[s];
                 }
-                for (int q = 0; q < nb; ++q) {
-                    int j = F.occB[q];
-                    v += eri[(((size_t)a * N + r) * N + j) * N + j];
-                }
-                num = flip_sign(c * v, info >> 16);
-                haa = hii + sa_delta[s];
             }
-            sink<MODE>(p, A ^ (1ull << r) ^ (1ull << a), B, sa_zt[s] ^ ZtbB, num, haa);
+            bt.flush(p);
         }
         // ---- beta singles
         if (a_in)
-            for (int s = tid; s < p.n_sb; s += kGenThreads) {
-                uint32_t info = sb_info[s];
-                int r = info & 0xFF, a = (info >> 8) & 0xFF;
-                double num = 0.0, haa = 0.0;
-                if constexpr (kVal) {
-                    double v = ht[a * N + r];
-                    for (int q = 0; q < nb; ++q) {
-                        int j = F.occB[q];
-                        v += eri[(((size_t)a * N + r) * N + j) * N + j] -
-                             eri[(((size_t)a * N + j) * N + j) * N + r];
+            for (int s0 = tid; s0 < p.n_sb; s0 += kGenThreads * kGenBatch) {
+#pragma unroll
+                for (int u = 0; u < kGenBatch; ++u) {
+                    int s = s0 + u * kGenThreads;
+                    bt.ok[u] = s < p.n_sb;
+                    if (!bt.ok[u]) continue;
+                    uint32_t info = sb_info[s];
+                    int r = info & 0xFF, a = (info >> 8) & 0xFF;
+                    bt.a[u] = A;
+                    bt.b[u] = B ^ (1ull << r) ^ (1ull << a);
+                    bt.zt[u] = ZtaA ^ sb_zt[s];
+                    if constexpr (kVal) {
+                        double v = ht[a * N + r];
+                        for (int q = 0; q < nb; ++q) {
+                            int j = F.occB[q];
+                            v += eri[(((size_t)a * N + r) * N + j) * N + j] -
+                                 eri[(((size_t)a * N + j) * N + j) * N + r];
+                        }
+                        for (int q = 0; q < na; ++q) {
+                            int j = F.occA[q];
+                            v += eri[(((size_t)a * N + r) * N + j) * N + j];
+                        }
+                        bt.num[u] = flip_sign(c * v, info >> 16);
+                        bt.den[u] = d0 - sb_delta[s];
                     }
-                    for (int q = 0; q < na; ++q) {
-                        int j = F.occA[q];
-                        v += eri[(((size_t)a * N + r) * N + j) * N + j];
-                    }
-                    num = flip_sign(c * v, info >> 16);
-                    haa = hii + sb_delta[s];
                 }
-                sink<MODE>(p, A, B ^ (1ull << r) ^ (1ull << a), ZtaA ^ sb_zt[s], num, haa);
+                bt.flush(p);
             }
         // ---- alpha-beta doubles: one alpha single per warp, beta singles over lanes
         for (int k = warp; k < n_sa_pass; k += nw) {
@@ -512,25 +624,34 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
             int rA = info & 0xFF, aA = (info >> 8) & 0xFF;
             uint64_t a2 = A ^ (1ull << rA) ^ (1ull << aA);
             uint64_t ztA = sa_zt[s];
-            double baseH = 0.0, cA = 0.0;
+            int64_t baseD = 0;
+            double cA = 0.0;
             const double *slice = nullptr;
             if constexpr (kVal) {
                 // u[q] = J(aA, q) - J(rA, q): the alpha-beta cross terms of H_aa
-                for (int q = lane; q < N; q += 32) vec[q] = Jt[aA * N + q] - Jt[rA * N + q];
+                for (int q = lane; q < N; q += 32) vec[q] = Jx[aA * N + q] - Jx[rA * N + q];
                 __syncwarp();
-                baseH = hii + sa_delta[s];
+                baseD = d0 - sa_delta[s];
                 cA = flip_sign(c, info >> 16);
                 slice = eri + ((size_t)aA * N + rA) * N * N;
             }
-            for (int sb = lane; sb < p.n_sb; sb += 32) {
-                uint32_t bi = sb_info[sb];
-                int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
-                double num = 0.0, haa = 0.0;
-                if constexpr (kVal) {
-                    num = flip_sign(cA * slice[aB * N + rB], bi >> 16);
-                    haa = baseH + sb_delta[sb] + (vec[aB] - vec[rB]);
+            for (int sb0 = lane; sb0 < p.n_sb; sb0 += 32 * kGenBatch) {
+#pragma unroll
+                for (int u = 0; u < kGenBatch; ++u) {
+                    int sb = sb0 + 32 * u;
+                    bt.ok[u] = sb < p.n_sb;
+                    if (!bt.ok[u]) continue;
+                    uint32_t bi = sb_info[sb];
+                    int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
+                    bt.a[u] = a2;
+                    bt.b[u] = B ^ (1ull << rB) ^ (1ull << aB);
+                    bt.zt[u] = ztA ^ sb_zt[sb];
+                    if constexpr (kVal) {
+                        bt.num[u] = flip_sign(cA * slice[aB * N + rB], bi >> 16);
+                        bt.den[u] = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
+                    }
                 }
-                sink<MODE>(p, a2, B ^ (1ull << rB) ^ (1ull << aB), ztA ^ sb_zt[sb], num, haa);
+                bt.flush(p);
             }
             __syncwarp();
         }
@@ -542,7 +663,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
             const int *occ = spin ? F.occB : F.occA;
             const int *vir = spin ? F.virB : F.virA;
             const int nv = spin ? nvb : nva;
-            const double *g = spin ? F.gB : F.gA;
+            const int64_t *g = spin ? F.gB : F.gA;
             const uint64_t W = spin ? B : A;
             for (int pi = warp; pi < npo; pi += nw) {
                 int pr = pairs[pi];
@@ -550,40 +671,51 @@ __global__ void __launch_bounds__(kGenThreads) gen_kernel(const GenParams p)
                 uint64_t w12 = W ^ (1ull << r1) ^ (1ull << r2);
                 uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
                 uint64_t zt12 = spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
-                double base = 0.0;
+                int64_t base = 0;
                 if constexpr (kVal) {
+                    // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
+                    // v(x) = g(x) - W(r1,x) - W(r2,x)
                     for (int j = lane; j < nv; j += 32) {
                         int x = vir[j];
-                        vec[j] = g[x] - WSt[r1 * N + x] - WSt[r2 * N + x];
+                        vec[j] = g[x] - WSx[r1 * N + x] - WSx[r2 * N + x];
                     }
                     __syncwarp();
-                    base = hii - g[r1] - g[r2] + WSt[r1 * N + r2];
+                    base = d0 + g[r1] + g[r2] - WSx[r1 * N + r2];
                 }
-                for (int t = lane; t < npv; t += 32) {
-                    int pv = pairs[t];
-                    int j1 = pv & 0xFF, j2 = pv >> 8;
-                    int a1 = vir[j1], a2 = vir[j2];
-                    uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
-                    uint64_t zt;
-                    if (spin == 0) {
-                        uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
-                        if (cl < p.class_lo || cl >= p.class_hi) continue;
-                        if (!cons_ok(p.cons_mod, p.cons_rem, w2)) continue;
-                        zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
-                    } else {
-                        zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
+                for (int t0 = lane; t0 < npv; t0 += 32 * kGenBatch) {
+#pragma unroll
+                    for (int u = 0; u < kGenBatch; ++u) {
+                        int t = t0 + 32 * u;
+                        bt.ok[u] = t < npv;
+                        if (!bt.ok[u]) continue;
+                        int pv = pairs[t];
+                        int j1 = pv & 0xFF, j2 = pv >> 8;
+                        int a1 = vir[j1], a2 = vir[j2];
+                        uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
+                        if (spin == 0) {
+                            uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
+                            if (cl < p.class_lo || cl >= p.class_hi || !cons_ok(p.cons_mod, p.cons_rem, w2)) {
+                                bt.ok[u] = false;
+                                continue;
+                            }
+                            bt.a[u] = w2;
+                            bt.b[u] = B;
+                            bt.zt[u] = zt12 ^ F.zta[a1] ^ F.zta[a2];
+                        } else {
+                            bt.a[u] = A;
+                            bt.b[u] = w2;
+                            bt.zt[u] = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
+                        }
+                        if constexpr (kVal) {
+                            uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
+                            uint32_t par = __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                            double e = eri[(((size_t)a1 * N + r1) * N + a2) * N + r2] -
+                                       eri[(((size_t)a1 * N + r2) * N + a2) * N + r1];
+                            bt.num[u] = flip_sign(c * e, par);
+                            bt.den[u] = base - vec[j1] - vec[j2] - WSx[a1 * N + a2];
+                        }
                     }
-                    double num = 0.0, haa = 0.0;
-                    if constexpr (kVal) {
-                        uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
-                        uint32_t par = __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                        double e = eri[(((size_t)a1 * N + r1) * N + a2) * N + r2] -
-                                   eri[(((size_t)a1 * N + r2) * N + a2) * N + r1];
-                        num = flip_sign(c * e, par);
-                        haa = base + vec[j1] + vec[j2] + WSt[a1 * N + a2];
-                    }
-                    if (spin == 0) sink<MODE>(p, w2, B, zt, num, haa);
-                    else sink<MODE>(p, A, w2, zt, num, haa);
+                    bt.flush(p);
                 }
                 __syncwarp();
             }
@@ -615,6 +747,20 @@ __global__ void diag_kernel(const SysDev sys, const uint64_t *__restrict__ keys,
     out[i] = e;
 }
 
+__global__ void ref_d0_kernel(const double *__restrict__ hii, uint64_t n, double e0, int64_t *__restrict__ d0)
+{
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    d0[i] = __double2ll_rn((e0 - hii[i]) * kDenScale);
+}
+
+cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    ref_d0_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(hii, n, e0, d0);
+    return cudaGetLastError();
+}
+
 // ================================================================ scans
 
 constexpr int kScanThreads = 1024;
@@ -623,12 +769,9 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 size_t scan_tmp_elems(uint64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-__device__ void block_scan_excl_u64(unsigned long long *v, int count_per_thread_dummy,
-                                    unsigned long long local_sum, unsigned long long &prefix,
+__device__ void block_scan_excl_u64(unsigned long long local_sum, unsigned long long &prefix,
                                     unsigned long long *warp_tot, unsigned long long &total)
 {
-    (void)v;
-    (void)count_per_thread_dummy;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     unsigned long long incl = local_sum;
 #pragma unroll
@@ -665,7 +808,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(const uint32_t 
     for (int k = 0; k < kScanItems; ++k)
         if (base + k < n) s += in[base + k];
     unsigned long long pre, tot;
-    block_scan_excl_u64(nullptr, 0, s, pre, wt, tot);
+    block_scan_excl_u64(s, pre, wt, tot);
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
@@ -677,7 +820,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_parts_kernel(unsigned long 
         uint64_t i = b0 + threadIdx.x;
         unsigned long long v = i < nparts ? part[i] : 0ull;
         unsigned long long pre, tot;
-        block_scan_excl_u64(nullptr, 0, v, pre, wt, tot);
+        block_scan_excl_u64(v, pre, wt, tot);
         if (i < nparts) part[i] = carry + pre;
         carry += tot;
     }
@@ -699,7 +842,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
         s += v[k];
     }
     unsigned long long pre, tot;
-    block_scan_excl_u64(nullptr, 0, s, pre, wt, tot);
+    block_scan_excl_u64(s, pre, wt, tot);
     unsigned long long run = part[blockIdx.x] + pre;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -713,9 +856,7 @@ cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, 
                                    unsigned long long *tmp, cudaStream_t s)
 {
     uint64_t nparts = (n + kScanTile - 1) / kScanTile;
-    if (nparts == 0) {
-        return cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
-    }
+    if (nparts == 0) return cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     scan_sums_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, tmp);
     scan_parts_kernel<<<1, kScanThreads, 0, s>>>(tmp, nparts);
     scan_apply_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, tmp, nparts, out);
@@ -795,39 +936,50 @@ cudaError_t launch_sort_slices(const unsigned long long *ref_off, uint64_t *ref_
 
 // ============================================================ tile kernels
 
-struct TileSmem {
-    uint64_t bar;
-    uint32_t misc[4];
-    uint32_t warp_tot[32];
-    double red_d[2][32];
-    unsigned long long red_u[3][32];
-    uint32_t red_c[4][32];
-    uint64_t rk[2 * kRefSliceSmem];
+// Per-thread statistics, all exact integers.
+struct KeyStats {
+    uint64_t e2_lo;
+    int64_t e2_hi;
+    uint64_t dsum, dxor, min_den;
+    uint32_t n_unique, n_in_ref, n_ext, n_pos;
+    uint32_t err;
+    __device__ void clear()
+    {
+        e2_lo = 0;
+        e2_hi = 0;
+        dsum = dxor = 0;
+        min_den = ~0ull;
+        n_unique = n_in_ref = n_ext = n_pos = 0;
+        err = 0;
+    }
 };
 
 // Group `cnt` keys held in shared memory so that equal keys are adjacent:
-// counting sort by a key hash into B >= cnt buckets, then insertion sort of
-// each bucket by the 128-bit key (alpha word most significant).  On return
-// perm[0..cnt) lists record indices in (bucket, key) order.
+// counting sort by a key hash into B buckets (B a power of two, about cnt/2),
+// then insertion sort of each bucket by the 128-bit key (alpha word most
+// significant).  On return perm[0..cnt) lists record indices in (bucket, key)
+// order.  hist must be zero on entry and is left holding bucket offsets.
 template <class KeyAt>
-__device__ void group_keys(int cnt, KeyAt key, uint16_t *perm, uint16_t *bkt, uint16_t *rnk, uint32_t *hist,
+__device__ void group_keys(int cnt, int max_buckets, KeyAt key, uint16_t *perm, uint16_t *rnk, uint32_t *hist,
                            uint32_t *warp_tot)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     int B = 32;
-    while (B < cnt) B <<= 1;
-    for (int i = tid; i < B; i += nt) hist[i] = 0;
-    __syncthreads();
+    while (2 * B < cnt && B < max_buckets) B <<= 1;
     for (int i = tid; i < cnt; i += nt) {
         uint64_t a, b;
         key(i, a, b);
         uint32_t bb = bucket_hash(a, b) & (uint32_t)(B - 1);
-        bkt[i] = (uint16_t)bb;
         rnk[i] = (uint16_t)atomicAdd(&hist[bb], 1u);
     }
     __syncthreads();
     block_scan_excl_u32(hist, B, warp_tot);
-    for (int i = tid; i < cnt; i += nt) perm[hist[bkt[i]] + rnk[i]] = (uint16_t)i;
+    for (int i = tid; i < cnt; i += nt) {
+        uint64_t a, b;
+        key(i, a, b);
+        uint32_t bb = bucket_hash(a, b) & (uint32_t)(B - 1);
+        perm[hist[bb] + rnk[i]] = (uint16_t)i;
+    }
     __syncthreads();
     for (int bb = tid; bb < B; bb += nt) {
         int s = (int)hist[bb];
@@ -848,6 +1000,7 @@ __device__ void group_keys(int cnt, KeyAt key, uint16_t *perm, uint16_t *bkt, ui
         }
     }
     __syncthreads();
+    for (int i = tid; i < B; i += nt) hist[i] = 0;  // ready for the next call
 }
 
 __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long n, uint64_t a, uint64_t b)
@@ -863,23 +1016,10 @@ __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long 
     return false;
 }
 
-struct KeyStats {
-    double e2, min_den;
-    unsigned long long dsum, dxor;
-    uint32_t n_unique, n_in_ref, n_ext, n_pos;
-    __device__ void clear()
-    {
-        e2 = 0.0;
-        min_den = DBL_MAX;
-        dsum = dxor = 0;
-        n_unique = n_in_ref = n_ext = n_pos = 0;
-    }
-};
-
 // One unique key: explicit filter against the reference slice, then the
-// Epstein-Nesbet term num^2 / (E0 - H_aa) (Eq. 3).
+// Epstein-Nesbet term num^2 / (E0 - H_aa) of Eq. 3, added exactly.
 __device__ __forceinline__ void finish_key(const TileParams &p, const uint64_t *rk, unsigned long long nrk,
-                                           uint64_t a, uint64_t b, uint64_t fl, int64_t fh, double haa,
+                                           uint64_t a, uint64_t b, uint64_t fl, int64_t fh, int64_t den,
                                            KeyStats &st)
 {
     st.n_unique++;
@@ -888,12 +1028,13 @@ __device__ __forceinline__ void finish_key(const TileParams &p, const uint64_t *
         return;
     }
     double num = fx_to_double(fl, fh);
-    double den = p.e0 - haa;
-    st.e2 += num * num / den;
+    double d = den_to_double(den);
+    double term = (num * num) * recip(d, den);
+    fx_add_double(st.e2_lo, st.e2_hi, term, st.err);
     st.n_ext++;
-    double ad = fabs(den);
+    uint64_t ad = den < 0 ? (uint64_t)(-den) : (uint64_t)den;
     st.min_den = ad < st.min_den ? ad : st.min_den;
-    st.n_pos += den > 0.0;
+    st.n_pos += den > 0;
     st.dsum += digest1(a, b);
     st.dxor ^= digest2(a, b);
     if (p.dump_keys) {
@@ -902,159 +1043,196 @@ __device__ __forceinline__ void finish_key(const TileParams &p, const uint64_t *
             p.dump_keys[2 * slot] = a;
             p.dump_keys[2 * slot + 1] = b;
             p.dump_num[slot] = num;
-            p.dump_haa[slot] = haa;
+            p.dump_haa[slot] = p.e0 - d;
         }
     }
 }
 
-// Fixed-shape block reduction of the per-thread statistics; thread 0 returns them.
-__device__ KeyStats block_reduce_stats(KeyStats st, TileSmem &S)
+// Sum the per-thread statistics of the CTA and add them to the run total.
+__device__ void flush_stats(const TileParams &p, KeyStats st, unsigned long long (*red)[32])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
-        st.e2 += __shfl_down_sync(0xffffffffu, st.e2, off);
-        st.min_den = fmin(st.min_den, __shfl_down_sync(0xffffffffu, st.min_den, off));
+        uint64_t olo = __shfl_down_sync(0xffffffffu, st.e2_lo, off);
+        int64_t ohi = __shfl_down_sync(0xffffffffu, st.e2_hi, off);
+        fx_add_fx(st.e2_lo, st.e2_hi, olo, ohi);
         st.dsum += __shfl_down_sync(0xffffffffu, st.dsum, off);
         st.dxor ^= __shfl_down_sync(0xffffffffu, st.dxor, off);
+        uint64_t om = __shfl_down_sync(0xffffffffu, st.min_den, off);
+        st.min_den = om < st.min_den ? om : st.min_den;
         st.n_unique += __shfl_down_sync(0xffffffffu, st.n_unique, off);
         st.n_in_ref += __shfl_down_sync(0xffffffffu, st.n_in_ref, off);
         st.n_ext += __shfl_down_sync(0xffffffffu, st.n_ext, off);
         st.n_pos += __shfl_down_sync(0xffffffffu, st.n_pos, off);
+        st.err |= __shfl_down_sync(0xffffffffu, st.err, off);
     }
     if (lane == 0) {
-        S.red_d[0][warp] = st.e2;
-        S.red_d[1][warp] = st.min_den;
-        S.red_u[0][warp] = st.dsum;
-        S.red_u[1][warp] = st.dxor;
-        S.red_c[0][warp] = st.n_unique;
-        S.red_c[1][warp] = st.n_in_ref;
-        S.red_c[2][warp] = st.n_ext;
-        S.red_c[3][warp] = st.n_pos;
+        red[0][warp] = st.e2_lo;
+        red[1][warp] = (unsigned long long)st.e2_hi;
+        red[2][warp] = st.dsum;
+        red[3][warp] = st.dxor;
+        red[4][warp] = st.min_den;
+        red[5][warp] = st.n_unique;
+        red[6][warp] = st.n_in_ref;
+        red[7][warp] = st.n_ext;
+        red[8][warp] = st.n_pos;
+        red[9][warp] = st.err;
     }
     __syncthreads();
-    KeyStats r;
-    r.clear();
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        uint64_t lo = 0, dsum = 0, dxor = 0, mind = ~0ull, nu = 0, nr = 0, ne = 0, np = 0, er = 0;
+        int64_t hi = 0;
         for (int w = 0; w < nw; ++w) {
-            r.e2 += S.red_d[0][w];
-            r.min_den = fmin(r.min_den, S.red_d[1][w]);
-            r.dsum += S.red_u[0][w];
-            r.dxor ^= S.red_u[1][w];
-            r.n_unique += S.red_c[0][w];
-            r.n_in_ref += S.red_c[1][w];
-            r.n_ext += S.red_c[2][w];
-            r.n_pos += S.red_c[3][w];
+            fx_add_fx(lo, hi, red[0][w], (int64_t)red[1][w]);
+            dsum += red[2][w];
+            dxor ^= red[3][w];
+            mind = red[4][w] < mind ? red[4][w] : mind;
+            nu += red[5][w];
+            nr += red[6][w];
+            ne += red[7][w];
+            np += red[8][w];
+            er |= red[9][w];
         }
-    __syncthreads();
-    return r;
-}
-
-__device__ void write_part(const TileParams &p, uint64_t t, const KeyStats &r)
-{
-    TilePart tp;
-    tp.e2 = r.e2;
-    tp.min_den = r.min_den;
-    tp.dsum = r.dsum;
-    tp.dxor = r.dxor;
-    tp.n_unique = r.n_unique;
-    tp.n_in_ref = r.n_in_ref;
-    tp.n_ext = r.n_ext;
-    tp.n_pos = r.n_pos;
-    p.parts[t] = tp;
+        RunAcc *acc = p.acc;
+        unsigned long long old = atomicAdd(&acc->e2_lo, (unsigned long long)lo);
+        unsigned long long carry = (old + lo) < old ? 1ull : 0ull;
+        atomicAdd((unsigned long long *)&acc->e2_hi, (unsigned long long)hi + carry);
+        atomicAdd(&acc->dsum, dsum);
+        atomicXor(&acc->dxor, dxor);
+        atomicMin(&acc->min_den, mind);
+        atomicAdd(&acc->n_unique, nu);
+        atomicAdd(&acc->n_in_ref, nr);
+        atomicAdd(&acc->n_ext, ne);
+        atomicAdd(&acc->n_pos, np);
+        if (er) atomicOr(p.err, (unsigned)er);
+    }
 }
 
 // Load the tile's reference slice; returns a pointer usable for binary search.
-__device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, TileSmem &S, unsigned long long &n)
+__device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint64_t *rk_smem, unsigned long long &n)
 {
     unsigned long long s = p.ref_off[t], e = p.ref_off[t + 1];
     n = e - s;
     if (n <= (unsigned long long)kRefSliceSmem) {
-        for (unsigned long long i = threadIdx.x; i < 2 * n; i += blockDim.x) S.rk[i] = p.ref_keys[2 * s + i];
-        return S.rk;
+        for (unsigned long long i = threadIdx.x; i < 2 * n; i += blockDim.x) rk_smem[i] = p.ref_keys[2 * s + i];
+        return rk_smem;
     }
     return p.ref_keys + 2 * s;
 }
 
-// Shared memory of the main tile kernel.
+// Reduce the grouped records: every thread walks a contiguous range of the
+// sorted positions and finishes the keys whose first record lies in it.
+template <class Rec, bool kFixed>
+__device__ __forceinline__ void reduce_groups(const TileParams &p, const Rec *recs, const uint16_t *perm, int cnt,
+                                              const uint64_t *rk, unsigned long long nrk, KeyStats &st)
+{
+    const int nt = blockDim.x;
+    const int chunk = (cnt + nt - 1) / nt;
+    const int s = threadIdx.x * chunk, e = min(cnt, s + chunk);
+    for (int j = s; j < e; ++j) {
+        const Rec &r0 = recs[perm[j]];
+        if (j > 0) {
+            const Rec &rp = recs[perm[j - 1]];
+            if (rp.a == r0.a && rp.b == r0.b) continue;
+        }
+        uint64_t fl = 0;
+        int64_t fh = 0;
+        int64_t den = r0.den;
+        for (int k = j; k < cnt; ++k) {
+            const Rec &r2 = recs[perm[k]];
+            if (k > j && (r2.a != r0.a || r2.b != r0.b)) break;
+            if constexpr (kFixed) fx_add_fx(fl, fh, r2.fx_lo, r2.fx_hi);
+            else fx_add_double(fl, fh, r2.num, st.err);
+            den = r2.den < den ? r2.den : den;
+        }
+        finish_key(p, rk, nrk, r0.a, r0.b, fl, fh, den, st);
+    }
+}
+
+// Shared memory of the main tile kernel: two record buffers (the next tile is
+// fetched by TMA while the current one is grouped).
 struct MainSmem {
-    Rec32 recs[kTileCap];
-    uint16_t perm[kTileCap], bkt[kTileCap], rnk[kTileCap];
-    uint32_t hist[kTileCap];
-    TileSmem S;
+    Rec32 recs[2][kTileCap];
+    uint16_t perm[kTileCap], rnk[kTileCap];
+    uint32_t hist[kTileBuckets];
+    uint64_t rk[2 * kRefSliceSmem];
+    uint64_t bar[2];
+    uint32_t warp_tot[32];
+    unsigned long long red[10][32];
 };
 
 size_t tile_smem_bytes() { return sizeof(MainSmem); }
 
+__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, uint64_t t, int buf)
+{
+    unsigned long long off = p.tile_off[t], cnt = p.tile_off[t + 1] - off;
+    if (cnt == 0 || cnt > (unsigned long long)kTileCap) return;
+    fence_proxy_async_smem();
+    bulk_load(M.recs[buf], p.recs + off, (uint32_t)(cnt * sizeof(Rec32)), &M.bar[buf]);
+}
+
+// Persistent: CTA g handles tiles g, g + G, g + 2G, ...
 __global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
-    const uint64_t t = blockIdx.x;
-    const unsigned long long off = p.tile_off[t];
-    const int cnt64 = 0;
-    (void)cnt64;
-    const unsigned long long cntl = p.tile_off[t + 1] - off;
-    if (cntl > (unsigned long long)kTileCap) {
-        if (threadIdx.x == 0) {
-            unsigned idx = atomicAdd(p.big_count, 1u);
-            p.big_list[idx] = (uint32_t)t;
-        }
-        return;
-    }
-    const int cnt = (int)cntl;
-    if (threadIdx.x == 0 && cnt > 0) {
-        mbar_init(&M.S.bar, 1);
-        bulk_load(M.recs, p.recs + off, (uint32_t)(cnt * sizeof(Rec32)), &M.S.bar);
-    }
-    unsigned long long nrk;
-    const uint64_t *rk = load_ref_slice(p, t, M.S, nrk);
-    __syncthreads();
+    const uint64_t G = gridDim.x;
     KeyStats st;
     st.clear();
-    if (cnt > 0) {
-        mbar_wait_bounded(&M.S.bar, 0, p.err);
-        auto key = [&](int i, uint64_t &a, uint64_t &b) {
-            a = M.recs[i].a;
-            b = M.recs[i].b;
-        };
-        group_keys(cnt, key, M.perm, M.bkt, M.rnk, M.hist, M.S.warp_tot);
-        uint32_t err = 0;
-        const int nt = blockDim.x;
-        const int chunk = (cnt + nt - 1) / nt;
-        const int s = threadIdx.x * chunk, e = min(cnt, s + chunk);
-        for (int j = s; j < e; ++j) {
-            const Rec32 &r0 = M.recs[M.perm[j]];
-            if (j > 0) {
-                const Rec32 &rp = M.recs[M.perm[j - 1]];
-                if (rp.a == r0.a && rp.b == r0.b) continue;
-            }
-            uint64_t fl = 0;
-            int64_t fh = 0;
-            double haa = r0.haa;
-            fx_add_double(fl, fh, r0.num, err);
-            for (int k = j + 1; k < cnt; ++k) {
-                const Rec32 &rk2 = M.recs[M.perm[k]];
-                if (rk2.a != r0.a || rk2.b != r0.b) break;
-                fx_add_double(fl, fh, rk2.num, err);
-                haa = fmin(haa, rk2.haa);
-            }
-            finish_key(p, rk, nrk, r0.a, r0.b, fl, fh, haa, st);
-        }
-        if (err) atomicOr(p.err, err);
-        if (threadIdx.x == 0) mbar_inval(&M.S.bar);
+    for (int i = threadIdx.x; i < kTileBuckets; i += blockDim.x) M.hist[i] = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&M.bar[0], 1);
+        mbar_init(&M.bar[1], 1);
+        if (blockIdx.x < p.n_tiles) issue_tile(p, M, blockIdx.x, 0);
     }
-    KeyStats r = block_reduce_stats(st, M.S);
-    if (threadIdx.x == 0) write_part(p, t, r);
+    __syncthreads();
+    uint32_t phase[2] = {0u, 0u};
+    int k = 0;
+    for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G, ++k) {
+        const int buf = k & 1;
+        const unsigned long long off = p.tile_off[t];
+        const unsigned long long cntl = p.tile_off[t + 1] - off;
+        if (threadIdx.x == 0 && t + G < p.n_tiles) issue_tile(p, M, t + G, buf ^ 1);
+        if (cntl == 0) continue;
+        if (cntl > (unsigned long long)kTileCap) {
+            if (threadIdx.x == 0) {
+                unsigned idx = atomicAdd(&p.acc->n_big, 1u);
+                p.big_list[idx] = (uint32_t)t;
+                atomicMax(&p.acc->big_max, cntl);
+            }
+            continue;
+        }
+        const int cnt = (int)cntl;
+        unsigned long long nrk;
+        const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
+        mbar_wait_bounded(&M.bar[buf], phase[buf], p.err);
+        phase[buf] ^= 1u;
+        const Rec32 *recs = M.recs[buf];
+        auto key = [&](int i, uint64_t &a, uint64_t &b) {
+            a = recs[i].a;
+            b = recs[i].b;
+        };
+        group_keys(cnt, kTileBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+        reduce_groups<Rec32, false>(p, recs, M.perm, cnt, rk, nrk, st);
+        __syncthreads();  // buffer, perm and slice free for the next tile
+    }
+    flush_stats(p, st, M.red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_inval(&M.bar[0]);
+        mbar_inval(&M.bar[1]);
+    }
 }
 
-cudaError_t launch_tiles(const TileParams &p, cudaStream_t s)
+cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 {
     if (p.n_tiles == 0) return cudaSuccess;
     size_t sm = tile_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    tile_kernel<<<(unsigned)p.n_tiles, kTileThreads, sm, s>>>(p);
+    unsigned g = (unsigned)(p.n_tiles < (uint64_t)n_ctas ? p.n_tiles : (uint64_t)n_ctas);
+    tile_kernel<<<g, kTileThreads, sm, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1062,24 +1240,60 @@ cudaError_t launch_tiles(const TileParams &p, cudaStream_t s)
 
 // Chunked grouping for tiles above shared-memory capacity: every chunk is
 // grouped in shared memory and reduced to (key, exact fixed-point numerator,
-// min H_aa) records; the reduced list is regrouped until it fits, then
-// finished like a normal tile.  Fixed-point sums make the result independent
-// of chunking.
+// min denominator) records; the reduced list is regrouped until it fits, then
+// finished like a normal tile.  Exact sums make the result independent of
+// the chunking.
 struct BigSmem {
     union {
         Rec32 r32[kTileCap];
         Rec48 r48[kBigCap];
     } u;
-    uint16_t perm[kBigCap > kTileCap ? kBigCap : kTileCap];
-    uint16_t bkt[kBigCap > kTileCap ? kBigCap : kTileCap];
-    uint16_t rnk[kBigCap > kTileCap ? kBigCap : kTileCap];
-    uint32_t hist[kBigCap > kTileCap ? kBigCap : kTileCap];
+    uint16_t perm[kBigCap], rnk[kBigCap];
+    uint32_t hist[kBigBuckets];
+    uint64_t rk[2 * kRefSliceSmem];
+    uint64_t bar;
     unsigned int out_count;
-    TileSmem S;
+    uint32_t warp_tot[32];
+    unsigned long long red[10][32];
 };
 
 size_t big_smem_bytes() { return sizeof(BigSmem); }
-int big_grid() { return 64; }
+
+// Reduce grouped records of one chunk into Rec48 entries appended to dst.
+template <class Rec, bool kFixed>
+__device__ void chunk_to_partials(const Rec *recs, const uint16_t *perm, int m, Rec48 *dst, unsigned int *count,
+                                  uint32_t &err)
+{
+    const int nt = blockDim.x;
+    const int chunk = (m + nt - 1) / nt;
+    const int s = threadIdx.x * chunk, e = min(m, s + chunk);
+    for (int j = s; j < e; ++j) {
+        const Rec &r0 = recs[perm[j]];
+        if (j > 0) {
+            const Rec &rp = recs[perm[j - 1]];
+            if (rp.a == r0.a && rp.b == r0.b) continue;
+        }
+        uint64_t fl = 0;
+        int64_t fh = 0;
+        int64_t den = r0.den;
+        for (int k = j; k < m; ++k) {
+            const Rec &r2 = recs[perm[k]];
+            if (k > j && (r2.a != r0.a || r2.b != r0.b)) break;
+            if constexpr (kFixed) fx_add_fx(fl, fh, r2.fx_lo, r2.fx_hi);
+            else fx_add_double(fl, fh, r2.num, err);
+            den = r2.den < den ? r2.den : den;
+        }
+        unsigned int slot = atomicAdd(count, 1u);
+        Rec48 o;
+        o.a = r0.a;
+        o.b = r0.b;
+        o.fx_lo = fl;
+        o.fx_hi = fh;
+        o.den = den;
+        o.pad = 0;
+        dst[slot] = o;
+    }
+}
 
 __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TileParams p)
 {
@@ -1087,16 +1301,18 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
     BigSmem &M = *reinterpret_cast<BigSmem *>(smem_raw);
     Rec48 *bufA = p.scratch + (size_t)blockIdx.x * 2 * p.scratch_cap;
     Rec48 *bufB = bufA + p.scratch_cap;
-    const unsigned int nbig = *p.big_count;
+    const unsigned int nbig = p.acc->n_big;
+    KeyStats st;
+    st.clear();
     uint32_t phase = 0;
-    if (threadIdx.x == 0) mbar_init(&M.S.bar, 1);
+    for (int i = threadIdx.x; i < kBigBuckets; i += blockDim.x) M.hist[i] = 0;
+    if (threadIdx.x == 0) mbar_init(&M.bar, 1);
     __syncthreads();
     const int nt = blockDim.x;
     for (unsigned int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
         const uint64_t t = p.big_list[idx];
         const unsigned long long off = p.tile_off[t];
         const unsigned long long cnt = p.tile_off[t + 1] - off;
-        uint32_t err = 0;
         bool bad = false;
         if (cnt > p.scratch_cap) {
             if (threadIdx.x == 0) atomicOr(p.err, kErrScratch);
@@ -1108,45 +1324,19 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
             const int m = (int)min((unsigned long long)kTileCap, cnt - cs);
             if (threadIdx.x == 0) {
                 fence_proxy_async_smem();
-                bulk_load(M.u.r32, p.recs + off + cs, (uint32_t)(m * sizeof(Rec32)), &M.S.bar);
+                bulk_load(M.u.r32, p.recs + off + cs, (uint32_t)(m * sizeof(Rec32)), &M.bar);
                 M.out_count = 0;
             }
-            mbar_wait_bounded(&M.S.bar, phase, p.err);
+            mbar_wait_bounded(&M.bar, phase, p.err);
             phase ^= 1;
             __syncthreads();
+            const Rec32 *recs = M.u.r32;
             auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                a = M.u.r32[i].a;
-                b = M.u.r32[i].b;
+                a = recs[i].a;
+                b = recs[i].b;
             };
-            group_keys(m, key, M.perm, M.bkt, M.rnk, M.hist, M.S.warp_tot);
-            const int chunk = (m + nt - 1) / nt;
-            const int s = threadIdx.x * chunk, e = min(m, s + chunk);
-            for (int j = s; j < e; ++j) {
-                const Rec32 &r0 = M.u.r32[M.perm[j]];
-                if (j > 0) {
-                    const Rec32 &rp = M.u.r32[M.perm[j - 1]];
-                    if (rp.a == r0.a && rp.b == r0.b) continue;
-                }
-                uint64_t fl = 0;
-                int64_t fh = 0;
-                double haa = r0.haa;
-                fx_add_double(fl, fh, r0.num, err);
-                for (int k = j + 1; k < m; ++k) {
-                    const Rec32 &r2 = M.u.r32[M.perm[k]];
-                    if (r2.a != r0.a || r2.b != r0.b) break;
-                    fx_add_double(fl, fh, r2.num, err);
-                    haa = fmin(haa, r2.haa);
-                }
-                unsigned int slot = atomicAdd(&M.out_count, 1u);
-                Rec48 o;
-                o.a = r0.a;
-                o.b = r0.b;
-                o.fx_lo = fl;
-                o.fx_hi = fh;
-                o.haa = haa;
-                o.pad = 0;
-                bufA[u + slot] = o;
-            }
+            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+            chunk_to_partials<Rec32, false>(recs, M.perm, m, bufA + u, &M.out_count, st.err);
             __syncthreads();
             u += M.out_count;
             __syncthreads();
@@ -1157,43 +1347,20 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
             unsigned long long u2 = 0;
             for (unsigned long long cs = 0; cs < u; cs += kBigCap) {
                 const int m = (int)min((unsigned long long)kBigCap, u - cs);
-                __syncthreads();
                 if (threadIdx.x == 0) M.out_count = 0;
                 for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[cs + i];
                 __syncthreads();
+                const Rec48 *recs = M.u.r48;
                 auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                    a = M.u.r48[i].a;
-                    b = M.u.r48[i].b;
+                    a = recs[i].a;
+                    b = recs[i].b;
                 };
-                group_keys(m, key, M.perm, M.bkt, M.rnk, M.hist, M.S.warp_tot);
-                const int chunk = (m + nt - 1) / nt;
-                const int s = threadIdx.x * chunk, e = min(m, s + chunk);
-                for (int j = s; j < e; ++j) {
-                    const Rec48 &r0 = M.u.r48[M.perm[j]];
-                    if (j > 0) {
-                        const Rec48 &rp = M.u.r48[M.perm[j - 1]];
-                        if (rp.a == r0.a && rp.b == r0.b) continue;
-                    }
-                    uint64_t fl = r0.fx_lo;
-                    int64_t fh = r0.fx_hi;
-                    double haa = r0.haa;
-                    for (int k = j + 1; k < m; ++k) {
-                        const Rec48 &r2 = M.u.r48[M.perm[k]];
-                        if (r2.a != r0.a || r2.b != r0.b) break;
-                        fx_add_fx(fl, fh, r2.fx_lo, r2.fx_hi);
-                        haa = fmin(haa, r2.haa);
-                    }
-                    unsigned int slot = atomicAdd(&M.out_count, 1u);
-                    Rec48 o = r0;
-                    o.fx_lo = fl;
-                    o.fx_hi = fh;
-                    o.haa = haa;
-                    dst[u2 + slot] = o;
-                }
+                group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+                chunk_to_partials<Rec48, true>(recs, M.perm, m, dst + u2, &M.out_count, st.err);
                 __syncthreads();
                 u2 += M.out_count;
+                __syncthreads();
             }
-            __syncthreads();
             if (u2 >= u) {
                 if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
                 bad = true;
@@ -1206,50 +1373,29 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
         }
         // final grouping and the energy
         unsigned long long nrk;
-        __syncthreads();
-        const uint64_t *rk = load_ref_slice(p, t, M.S, nrk);
-        KeyStats st;
-        st.clear();
+        const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
         if (!bad) {
             const int m = (int)u;
             for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
             __syncthreads();
+            const Rec48 *recs = M.u.r48;
             auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                a = M.u.r48[i].a;
-                b = M.u.r48[i].b;
+                a = recs[i].a;
+                b = recs[i].b;
             };
-            group_keys(m, key, M.perm, M.bkt, M.rnk, M.hist, M.S.warp_tot);
-            const int chunk = (m + nt - 1) / nt;
-            const int s = threadIdx.x * chunk, e = min(m, s + chunk);
-            for (int j = s; j < e; ++j) {
-                const Rec48 &r0 = M.u.r48[M.perm[j]];
-                if (j > 0) {
-                    const Rec48 &rp = M.u.r48[M.perm[j - 1]];
-                    if (rp.a == r0.a && rp.b == r0.b) continue;
-                }
-                uint64_t fl = r0.fx_lo;
-                int64_t fh = r0.fx_hi;
-                double haa = r0.haa;
-                for (int k = j + 1; k < m; ++k) {
-                    const Rec48 &r2 = M.u.r48[M.perm[k]];
-                    if (r2.a != r0.a || r2.b != r0.b) break;
-                    fx_add_fx(fl, fh, r2.fx_lo, r2.fx_hi);
-                    haa = fmin(haa, r2.haa);
-                }
-                finish_key(p, rk, nrk, r0.a, r0.b, fl, fh, haa, st);
-            }
+            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+            reduce_groups<Rec48, true>(p, recs, M.perm, m, rk, nrk, st);
         }
-        if (err) atomicOr(p.err, err);
-        KeyStats r = block_reduce_stats(st, M.S);
-        if (threadIdx.x == 0) write_part(p, t, r);
         __syncthreads();
     }
+    flush_stats(p, st, M.red);
     __syncthreads();
-    if (threadIdx.x == 0) mbar_inval(&M.S.bar);
+    if (threadIdx.x == 0) mbar_inval(&M.bar);
 }
 
 cudaError_t launch_big_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 {
+    if (n_ctas <= 0) return cudaSuccess;
     size_t sm = big_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(big_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -1257,178 +1403,55 @@ cudaError_t launch_big_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// ========================================================= pass reduction
+// ========================================================= pass bookkeeping
 
-constexpr int kRedCtas = 256;
-constexpr int kRedThreads = 256;
-
-struct RedSmem {
-    double d[2][kRedThreads / 32];
-    unsigned long long u[2][kRedThreads / 32];
-    unsigned long long c[4][kRedThreads / 32];
-};
-
-// Neumaier step.
-__device__ __forceinline__ void nsum(double &s, double &c, double x)
+__global__ void pass_finish_kernel(const unsigned long long *__restrict__ tile_off, uint64_t n_tiles,
+                                   unsigned long long expected, RunAcc *acc, uint32_t *err)
 {
-    double t = s + x;
-    if (fabs(s) >= fabs(x)) c += (s - t) + x;
-    else c += (x - t) + s;
-    s = t;
-}
-
-__device__ void reduce_parts_block(const TilePart *parts, uint64_t begin, uint64_t end, TilePart &out, RedSmem &S)
-{
-    double s = 0.0, cc = 0.0, mind = DBL_MAX;
-    unsigned long long dsum = 0, dxor = 0, nu = 0, nr = 0, ne = 0, np = 0;
-    for (uint64_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        const TilePart &tp = parts[i];
-        nsum(s, cc, tp.e2);
-        mind = fmin(mind, tp.min_den);
-        dsum += tp.dsum;
-        dxor ^= tp.dxor;
-        nu += tp.n_unique;
-        nr += tp.n_in_ref;
-        ne += tp.n_ext;
-        np += tp.n_pos;
-    }
-    double v = s + cc;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        v += __shfl_down_sync(0xffffffffu, v, off);
-        mind = fmin(mind, __shfl_down_sync(0xffffffffu, mind, off));
-        dsum += __shfl_down_sync(0xffffffffu, dsum, off);
-        dxor ^= __shfl_down_sync(0xffffffffu, dxor, off);
-        nu += __shfl_down_sync(0xffffffffu, nu, off);
-        nr += __shfl_down_sync(0xffffffffu, nr, off);
-        ne += __shfl_down_sync(0xffffffffu, ne, off);
-        np += __shfl_down_sync(0xffffffffu, np, off);
-    }
-    if (lane == 0) {
-        S.d[0][warp] = v;
-        S.d[1][warp] = mind;
-        S.u[0][warp] = dsum;
-        S.u[1][warp] = dxor;
-        S.c[0][warp] = nu;
-        S.c[1][warp] = nr;
-        S.c[2][warp] = ne;
-        S.c[3][warp] = np;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, ac = 0.0, m = DBL_MAX;
-        unsigned long long x0 = 0, x1 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        for (int w = 0; w < nw; ++w) {
-            nsum(a, ac, S.d[0][w]);
-            m = fmin(m, S.d[1][w]);
-            x0 += S.u[0][w];
-            x1 ^= S.u[1][w];
-            c0 += S.c[0][w];
-            c1 += S.c[1][w];
-            c2 += S.c[2][w];
-            c3 += S.c[3][w];
-        }
-        out.e2 = a + ac;
-        out.min_den = m;
-        out.dsum = x0;
-        out.dxor = x1;
-        // counts of one chunk can exceed 32 bits: carried in the u64 fields below
-        out.n_unique = (uint32_t)c0;
-        out.n_in_ref = (uint32_t)c1;
-        out.n_ext = (uint32_t)c2;
-        out.n_pos = (uint32_t)c3;
-        S.c[0][0] = c0;
-        S.c[1][0] = c1;
-        S.c[2][0] = c2;
-        S.c[3][0] = c3;
-    }
-    __syncthreads();
-}
-
-struct ChunkPart {
-    double e2, min_den;
-    unsigned long long dsum, dxor, nu, nr, ne, np;
-};
-
-__global__ void __launch_bounds__(kRedThreads) pass_chunk_kernel(const TilePart *__restrict__ parts, uint64_t n,
-                                                                 ChunkPart *__restrict__ out)
-{
-    __shared__ RedSmem S;
-    uint64_t per = (n + gridDim.x - 1) / gridDim.x;
-    uint64_t b = blockIdx.x * per, e = b + per < n ? b + per : n;
-    if (b > n) b = n;
-    TilePart tp;
-    reduce_parts_block(parts, b, e, tp, S);
-    if (threadIdx.x == 0) {
-        ChunkPart c;
-        c.e2 = tp.e2;
-        c.min_den = tp.min_den;
-        c.dsum = tp.dsum;
-        c.dxor = tp.dxor;
-        c.nu = S.c[0][0];
-        c.nr = S.c[1][0];
-        c.ne = S.c[2][0];
-        c.np = S.c[3][0];
-        out[blockIdx.x] = c;
-    }
-}
-
-__global__ void pass_final_kernel(const ChunkPart *__restrict__ chunks, int nchunks,
-                                  const unsigned long long *__restrict__ tile_off, uint64_t n_tiles,
-                                  unsigned long long expected, RunAcc *acc)
-{
-    if (threadIdx.x != 0) return;
-    double s = 0.0, c = 0.0, m = DBL_MAX;
-    unsigned long long d0 = 0, d1 = 0, nu = 0, nr = 0, ne = 0, np = 0;
-    for (int i = 0; i < nchunks; ++i) {
-        nsum(s, c, chunks[i].e2);
-        m = fmin(m, chunks[i].min_den);
-        d0 += chunks[i].dsum;
-        d1 ^= chunks[i].dxor;
-        nu += chunks[i].nu;
-        nr += chunks[i].nr;
-        ne += chunks[i].ne;
-        np += chunks[i].np;
-    }
-    nsum(acc->e2_s, acc->e2_c, s + c);
-    acc->min_den = fmin(acc->min_den, m);
-    acc->dsum += d0;
-    acc->dxor ^= d1;
-    acc->n_unique += nu;
-    acc->n_in_ref += nr;
-    acc->n_ext += ne;
-    acc->n_pos += np;
     unsigned long long got = tile_off[n_tiles];
     acc->n_terms += got;
-    if (got != expected) acc->err |= kErrCount;
+    if (got != expected) atomicOr(err, kErrCount);
+    acc->n_big = 0;
+    acc->big_max = 0;
 }
 
-cudaError_t launch_pass_reduce(const TilePart *parts, uint64_t n_tiles, TilePart *chunk_tmp,
-                               const unsigned long long *tile_off, unsigned long long expected_terms,
-                               RunAcc *acc, cudaStream_t s)
+cudaError_t launch_pass_finish(const unsigned long long *tile_off, uint64_t n_tiles,
+                               unsigned long long expected_terms, RunAcc *acc, uint32_t *err, cudaStream_t s)
 {
-    ChunkPart *ch = reinterpret_cast<ChunkPart *>(chunk_tmp);
-    pass_chunk_kernel<<<kRedCtas, kRedThreads, 0, s>>>(parts, n_tiles, ch);
-    pass_final_kernel<<<1, 32, 0, s>>>(ch, kRedCtas, tile_off, n_tiles, expected_terms, acc);
+    pass_finish_kernel<<<1, 1, 0, s>>>(tile_off, n_tiles, expected_terms, acc, err);
     return cudaGetLastError();
 }
 
 __global__ void acc_init_kernel(RunAcc *acc)
 {
     RunAcc a;
-    a.e2_s = 0.0;
-    a.e2_c = 0.0;
-    a.min_den = DBL_MAX;
-    a.n_terms = a.n_unique = a.n_in_ref = a.n_ext = a.dsum = a.dxor = a.n_pos = 0;
+    a.e2_lo = 0;
+    a.e2_hi = 0;
+    a.n_terms = a.n_unique = a.n_in_ref = a.n_ext = a.n_pos = a.dsum = a.dxor = 0;
+    a.min_den = ~0ull;
+    a.e2 = 0.0;
+    a.min_abs_den = 0.0;
     a.err = 0;
     a.n_big = 0;
+    a.big_max = 0;
     *acc = a;
 }
 
 cudaError_t launch_acc_init(RunAcc *acc, cudaStream_t s)
 {
     acc_init_kernel<<<1, 1, 0, s>>>(acc);
+    return cudaGetLastError();
+}
+
+__global__ void acc_finalize_kernel(RunAcc *acc)
+{
+    acc->e2 = fx_to_double(acc->e2_lo, acc->e2_hi);
+    acc->min_abs_den = acc->min_den == ~0ull ? INFINITY : u128_to_double(acc->min_den, 0, kDenShift, false);
+}
+
+cudaError_t launch_acc_finalize(RunAcc *acc, cudaStream_t s)
+{
+    acc_finalize_kernel<<<1, 1, 0, s>>>(acc);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,67 @@
+"""The 20-electron / 40-orbital / 100,000-determinant workload at full size,
+in the launch configuration the benchmark times (default options).
+
+The oracle cannot enumerate all 1.3e10 terms in test time, so parity at full
+size is checked (1) on a sampled constraint class (Algorithm 2: the excited
+determinants with alpha % m == r), which the oracle computes exactly, and
+(2) through properties that hold at any size: the closed-form term count,
+the set bookkeeping, run-to-run bit identity and independence of the pass
+plan.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_02049_gb300 import inputs, pt2
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    from paper_1808_02049_gb300 import build
+
+    build.build_library()
+    s, r = inputs.make_config(1)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    c = pt2.Context(0)
+    sid = c.load_system(s.h, s.eri)
+    rid = c.load_reference(sid, r.keys, r.coef, e0)
+    yield dict(c=c, s=s, r=r, e0=e0, rid=rid)
+    c.close()
+
+
+def test_full_size_properties(cfg1):
+    c, rid = cfg1["c"], cfg1["rid"]
+    a = c.run(rid)
+    n, v = 10, 30
+    T = 2 * n * v + 2 * math.comb(n, 2) * math.comb(v, 2) + (n * v) ** 2
+    assert a["n_terms"] == T * 100_000 == 12_975_000_000
+    assert a["n_unique"] == a["n_in_ref"] + a["n_external"]
+    assert a["n_in_ref"] <= 100_000
+    assert a["n_passes"] >= 1
+    assert math.isfinite(a["e2"]) and a["e2"] < 0
+    b = c.run(rid)
+    assert b["e2"] == a["e2"]
+    assert (b["digest_sum"], b["digest_xor"], b["n_external"]) == (a["digest_sum"], a["digest_xor"], a["n_external"])
+    # a different pass plan and tiling give the identical energy and set
+    d = c.run(rid, pass_budget_bytes=60 << 30, tile_target=700)
+    assert d["n_passes"] > a["n_passes"]
+    assert d["e2"] == a["e2"]
+    assert (d["digest_sum"], d["digest_xor"], d["n_external"]) == (a["digest_sum"], a["digest_xor"], a["n_external"])
+
+
+@pytest.mark.parametrize("cls", [(49999, 7), (50021, 123)])
+def test_sampled_constraint_class_matches_oracle(cfg1, cls):
+    c, s, r, e0, rid = cfg1["c"], cfg1["s"], cfg1["r"], cfg1["e0"], cfg1["rid"]
+    got = c.run(rid, constraint=cls)
+    ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=cls)
+    assert got["n_terms"] == ref["n_terms"]
+    assert got["n_external"] == ref["n_external"]
+    assert got["n_in_ref"] == ref["n_in_ref"]
+    assert (got["digest_sum"], got["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
+    assert got["n_pos_denom"] == ref["n_pos_denom"]
+    assert abs(got["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
