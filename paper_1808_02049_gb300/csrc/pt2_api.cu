@@ -424,12 +424,8 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
         c->launches++;
         if (prof) CK(cudaEventRecord(E[5], st), "event");
         // oversize tiles: size the scratch from what the tile kernel found
-        struct {
-            unsigned int n_big;
-            unsigned int pad;
-            unsigned long long big_max;
-        } bi;
-        CK(cudaMemcpyAsync(&bi, &acc->n_big, sizeof bi, cudaMemcpyDeviceToHost, st), "copy");
+        RunAcc bi;
+        CK(cudaMemcpyAsync(&bi, acc, sizeof bi, cudaMemcpyDeviceToHost, st), "copy");
         CK(cudaStreamSynchronize(st), "sync");
         n_big_total += bi.n_big;
         if (bi.n_big) {
