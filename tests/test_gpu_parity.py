@@ -209,7 +209,7 @@ def test_tiny_systems_match_brute_force(ctx, n_orb, na, nb, n_ref, seed):
     assert np.array_equal(k, bf["keys"])
     np.testing.assert_allclose(num, bf["num"], rtol=0, atol=1e-12)
     np.testing.assert_allclose(haa, bf["haa"], rtol=0, atol=1e-12)
-    assert abs(got["e2"] - bf["e2"]) <= 1e-12 * max(1.0, abs(bf["e2"]))
+    assert e2_close(got["e2"], bf["e2"])
 
 
 def test_edge_cases(ctx):
