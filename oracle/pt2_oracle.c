@@ -357,8 +357,11 @@ static void nsum_add(nsum_t *t, double x)
     t->s = s;
 }
 
-uint64_t oracle_digest_mix1(uint64_t a, uint64_t b) { return fmix(fmix(a) ^ b); }
-uint64_t oracle_digest_mix2(uint64_t a, uint64_t b) { return fmix(a ^ fmix(b ^ 0x9e3779b97f4a7c15ull)); }
+/* Set digest of the external set (a verification aid, not part of the
+ * method): mix1 summed mod 2^64 and mix2 xor-ed over the keys.  Multiplying
+ * by odd 64-bit constants and finishing with the SplitMix64 output function. */
+uint64_t oracle_digest_mix1(uint64_t a, uint64_t b) { return fmix(a ^ (b * 0x9e3779b97f4a7c15ull)); }
+uint64_t oracle_digest_mix2(uint64_t a, uint64_t b) { return fmix(b ^ (a * 0xc2b2ae3d27d4eb4full)); }
 
 /* Validation shared by the entry points: returns 0 when the reference is a
  * set of distinct determinants with equal alpha and beta electron counts and

@@ -310,6 +310,10 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     // per record: 32 bytes plus about 60 bytes of tile bookkeeping per tile
     const double per_rec = sizeof(Rec32) + 60.0 / (double)tile_target;
     uint64_t max_rec = (uint64_t)((double)pass_budget / per_rec);
+    // Emission scatters every term to a random tile through an atomic cursor;
+    // when the cursors of a pass no longer fit in L2 those atomics go to DRAM,
+    // so a default pass holds at most kMaxTilesPerPass tiles.
+    if (!o.pass_budget_bytes) max_rec = std::min<uint64_t>(max_rec, kMaxTilesPerPass * tile_target);
     if (max_rec < 1024)
         return fail(c, PT2_ERR_OOM, "pass budget of %llu bytes is too small (context budget %llu, in use %llu)",
                     (unsigned long long)pass_budget, (unsigned long long)c->budget, (unsigned long long)c->used);

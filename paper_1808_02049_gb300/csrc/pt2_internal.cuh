@@ -12,11 +12,12 @@ constexpr int kMaxOrb = 64;
 constexpr int kClassBits = 12;               // alpha-hash classes used to form passes
 constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
-constexpr int kGenBatch = 4;                 // terms a lane prepares before issuing their atomics
+constexpr int kGenBatch = 8;                 // terms whose slots a lane requests before storing any
 constexpr int kTileThreads = 512;            // tile sort-reduce CTA
 constexpr int kTileCap = 1536;               // records a tile CTA groups in shared memory
 constexpr int kTileBuckets = 1024;           // hash buckets of the in-tile counting sort (>= kTileCap / 2)
 constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
+constexpr uint64_t kMaxTilesPerPass = 1600000;  // keeps the tile cursors (8 B each) resident in L2
 constexpr int kBigThreads = 512;
 constexpr int kBigCap = 2048;                // Rec48 records grouped per chunk (oversize path)
 constexpr int kBigBuckets = 2048;

@@ -63,8 +63,8 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t z)
 }
 
 // Order-independent digest of the external set.
-__device__ __forceinline__ uint64_t digest1(uint64_t a, uint64_t b) { return fmix64(fmix64(a) ^ b); }
-__device__ __forceinline__ uint64_t digest2(uint64_t a, uint64_t b) { return fmix64(a ^ fmix64(b ^ 0x9e3779b97f4a7c15ull)); }
+__device__ __forceinline__ uint64_t digest1(uint64_t a, uint64_t b) { return fmix64(a ^ (b * 0x9e3779b97f4a7c15ull)); }
+__device__ __forceinline__ uint64_t digest2(uint64_t a, uint64_t b) { return fmix64(b ^ (a * 0xc2b2ae3d27d4eb4full)); }
 
 // Hash of a key that spreads it over the buckets of its tile.
 __device__ __forceinline__ uint32_t bucket_hash(uint64_t a, uint64_t b)
@@ -334,55 +334,53 @@ __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
     j1 = t - k * (k - 1) / 2;
 }
 
-// A lane's batch of up to kGenBatch terms: all tiles and slots are requested
-// before any record is stored, so the atomics of a batch are in flight together.
-template <int MODE>
-struct Batch {
-    uint64_t a[kGenBatch], b[kGenBatch], zt[kGenBatch];
-    double num[kGenBatch];
-    int64_t den[kGenBatch];
+// One batch of up to kGenBatch terms of a lane, items i0, i0 + step, ...:
+// first every term's tile is hashed and its slot requested (the atomics of
+// the batch are then in flight together), then the values are computed and
+// stored, so the arithmetic overlaps the atomic round trips.
+//   key(i, zt) -> false if item i is outside the pass, else sets the tile hash
+//   val(i, a, b, num, den) -> the record of item i
+template <int MODE, class KeyFn, class ValFn>
+__device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step, int n, KeyFn key, ValFn val)
+{
+    unsigned long long slot[kGenBatch];
     bool ok[kGenBatch];
-
-    __device__ __forceinline__ void flush(const GenParams &p)
-    {
-        if constexpr (MODE == kModeTileCount) {
 #pragma unroll
-            for (int u = 0; u < kGenBatch; ++u)
-                if (ok[u]) atomicAdd(&p.tile_counts[__umul64hi(zt[u], p.n_tiles)], 1u);
-        } else if constexpr (MODE == kModeEmit) {
-            unsigned long long slot[kGenBatch];
-#pragma unroll
-            for (int u = 0; u < kGenBatch; ++u)
-                slot[u] = ok[u] ? atomicAdd(&p.cursor[__umul64hi(zt[u], p.n_tiles)], 1ull) : 0ull;
-#pragma unroll
-            for (int u = 0; u < kGenBatch; ++u) {
-                if (!ok[u]) continue;
-                if (slot[u] >= p.rec_cap) {  // emission disagrees with the tile counts
-                    atomicOr(p.err, kErrCount);
-                    continue;
-                }
-                double2 *dst = reinterpret_cast<double2 *>(p.recs + slot[u]);
-                dst[0] = make_double2(__longlong_as_double((long long)a[u]), __longlong_as_double((long long)b[u]));
-                dst[1] = make_double2(num[u], __longlong_as_double((long long)den[u]));
-            }
-        } else if constexpr (MODE == kModeDetTerms) {
-#pragma unroll
-            for (int u = 0; u < kGenBatch; ++u) {
-                if (!ok[u]) continue;
-                unsigned long long slot = atomicAdd(&p.cursor[0], 1ull);
-                if (slot < p.rec_cap) {
-                    Rec32 r;
-                    r.a = a[u];
-                    r.b = b[u];
-                    r.num = num[u];
-                    // this mode reports H_aa itself (as double bits) for parity checks
-                    r.den = __double_as_longlong(p.e0 - den_to_double(den[u]));
-                    p.recs[slot] = r;
-                }
+    for (int u = 0; u < kGenBatch; ++u) {
+        const int i = i0 + u * step;
+        uint64_t zt = 0;
+        ok[u] = i < n && key(i, zt);
+        slot[u] = 0;
+        if (ok[u]) {
+            if constexpr (MODE == kModeTileCount) {
+                atomicAdd(&p.tile_counts[__umul64hi(zt, p.n_tiles)], 1u);
+            } else if constexpr (MODE == kModeEmit) {
+                slot[u] = atomicAdd(&p.cursor[__umul64hi(zt, p.n_tiles)], 1ull);
+            } else {
+                slot[u] = atomicAdd(&p.cursor[0], 1ull);
             }
         }
     }
-};
+    if constexpr (MODE == kModeEmit || MODE == kModeDetTerms) {
+#pragma unroll
+        for (int u = 0; u < kGenBatch; ++u) {
+            if (!ok[u]) continue;
+            if (slot[u] >= p.rec_cap) {  // emission disagrees with the counts
+                if constexpr (MODE == kModeEmit) atomicOr(p.err, kErrCount);
+                continue;
+            }
+            uint64_t a, b;
+            double num;
+            int64_t den;
+            val(i0 + u * step, a, b, num, den);
+            if constexpr (MODE == kModeDetTerms)  // this mode reports H_aa itself (as double bits)
+                den = __double_as_longlong(p.e0 - den_to_double(den));
+            double2 *dst = reinterpret_cast<double2 *>(p.recs + slot[u]);
+            dst[0] = make_double2(__longlong_as_double((long long)a), __longlong_as_double((long long)b));
+            dst[1] = make_double2(num, __longlong_as_double((long long)den));
+        }
+    }
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
@@ -556,22 +554,19 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
         return;
     } else {
         const uint64_t ZtaA = F.ZtaA, ZtbB = F.ZtbB;
-        Batch<MODE> bt;
 
         // ---- alpha singles (few per determinant: O(n) element each)
-        for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch) {
-#pragma unroll
-            for (int u = 0; u < kGenBatch; ++u) {
-                int k = k0 + u * kGenThreads;
-                bt.ok[u] = k < n_sa_pass;
-                if (!bt.ok[u]) continue;
-                int s = sa_pass[k];
-                uint32_t info = sa_info[s];
-                int r = info & 0xFF, a = (info >> 8) & 0xFF;
-                bt.a[u] = A ^ (1ull << r) ^ (1ull << a);
-                bt.b[u] = B;
-                bt.zt[u] = sa_zt[s] ^ ZtbB;
-                if constexpr (kVal) {
+        for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch)
+            emit_batch<MODE>(
+                p, k0, kGenThreads, n_sa_pass,
+                [&](int k, uint64_t &zt) {
+                    zt = sa_zt[sa_pass[k]] ^ ZtbB;
+                    return true;
+                },
+                [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                    const int s = sa_pass[k];
+                    const uint32_t info = sa_info[s];
+                    const int r = info & 0xFF, a = (info >> 8) & 0xFF;
                     double v = ht[a * N + r];
                     for (int q = 0; q < na; ++q) {
                         int j = F.occA[q];
@@ -581,26 +576,23 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
                         int j = F.occB[q];
                         v += eri[(((size_t)a * N + r) * N + j) * N + j];
                     }
-                    bt.num[u] = flip_sign(c * v, info >> 16);
-                    bt.den[u] = d0 - sa_delta[s];
-                }
-            }
-            bt.flush(p);
-        }
+                    ka = A ^ (1ull << r) ^ (1ull << a);
+                    kb = B;
+                    num = flip_sign(c * v, info >> 16);
+                    den = d0 - sa_delta[s];
+                });
         // ---- beta singles
         if (a_in)
-            for (int s0 = tid; s0 < p.n_sb; s0 += kGenThreads * kGenBatch) {
-#pragma unroll
-                for (int u = 0; u < kGenBatch; ++u) {
-                    int s = s0 + u * kGenThreads;
-                    bt.ok[u] = s < p.n_sb;
-                    if (!bt.ok[u]) continue;
-                    uint32_t info = sb_info[s];
-                    int r = info & 0xFF, a = (info >> 8) & 0xFF;
-                    bt.a[u] = A;
-                    bt.b[u] = B ^ (1ull << r) ^ (1ull << a);
-                    bt.zt[u] = ZtaA ^ sb_zt[s];
-                    if constexpr (kVal) {
+            for (int s0 = tid; s0 < p.n_sb; s0 += kGenThreads * kGenBatch)
+                emit_batch<MODE>(
+                    p, s0, kGenThreads, p.n_sb,
+                    [&](int s, uint64_t &zt) {
+                        zt = ZtaA ^ sb_zt[s];
+                        return true;
+                    },
+                    [&](int s, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                        const uint32_t info = sb_info[s];
+                        const int r = info & 0xFF, a = (info >> 8) & 0xFF;
                         double v = ht[a * N + r];
                         for (int q = 0; q < nb; ++q) {
                             int j = F.occB[q];
@@ -611,19 +603,18 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
                             int j = F.occA[q];
                             v += eri[(((size_t)a * N + r) * N + j) * N + j];
                         }
-                        bt.num[u] = flip_sign(c * v, info >> 16);
-                        bt.den[u] = d0 - sb_delta[s];
-                    }
-                }
-                bt.flush(p);
-            }
+                        ka = A;
+                        kb = B ^ (1ull << r) ^ (1ull << a);
+                        num = flip_sign(c * v, info >> 16);
+                        den = d0 - sb_delta[s];
+                    });
         // ---- alpha-beta doubles: one alpha single per warp, beta singles over lanes
         for (int k = warp; k < n_sa_pass; k += nw) {
-            int s = sa_pass[k];
-            uint32_t info = sa_info[s];
-            int rA = info & 0xFF, aA = (info >> 8) & 0xFF;
-            uint64_t a2 = A ^ (1ull << rA) ^ (1ull << aA);
-            uint64_t ztA = sa_zt[s];
+            const int s = sa_pass[k];
+            const uint32_t info = sa_info[s];
+            const int rA = info & 0xFF, aA = (info >> 8) & 0xFF;
+            const uint64_t a2 = A ^ (1ull << rA) ^ (1ull << aA);
+            const uint64_t ztA = sa_zt[s];
             int64_t baseD = 0;
             double cA = 0.0;
             const double *slice = nullptr;
@@ -635,24 +626,21 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
                 cA = flip_sign(c, info >> 16);
                 slice = eri + ((size_t)aA * N + rA) * N * N;
             }
-            for (int sb0 = lane; sb0 < p.n_sb; sb0 += 32 * kGenBatch) {
-#pragma unroll
-                for (int u = 0; u < kGenBatch; ++u) {
-                    int sb = sb0 + 32 * u;
-                    bt.ok[u] = sb < p.n_sb;
-                    if (!bt.ok[u]) continue;
-                    uint32_t bi = sb_info[sb];
-                    int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
-                    bt.a[u] = a2;
-                    bt.b[u] = B ^ (1ull << rB) ^ (1ull << aB);
-                    bt.zt[u] = ztA ^ sb_zt[sb];
-                    if constexpr (kVal) {
-                        bt.num[u] = flip_sign(cA * slice[aB * N + rB], bi >> 16);
-                        bt.den[u] = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
-                    }
-                }
-                bt.flush(p);
-            }
+            for (int sb0 = lane; sb0 < p.n_sb; sb0 += 32 * kGenBatch)
+                emit_batch<MODE>(
+                    p, sb0, 32, p.n_sb,
+                    [&](int sb, uint64_t &zt) {
+                        zt = ztA ^ sb_zt[sb];
+                        return true;
+                    },
+                    [&](int sb, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                        const uint32_t bi = sb_info[sb];
+                        const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
+                        ka = a2;
+                        kb = B ^ (1ull << rB) ^ (1ull << aB);
+                        num = flip_sign(cA * slice[aB * N + rB], bi >> 16);
+                        den = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
+                    });
             __syncwarp();
         }
         // ---- same-spin doubles: one occupied pair per warp, virtual pairs over lanes
@@ -666,11 +654,12 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
             const int64_t *g = spin ? F.gB : F.gA;
             const uint64_t W = spin ? B : A;
             for (int pi = warp; pi < npo; pi += nw) {
-                int pr = pairs[pi];
-                int r1 = occ[pr & 0xFF], r2 = occ[pr >> 8];
-                uint64_t w12 = W ^ (1ull << r1) ^ (1ull << r2);
-                uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
-                uint64_t zt12 = spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
+                const int pr = pairs[pi];
+                const int r1 = occ[pr & 0xFF], r2 = occ[pr >> 8];
+                const uint64_t w12 = W ^ (1ull << r1) ^ (1ull << r2);
+                const uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
+                const uint64_t zt12 =
+                    spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
                 int64_t base = 0;
                 if constexpr (kVal) {
                     // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
@@ -682,41 +671,37 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
                     __syncwarp();
                     base = d0 + g[r1] + g[r2] - WSx[r1 * N + r2];
                 }
-                for (int t0 = lane; t0 < npv; t0 += 32 * kGenBatch) {
-#pragma unroll
-                    for (int u = 0; u < kGenBatch; ++u) {
-                        int t = t0 + 32 * u;
-                        bt.ok[u] = t < npv;
-                        if (!bt.ok[u]) continue;
-                        int pv = pairs[t];
-                        int j1 = pv & 0xFF, j2 = pv >> 8;
-                        int a1 = vir[j1], a2 = vir[j2];
-                        uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
-                        if (spin == 0) {
-                            uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
-                            if (cl < p.class_lo || cl >= p.class_hi || !cons_ok(p.cons_mod, p.cons_rem, w2)) {
-                                bt.ok[u] = false;
-                                continue;
+                for (int t0 = lane; t0 < npv; t0 += 32 * kGenBatch)
+                    emit_batch<MODE>(
+                        p, t0, 32, npv,
+                        [&](int t, uint64_t &zt) {
+                            const int pv = pairs[t];
+                            const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
+                            if (spin == 0) {
+                                uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
+                                if (cl < p.class_lo || cl >= p.class_hi) return false;
+                                if (!cons_ok(p.cons_mod, p.cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
+                                zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
+                            } else {
+                                zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
                             }
-                            bt.a[u] = w2;
-                            bt.b[u] = B;
-                            bt.zt[u] = zt12 ^ F.zta[a1] ^ F.zta[a2];
-                        } else {
-                            bt.a[u] = A;
-                            bt.b[u] = w2;
-                            bt.zt[u] = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
-                        }
-                        if constexpr (kVal) {
-                            uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
-                            uint32_t par = __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                            double e = eri[(((size_t)a1 * N + r1) * N + a2) * N + r2] -
-                                       eri[(((size_t)a1 * N + r2) * N + a2) * N + r1];
-                            bt.num[u] = flip_sign(c * e, par);
-                            bt.den[u] = base - vec[j1] - vec[j2] - WSx[a1 * N + a2];
-                        }
-                    }
-                    bt.flush(p);
-                }
+                            return true;
+                        },
+                        [&](int t, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                            const int pv = pairs[t];
+                            const int j1 = pv & 0xFF, j2 = pv >> 8;
+                            const int a1 = vir[j1], a2 = vir[j2];
+                            const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
+                            ka = spin ? A : w2;
+                            kb = spin ? w2 : B;
+                            const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
+                            const uint32_t par =
+                                __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                            const double e = eri[(((size_t)a1 * N + r1) * N + a2) * N + r2] -
+                                             eri[(((size_t)a1 * N + r2) * N + a2) * N + r1];
+                            num = flip_sign(c * e, par);
+                            den = base - vec[j1] - vec[j2] - WSx[a1 * N + a2];
+                        });
                 __syncwarp();
             }
         }
@@ -1019,15 +1004,13 @@ __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long 
 // One unique key: explicit filter against the reference slice, then the
 // Epstein-Nesbet term num^2 / (E0 - H_aa) of Eq. 3, added exactly.
 __device__ __forceinline__ void finish_key(const TileParams &p, const uint64_t *rk, unsigned long long nrk,
-                                           uint64_t a, uint64_t b, uint64_t fl, int64_t fh, int64_t den,
-                                           KeyStats &st)
+                                           uint64_t a, uint64_t b, double num, int64_t den, KeyStats &st)
 {
     st.n_unique++;
     if (in_slice(rk, nrk, a, b)) {
         st.n_in_ref++;
         return;
     }
-    double num = fx_to_double(fl, fh);
     double d = den_to_double(den);
     double term = (num * num) * recip(d, den);
     fx_add_double(st.e2_lo, st.e2_hi, term, st.err);
@@ -1146,7 +1129,59 @@ __device__ __forceinline__ void reduce_groups(const TileParams &p, const Rec *re
             else fx_add_double(fl, fh, r2.num, st.err);
             den = r2.den < den ? r2.den : den;
         }
-        finish_key(p, rk, nrk, r0.a, r0.b, fl, fh, den, st);
+        finish_key(p, rk, nrk, r0.a, r0.b, fx_to_double(fl, fh), den, st);
+    }
+}
+
+// Positions in the grouped order where a new key starts, collected in any
+// order (every sum they feed is exact, so the order does not matter).
+template <class Rec>
+__device__ __forceinline__ void collect_heads(const Rec *recs, const uint16_t *perm, int cnt, uint16_t *heads,
+                                              unsigned int *nheads)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < cnt; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        bool head = false;
+        if (j < cnt) {
+            const Rec &r0 = recs[perm[j]];
+            head = j == 0 || !(recs[perm[j - 1]].a == r0.a && recs[perm[j - 1]].b == r0.b);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, head);
+        unsigned base = 0;
+        if (lane == 0 && m) base = atomicAdd(nheads, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (head) heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
+    }
+}
+
+// Every thread finishes whole keys: a single record passes its FP64
+// numerator through; duplicates are summed exactly in fixed point first.
+__device__ __forceinline__ void finish_heads(const TileParams &p, const Rec32 *recs, const uint16_t *perm, int cnt,
+                                             const uint16_t *heads, int nh, const uint64_t *rk,
+                                             unsigned long long nrk, KeyStats &st)
+{
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int j = heads[h];
+        const Rec32 &r0 = recs[perm[j]];
+        double num = r0.num;
+        int64_t den = r0.den;
+        if (j + 1 < cnt) {
+            const Rec32 &r1 = recs[perm[j + 1]];
+            if (r1.a == r0.a && r1.b == r0.b) {
+                uint64_t fl = 0;
+                int64_t fh = 0;
+                fx_add_double(fl, fh, r0.num, st.err);
+                for (int k = j + 1; k < cnt; ++k) {
+                    const Rec32 &r2 = recs[perm[k]];
+                    if (r2.a != r0.a || r2.b != r0.b) break;
+                    fx_add_double(fl, fh, r2.num, st.err);
+                    den = r2.den < den ? r2.den : den;
+                }
+                num = fx_to_double(fl, fh);
+            }
+        }
+        finish_key(p, rk, nrk, r0.a, r0.b, num, den, st);
     }
 }
 
@@ -1158,6 +1193,7 @@ struct MainSmem {
     uint32_t hist[kTileBuckets];
     uint64_t rk[2 * kRefSliceSmem];
     uint64_t bar[2];
+    unsigned int nheads;
     uint32_t warp_tot[32];
     unsigned long long red[10][32];
 };
@@ -1187,7 +1223,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams 
         if (blockIdx.x < p.n_tiles) issue_tile(p, M, blockIdx.x, 0);
     }
     __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phases = 0;  // bit b: parity of the next phase of buffer b
     int k = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G, ++k) {
         const int buf = k & 1;
@@ -1206,15 +1242,18 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams 
         const int cnt = (int)cntl;
         unsigned long long nrk;
         const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
-        mbar_wait_bounded(&M.bar[buf], phase[buf], p.err);
-        phase[buf] ^= 1u;
+        mbar_wait_bounded(&M.bar[buf], (phases >> buf) & 1u, p.err);
+        phases ^= 1u << buf;
         const Rec32 *recs = M.recs[buf];
         auto key = [&](int i, uint64_t &a, uint64_t &b) {
             a = recs[i].a;
             b = recs[i].b;
         };
+        if (threadIdx.x == 0) M.nheads = 0;
         group_keys(cnt, kTileBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
-        reduce_groups<Rec32, false>(p, recs, M.perm, cnt, rk, nrk, st);
+        collect_heads(recs, M.perm, cnt, M.rnk, &M.nheads);  // rnk is free after grouping
+        __syncthreads();
+        finish_heads(p, recs, M.perm, cnt, M.rnk, (int)M.nheads, rk, nrk, st);
         __syncthreads();  // buffer, perm and slice free for the next tile
     }
     flush_stats(p, st, M.red);
