@@ -13,9 +13,9 @@ constexpr int kClassBits = 12;               // alpha-hash classes used to form 
 constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
 constexpr int kGenBatch = 8;                 // terms whose slots a lane requests before storing any
-constexpr int kTileThreads = 512;            // tile sort-reduce CTA
-constexpr int kTileCap = 1536;               // records a tile CTA groups in shared memory
-constexpr int kTileBuckets = 1024;           // hash buckets of the in-tile counting sort (>= kTileCap / 2)
+constexpr int kTileThreads = 1024;           // tile sort-reduce CTA (one per SM)
+constexpr int kTileCap = 3072;               // records a tile CTA groups in shared memory
+constexpr int kTileBuckets = 2048;           // hash buckets of the in-tile counting sort (>= kTileCap / 2)
 constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
 constexpr uint64_t kMaxTilesPerPass = 1600000;  // keeps the tile cursors (8 B each) resident in L2
 constexpr int kBigThreads = 512;

@@ -941,38 +941,50 @@ struct KeyStats {
 
 // Group `cnt` keys held in shared memory so that equal keys are adjacent:
 // counting sort by a key hash into B buckets (B a power of two, about cnt/2),
-// then insertion sort of each bucket by the 128-bit key (alpha word most
-// significant).  On return perm[0..cnt) lists record indices in (bucket, key)
-// order.  hist must be zero on entry and is left holding bucket offsets.
+// then within each bucket equal keys are gathered: small buckets by an
+// insertion sort on the 128-bit key (alpha word most significant), large ones
+// (a key with many duplicates) by repeated warp-wide partitions.  On return
+// perm[0..cnt) lists record indices bucket by bucket with equal keys
+// contiguous.  hist must be zero on entry and is left zero.
 template <class KeyAt>
-__device__ void group_keys(int cnt, int max_buckets, KeyAt key, uint16_t *perm, uint16_t *rnk, uint32_t *hist,
-                           uint32_t *warp_tot)
+__device__ void group_keys(int cnt, int max_buckets, KeyAt key, uint16_t *perm, uint16_t *rnk, uint16_t *bkt,
+                           uint32_t *hist, uint32_t *warp_tot, unsigned int *nbig)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     int B = 32;
     while (2 * B < cnt && B < max_buckets) B <<= 1;
+    if (tid == 0) *nbig = 0;
     for (int i = tid; i < cnt; i += nt) {
         uint64_t a, b;
         key(i, a, b);
-        uint32_t bb = bucket_hash(a, b) & (uint32_t)(B - 1);
+        const uint32_t bb = bucket_hash(a, b) & (uint32_t)(B - 1);
+        bkt[i] = (uint16_t)bb;
         rnk[i] = (uint16_t)atomicAdd(&hist[bb], 1u);
     }
     __syncthreads();
     block_scan_excl_u32(hist, B, warp_tot);
-    for (int i = tid; i < cnt; i += nt) {
-        uint64_t a, b;
-        key(i, a, b);
-        uint32_t bb = bucket_hash(a, b) & (uint32_t)(B - 1);
-        perm[hist[bb] + rnk[i]] = (uint16_t)i;
-    }
+    for (int i = tid; i < cnt; i += nt) perm[hist[bkt[i]] + rnk[i]] = (uint16_t)i;
     __syncthreads();
+    // small buckets: one thread each; large ones are queued for a warp (bkt is free now)
     for (int bb = tid; bb < B; bb += nt) {
-        int s = (int)hist[bb];
-        int e = bb + 1 < B ? (int)hist[bb + 1] : cnt;
+        const int s = (int)hist[bb];
+        const int e = bb + 1 < B ? (int)hist[bb + 1] : cnt;
+        if (e - s <= 1) continue;
+        if (e - s > 24) {
+            bkt[atomicAdd(nbig, 1u)] = (uint16_t)bb;
+            continue;
+        }
+        uint64_t la, lb;  // last key of the sorted prefix
+        key(perm[s], la, lb);
         for (int i = s + 1; i < e; ++i) {
-            uint16_t x = perm[i];
+            const uint16_t x = perm[i];
             uint64_t a, b;
             key(x, a, b);
+            if (!key_less(a, b, la, lb)) {
+                la = a;
+                lb = b;
+                continue;
+            }
             int j = i;
             while (j > s) {
                 uint64_t pa, pb;
@@ -982,6 +994,43 @@ __device__ void group_keys(int cnt, int max_buckets, KeyAt key, uint16_t *perm, 
                 --j;
             }
             perm[j] = x;
+        }
+    }
+    __syncthreads();
+    const int nb = (int)*nbig;
+    for (int q = warp; q < nb; q += nw) {
+        const int bb = bkt[q];
+        const int s = (int)hist[bb];
+        const int e = bb + 1 < B ? (int)hist[bb + 1] : cnt;
+        int pos = s;
+        while (pos < e) {
+            uint64_t ka, kb;
+            key(perm[pos], ka, kb);
+            int n_eq = 0, n_ne = 0;
+            for (int base = pos; base < e; base += 32) {
+                const int j = base + lane;
+                uint16_t x = 0;
+                bool eq = false;
+                if (j < e) {
+                    x = perm[j];
+                    uint64_t a, b;
+                    key(x, a, b);
+                    eq = a == ka && b == kb;
+                }
+                const unsigned m_eq = __ballot_sync(0xffffffffu, j < e && eq);
+                const unsigned m_ne = __ballot_sync(0xffffffffu, j < e && !eq);
+                const unsigned lt = (1u << lane) - 1u;
+                if (j < e) {
+                    if (eq) rnk[pos + n_eq + __popc(m_eq & lt)] = x;
+                    else rnk[e - 1 - (n_ne + __popc(m_ne & lt))] = x;
+                }
+                n_eq += __popc(m_eq);
+                n_ne += __popc(m_ne);
+            }
+            __syncwarp();
+            for (int j = pos + lane; j < e; j += 32) perm[j] = rnk[j];
+            __syncwarp();
+            pos += n_eq;
         }
     }
     __syncthreads();
@@ -1156,10 +1205,11 @@ __device__ __forceinline__ void collect_heads(const Rec *recs, const uint16_t *p
 }
 
 // Every thread finishes whole keys: a single record passes its FP64
-// numerator through; duplicates are summed exactly in fixed point first.
+// numerator through; a few duplicates are summed exactly in fixed point by
+// the thread; runs longer than 32 records are queued for a whole warp.
 __device__ __forceinline__ void finish_heads(const TileParams &p, const Rec32 *recs, const uint16_t *perm, int cnt,
-                                             const uint16_t *heads, int nh, const uint64_t *rk,
-                                             unsigned long long nrk, KeyStats &st)
+                                             const uint16_t *heads, int nh, uint16_t *longq, unsigned int *nlong,
+                                             const uint64_t *rk, unsigned long long nrk, KeyStats &st)
 {
     for (int h = threadIdx.x; h < nh; h += blockDim.x) {
         const int j = heads[h];
@@ -1169,6 +1219,13 @@ __device__ __forceinline__ void finish_heads(const TileParams &p, const Rec32 *r
         if (j + 1 < cnt) {
             const Rec32 &r1 = recs[perm[j + 1]];
             if (r1.a == r0.a && r1.b == r0.b) {
+                if (j + 32 < cnt) {
+                    const Rec32 &rl = recs[perm[j + 32]];
+                    if (rl.a == r0.a && rl.b == r0.b) {  // long run: a warp takes it
+                        longq[atomicAdd(nlong, 1u)] = (uint16_t)j;
+                        continue;
+                    }
+                }
                 uint64_t fl = 0;
                 int64_t fh = 0;
                 fx_add_double(fl, fh, r0.num, st.err);
@@ -1185,78 +1242,161 @@ __device__ __forceinline__ void finish_heads(const TileParams &p, const Rec32 *r
     }
 }
 
+// A warp sums one long run of equal keys: lanes stride over the records,
+// the exact 128-bit partial sums are combined by shuffles.
+__device__ __forceinline__ void finish_long(const TileParams &p, const Rec32 *recs, const uint16_t *perm, int cnt,
+                                            const uint16_t *longq, int nl, const uint64_t *rk,
+                                            unsigned long long nrk, KeyStats &st)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < nl; q += nw) {
+        const int j = longq[q];
+        const uint64_t ka = recs[perm[j]].a, kb = recs[perm[j]].b;
+        uint64_t fl = 0;
+        int64_t fh = 0;
+        int64_t den = recs[perm[j]].den;
+        for (int base = j; base < cnt; base += 32) {
+            const int k = base + lane;
+            bool same = false;
+            if (k < cnt) {
+                const Rec32 &r = recs[perm[k]];
+                same = r.a == ka && r.b == kb;
+                if (same) {
+                    fx_add_double(fl, fh, r.num, st.err);
+                    den = r.den < den ? r.den : den;
+                }
+            }
+            if (__ballot_sync(0xffffffffu, same) != 0xffffffffu) break;
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const uint64_t olo = __shfl_down_sync(0xffffffffu, fl, off);
+            const int64_t ohi = __shfl_down_sync(0xffffffffu, fh, off);
+            const int64_t od = __shfl_down_sync(0xffffffffu, den, off);
+            fx_add_fx(fl, fh, olo, ohi);
+            den = od < den ? od : den;
+        }
+        if (lane == 0) finish_key(p, rk, nrk, ka, kb, fx_to_double(fl, fh), den, st);
+    }
+}
+
 // Shared memory of the main tile kernel: two record buffers (the next tile is
 // fetched by TMA while the current one is grouped).
 struct MainSmem {
     Rec32 recs[2][kTileCap];
-    uint16_t perm[kTileCap], rnk[kTileCap];
-    uint32_t hist[kTileBuckets];
+    uint16_t perm[kTileCap], rnk[kTileCap], bkt[kTileCap];
+    union {
+        uint32_t hist[kTileBuckets];
+        unsigned long long red[10][32];
+    } u;
     uint64_t rk[2 * kRefSliceSmem];
+    unsigned long long meta[4];  // current tile: offset, count, reference offset, reference count
     uint64_t bar[2];
-    unsigned int nheads;
+    unsigned int nheads, nlong, nbig;
     uint32_t warp_tot[32];
-    unsigned long long red[10][32];
 };
 
 size_t tile_smem_bytes() { return sizeof(MainSmem); }
 
-__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, uint64_t t, int buf)
+struct TileMeta {
+    unsigned long long off, cnt, roff, rcnt;
+};
+
+__device__ __forceinline__ TileMeta tile_meta(const TileParams &p, uint64_t t)
 {
-    unsigned long long off = p.tile_off[t], cnt = p.tile_off[t + 1] - off;
-    if (cnt == 0 || cnt > (unsigned long long)kTileCap) return;
-    fence_proxy_async_smem();
-    bulk_load(M.recs[buf], p.recs + off, (uint32_t)(cnt * sizeof(Rec32)), &M.bar[buf]);
+    TileMeta m{0, 0, 0, 0};
+    if (t < p.n_tiles) {
+        m.off = p.tile_off[t];
+        m.cnt = p.tile_off[t + 1] - m.off;
+        m.roff = p.ref_off[t];
+        m.rcnt = p.ref_off[t + 1] - m.roff;
+    }
+    return m;
 }
 
-// Persistent: CTA g handles tiles g, g + G, g + 2G, ...
-__global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams p)
+__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, const TileMeta &m, int buf)
+{
+    if (m.cnt == 0 || m.cnt > (unsigned long long)kTileCap) return;
+    fence_proxy_async_smem();
+    bulk_load(M.recs[buf], p.recs + m.off, (uint32_t)(m.cnt * sizeof(Rec32)), &M.bar[buf]);
+}
+
+// Persistent: CTA g handles tiles g, g + G, g + 2G, ...  Thread 0 keeps the
+// tile metadata two tiles ahead and the record load one tile ahead.
+__global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
     const uint64_t G = gridDim.x;
     KeyStats st;
     st.clear();
-    for (int i = threadIdx.x; i < kTileBuckets; i += blockDim.x) M.hist[i] = 0;
+    for (int i = threadIdx.x; i < kTileBuckets; i += blockDim.x) M.u.hist[i] = 0;
+    TileMeta nx{0, 0, 0, 0};
     if (threadIdx.x == 0) {
         mbar_init(&M.bar[0], 1);
         mbar_init(&M.bar[1], 1);
-        if (blockIdx.x < p.n_tiles) issue_tile(p, M, blockIdx.x, 0);
+        const TileMeta m0 = tile_meta(p, blockIdx.x);
+        nx = tile_meta(p, blockIdx.x + G);
+        issue_tile(p, M, m0, 0);
+        M.meta[0] = m0.off;
+        M.meta[1] = m0.cnt;
+        M.meta[2] = m0.roff;
+        M.meta[3] = m0.rcnt;
     }
     __syncthreads();
     uint32_t phases = 0;  // bit b: parity of the next phase of buffer b
     int k = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G, ++k) {
         const int buf = k & 1;
-        const unsigned long long off = p.tile_off[t];
-        const unsigned long long cntl = p.tile_off[t + 1] - off;
-        if (threadIdx.x == 0 && t + G < p.n_tiles) issue_tile(p, M, t + G, buf ^ 1);
-        if (cntl == 0) continue;
+        const unsigned long long cntl = M.meta[1];
+        const unsigned long long roff = M.meta[2], rcnt = M.meta[3];
+        TileMeta nnx{0, 0, 0, 0};
+        if (threadIdx.x == 0) {
+            issue_tile(p, M, nx, buf ^ 1);
+            nnx = tile_meta(p, t + 2 * G);  // consumed at the end of this iteration
+        }
         if (cntl > (unsigned long long)kTileCap) {
             if (threadIdx.x == 0) {
-                unsigned idx = atomicAdd(&p.acc->n_big, 1u);
+                const unsigned idx = atomicAdd(&p.acc->n_big, 1u);
                 p.big_list[idx] = (uint32_t)t;
                 atomicMax(&p.acc->big_max, cntl);
             }
-            continue;
+        } else if (cntl > 0) {
+            const int cnt = (int)cntl;
+            const uint64_t *rk = M.rk;
+            if (rcnt <= (unsigned long long)kRefSliceSmem) {
+                for (unsigned long long i = threadIdx.x; i < 2 * rcnt; i += blockDim.x) M.rk[i] = p.ref_keys[2 * roff + i];
+            } else {
+                rk = p.ref_keys + 2 * roff;
+            }
+            mbar_wait_bounded(&M.bar[buf], (phases >> buf) & 1u, p.err);
+            phases ^= 1u << buf;
+            const Rec32 *recs = M.recs[buf];
+            auto key = [&](int i, uint64_t &a, uint64_t &b) {
+                a = recs[i].a;
+                b = recs[i].b;
+            };
+            if (threadIdx.x == 0) {
+                M.nheads = 0;
+                M.nlong = 0;
+            }
+            group_keys(cnt, kTileBuckets, key, M.perm, M.rnk, M.bkt, M.u.hist, M.warp_tot, &M.nbig);
+            collect_heads(recs, M.perm, cnt, M.rnk, &M.nheads);  // rnk is free after grouping
+            __syncthreads();
+            finish_heads(p, recs, M.perm, cnt, M.rnk, (int)M.nheads, M.bkt, &M.nlong, rk, rcnt, st);
+            __syncthreads();
+            finish_long(p, recs, M.perm, cnt, M.bkt, (int)M.nlong, rk, rcnt, st);
         }
-        const int cnt = (int)cntl;
-        unsigned long long nrk;
-        const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
-        mbar_wait_bounded(&M.bar[buf], (phases >> buf) & 1u, p.err);
-        phases ^= 1u << buf;
-        const Rec32 *recs = M.recs[buf];
-        auto key = [&](int i, uint64_t &a, uint64_t &b) {
-            a = recs[i].a;
-            b = recs[i].b;
-        };
-        if (threadIdx.x == 0) M.nheads = 0;
-        group_keys(cnt, kTileBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
-        collect_heads(recs, M.perm, cnt, M.rnk, &M.nheads);  // rnk is free after grouping
-        __syncthreads();
-        finish_heads(p, recs, M.perm, cnt, M.rnk, (int)M.nheads, rk, nrk, st);
-        __syncthreads();  // buffer, perm and slice free for the next tile
+        if (threadIdx.x == 0) {
+            M.meta[0] = nx.off;
+            M.meta[1] = nx.cnt;
+            M.meta[2] = nx.roff;
+            M.meta[3] = nx.rcnt;
+            nx = nnx;
+        }
+        __syncthreads();  // buffer, perm, slice and metadata ready for the next tile
     }
-    flush_stats(p, st, M.red);
+    flush_stats(p, st, M.u.red);
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_inval(&M.bar[0]);
@@ -1282,16 +1422,22 @@ cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 // min denominator) records; the reduced list is regrouped until it fits, then
 // finished like a normal tile.  Exact sums make the result independent of
 // the chunking.
+constexpr int kBigIdx = kTileCap > kBigCap ? kTileCap : kBigCap;
+static_assert(kBigBuckets * 2 >= kBigIdx, "oversize buckets must cover half a chunk");
+static_assert(kBigBuckets <= 4 * kBigThreads && kTileBuckets <= 4 * kTileThreads, "block scan capacity");
+static_assert(kTileBuckets * 2 >= kTileCap, "tile buckets must cover half a tile");
+
 struct BigSmem {
     union {
         Rec32 r32[kTileCap];
         Rec48 r48[kBigCap];
     } u;
-    uint16_t perm[kBigCap], rnk[kBigCap];
+    // index arrays cover the larger of a Rec32 chunk and a Rec48 chunk
+    uint16_t perm[kBigIdx], rnk[kBigIdx], bkt[kBigIdx];
     uint32_t hist[kBigBuckets];
     uint64_t rk[2 * kRefSliceSmem];
     uint64_t bar;
-    unsigned int out_count;
+    unsigned int out_count, nbig;
     uint32_t warp_tot[32];
     unsigned long long red[10][32];
 };
@@ -1374,7 +1520,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
                 a = recs[i].a;
                 b = recs[i].b;
             };
-            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.bkt, M.hist, M.warp_tot, &M.nbig);
             chunk_to_partials<Rec32, false>(recs, M.perm, m, bufA + u, &M.out_count, st.err);
             __syncthreads();
             u += M.out_count;
@@ -1394,7 +1540,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
                     a = recs[i].a;
                     b = recs[i].b;
                 };
-                group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+                group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.bkt, M.hist, M.warp_tot, &M.nbig);
                 chunk_to_partials<Rec48, true>(recs, M.perm, m, dst + u2, &M.out_count, st.err);
                 __syncthreads();
                 u2 += M.out_count;
@@ -1422,7 +1568,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
                 a = recs[i].a;
                 b = recs[i].b;
             };
-            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.hist, M.warp_tot);
+            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.bkt, M.hist, M.warp_tot, &M.nbig);
             reduce_groups<Rec48, true>(p, recs, M.perm, m, rk, nrk, st);
         }
         __syncthreads();
