@@ -314,6 +314,9 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     // when the cursors of a pass no longer fit in L2 those atomics go to DRAM,
     // so a default pass holds at most kMaxTilesPerPass tiles.
     if (!o.pass_budget_bytes) max_rec = std::min<uint64_t>(max_rec, kMaxTilesPerPass * tile_target);
+    // Random 32-byte writes spread over a larger footprint run slower (address
+    // translation reach), so a default pass also stays below kMaxPassBytes.
+    if (!o.pass_budget_bytes) max_rec = std::min<uint64_t>(max_rec, kMaxPassBytes / sizeof(Rec32));
     if (max_rec < 1024)
         return fail(c, PT2_ERR_OOM, "pass budget of %llu bytes is too small (context budget %llu, in use %llu)",
                     (unsigned long long)pass_budget, (unsigned long long)c->budget, (unsigned long long)c->used);

@@ -18,6 +18,7 @@ constexpr int kTileCap = 3072;               // records a tile CTA groups in sha
 constexpr int kTileBuckets = 2048;           // hash buckets of the in-tile counting sort (>= kTileCap / 2)
 constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
 constexpr uint64_t kMaxTilesPerPass = 1600000;  // keeps the tile cursors (8 B each) resident in L2
+constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
 constexpr int kBigThreads = 512;
 constexpr int kBigCap = 2048;                // Rec48 records grouped per chunk (oversize path)
 constexpr int kBigBuckets = 2048;
