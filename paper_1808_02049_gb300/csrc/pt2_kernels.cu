@@ -1153,118 +1153,261 @@ __device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint6
     return p.ref_keys + 2 * s;
 }
 
-// Reduce the grouped records: every thread walks a contiguous range of the
-// sorted positions and finishes the keys whose first record lies in it.
-template <class Rec, bool kFixed>
-__device__ __forceinline__ void reduce_groups(const TileParams &p, const Rec *recs, const uint16_t *perm, int cnt,
-                                              const uint64_t *rk, unsigned long long nrk, KeyStats &st)
+// ------------------------------------------- in-tile LSD radix sort + reduce
+//
+// A tile (or a chunk of an oversize tile) of at most kSortCap records sits in
+// shared memory.  Its keys are compressed to 32-bit hashes (the paper's
+// generalised compression with hash functions) and sorted with a stable LSD
+// radix sort, four 8-bit digit passes staged through shared memory: each warp
+// ranks its items with eight ballots per digit, a block-wide scan turns the
+// per-warp digit counts into offsets, and items scatter to their rank.  Equal
+// keys then form contiguous runs; every run is verified against the full
+// 128-bit key (a hash collision makes the chunk fall back to an exact path)
+// and reduced by key.
+
+constexpr int kSortThreads = 1024;
+constexpr int kSortItems = kSortCap / kSortThreads;   // items per thread, striped
+constexpr int kSortRows = kSortItems * (kSortThreads / 32);
+constexpr int kLongRun = 8;                            // longer runs are summed by a warp
+static_assert(kSortItems == 2, "the sort is written for two items per thread");
+
+struct SortSmem {
+    uint64_t words[2][kSortCap];  // (hash << 16) | record index
+    union {
+        uint16_t cnt16[256 * kSortRows];  // [digit][row] counts, then offsets
+        unsigned long long red[10][32];   // final statistics reduction
+    } u;
+    uint16_t heads[kSortCap], longq[kSortCap];
+    uint32_t warp_tot[33];
+    unsigned int nheads, nlong, collision;
+};
+
+__device__ __forceinline__ uint32_t key_hash32(uint64_t a, uint64_t b)
 {
-    const int nt = blockDim.x;
-    const int chunk = (cnt + nt - 1) / nt;
-    const int s = threadIdx.x * chunk, e = min(cnt, s + chunk);
-    for (int j = s; j < e; ++j) {
-        const Rec &r0 = recs[perm[j]];
-        if (j > 0) {
-            const Rec &rp = recs[perm[j - 1]];
-            if (rp.a == r0.a && rp.b == r0.b) continue;
-        }
-        uint64_t fl = 0;
-        int64_t fh = 0;
-        int64_t den = r0.den;
-        for (int k = j; k < cnt; ++k) {
-            const Rec &r2 = recs[perm[k]];
-            if (k > j && (r2.a != r0.a || r2.b != r0.b)) break;
-            if constexpr (kFixed) fx_add_fx(fl, fh, r2.fx_lo, r2.fx_hi);
-            else fx_add_double(fl, fh, r2.num, st.err);
-            den = r2.den < den ? r2.den : den;
-        }
-        finish_key(p, rk, nrk, r0.a, r0.b, fx_to_double(fl, fh), den, st);
-    }
+    uint64_t h = (a ^ 0x2545F4914F6CDD1Dull) * 0x9E3779B97F4A7C15ull;
+    h ^= b;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 31;
+    h *= 0x94D049BB133111EBull;
+    return (uint32_t)(h >> 32);
 }
 
-// Positions in the grouped order where a new key starts, collected in any
-// order (every sum they feed is exact, so the order does not matter).
+// Exclusive scan of one value per thread over the block (1024 threads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = warp_tot[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += t;
+        }
+        warp_tot[lane] = wi - w;
+        if (lane == 31) warp_tot[32] = wi;
+    }
+    __syncthreads();
+    total = warp_tot[32];
+    return warp_tot[warp] + incl - v;
+}
+
+// One stable counting-sort pass on the 8-bit digit at `shift` of the hash.
+// Positions are striped: item it of thread t is position it * 1024 + t, and
+// row it * 32 + warp counts the items of one warp at one item index, so rows
+// in order cover positions in order.
+__device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int cnt, int shift, SortSmem &S)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint4 *c4 = reinterpret_cast<uint4 *>(S.u.cnt16);
+    constexpr int n4 = 256 * kSortRows * 2 / 16;
+    for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    uint64_t w[kSortItems];
+    uint32_t dig[kSortItems], rank[kSortItems];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int pos = it * kSortThreads + tid;
+        const bool valid = pos < cnt;
+        w[it] = valid ? src[pos] : 0ull;
+        const uint32_t d = (uint32_t)(w[it] >> (16 + shift)) & 0xFFu;
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit) {
+            const uint32_t bm = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bm : ~bm;
+        }
+        dig[it] = d;
+        rank[it] = __popc(peers & lt);
+        if (valid && rank[it] == 0) S.u.cnt16[d * kSortRows + it * 32 + warp] = (uint16_t)__popc(peers);
+    }
+    __syncthreads();
+    // exclusive scan of all counters, digit-major: thread t owns 16 consecutive entries
+    {
+        uint4 *base = c4 + 2 * tid;
+        uint4 q0 = base[0], q1 = base[1];
+        uint32_t v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += (v[k] & 0xFFFFu) + (v[k] >> 16);
+        uint32_t total;
+        uint32_t run = block_excl_scan(sum, S.warp_tot, total);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t lo = v[k] & 0xFFFFu, hi = v[k] >> 16;
+            const uint32_t olo = run;
+            run += lo;
+            const uint32_t ohi = run;
+            run += hi;
+            v[k] = olo | (ohi << 16);
+        }
+        base[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        base[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int pos = it * kSortThreads + tid;
+        if (pos < cnt) dst[S.u.cnt16[dig[it] * kSortRows + it * 32 + warp] + rank[it]] = w[it];
+    }
+    __syncthreads();
+}
+
+// Value of one unique key handed to a consumer: the numerator either as the
+// FP64 value of a single record or as an exact fixed-point sum.
+struct KeyVal {
+    uint64_t a, b;
+    bool fixed;
+    double num;
+    uint64_t fl;
+    int64_t fh;
+    int64_t den;
+};
+
 template <class Rec>
-__device__ __forceinline__ void collect_heads(const Rec *recs, const uint16_t *perm, int cnt, uint16_t *heads,
-                                              unsigned int *nheads)
+__device__ __forceinline__ void rec_value(const Rec &r, bool &fixed, double &num, uint64_t &fl, int64_t &fh);
+template <>
+__device__ __forceinline__ void rec_value<Rec32>(const Rec32 &r, bool &fixed, double &num, uint64_t &fl, int64_t &fh)
 {
-    const int lane = threadIdx.x & 31;
-    for (int j0 = 0; j0 < cnt; j0 += blockDim.x) {
-        const int j = j0 + threadIdx.x;
-        bool head = false;
-        if (j < cnt) {
-            const Rec &r0 = recs[perm[j]];
-            head = j == 0 || !(recs[perm[j - 1]].a == r0.a && recs[perm[j - 1]].b == r0.b);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, head);
-        unsigned base = 0;
-        if (lane == 0 && m) base = atomicAdd(nheads, (unsigned)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (head) heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
-    }
+    fixed = false;
+    num = r.num;
+    fl = 0;
+    fh = 0;
+}
+template <>
+__device__ __forceinline__ void rec_value<Rec48>(const Rec48 &r, bool &fixed, double &num, uint64_t &fl, int64_t &fh)
+{
+    fixed = true;
+    num = 0.0;
+    fl = r.fx_lo;
+    fh = r.fx_hi;
+}
+__device__ __forceinline__ void rec_add(const Rec32 &r, uint64_t &fl, int64_t &fh, uint32_t &err)
+{
+    fx_add_double(fl, fh, r.num, err);
+}
+__device__ __forceinline__ void rec_add(const Rec48 &r, uint64_t &fl, int64_t &fh, uint32_t &)
+{
+    fx_add_fx(fl, fh, r.fx_lo, r.fx_hi);
 }
 
-// Every thread finishes whole keys: a single record passes its FP64
-// numerator through; a few duplicates are summed exactly in fixed point by
-// the thread; runs longer than 32 records are queued for a whole warp.
-__device__ __forceinline__ void finish_heads(const TileParams &p, const Rec32 *recs, const uint16_t *perm, int cnt,
-                                             const uint16_t *heads, int nh, uint16_t *longq, unsigned int *nlong,
-                                             const uint64_t *rk, unsigned long long nrk, KeyStats &st)
+// Sort the chunk and hand every unique key to `emit` (any order; every thread
+// may call it).  Returns false, for all threads, if two different keys share
+// a hash; then nothing was emitted and the caller must use the exact path.
+template <class Rec, class Emit>
+__device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_t &err, Emit &&emit)
 {
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        const int j = heads[h];
-        const Rec32 &r0 = recs[perm[j]];
-        double num = r0.num;
-        int64_t den = r0.den;
-        if (j + 1 < cnt) {
-            const Rec32 &r1 = recs[perm[j + 1]];
-            if (r1.a == r0.a && r1.b == r0.b) {
-                if (j + 32 < cnt) {
-                    const Rec32 &rl = recs[perm[j + 32]];
-                    if (rl.a == r0.a && rl.b == r0.b) {  // long run: a warp takes it
-                        longq[atomicAdd(nlong, 1u)] = (uint16_t)j;
-                        continue;
-                    }
-                }
-                uint64_t fl = 0;
-                int64_t fh = 0;
-                fx_add_double(fl, fh, r0.num, st.err);
-                for (int k = j + 1; k < cnt; ++k) {
-                    const Rec32 &r2 = recs[perm[k]];
-                    if (r2.a != r0.a || r2.b != r0.b) break;
-                    fx_add_double(fl, fh, r2.num, st.err);
-                    den = r2.den < den ? r2.den : den;
-                }
-                num = fx_to_double(fl, fh);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint64_t *A = S.words[0], *B = S.words[1];
+    if (tid == 0) {
+        S.nheads = 0;
+        S.nlong = 0;
+        S.collision = 0;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int pos = it * kSortThreads + tid;
+        if (pos < cnt) A[pos] = ((uint64_t)key_hash32(recs[pos].a, recs[pos].b) << 16) | (uint64_t)pos;
+    }
+    __syncthreads();
+    lsd_pass(A, B, cnt, 0, S);
+    lsd_pass(B, A, cnt, 8, S);
+    lsd_pass(A, B, cnt, 16, S);
+    lsd_pass(B, A, cnt, 24, S);
+    // heads of equal-hash runs; a run must also hold a single 128-bit key
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int pos = it * kSortThreads + tid;
+        bool head = false;
+        if (pos < cnt) {
+            const uint64_t wv = A[pos];
+            head = pos == 0 || (A[pos - 1] >> 16) != (wv >> 16);
+            if (!head) {
+                const Rec &r0 = recs[wv & 0xFFFF], &rp = recs[A[pos - 1] & 0xFFFF];
+                if (r0.a != rp.a || r0.b != rp.b) S.collision = 1;
             }
         }
-        finish_key(p, rk, nrk, r0.a, r0.b, num, den, st);
+        const uint32_t m = __ballot_sync(0xffffffffu, head);
+        uint32_t base = 0;
+        if (lane == 0 && m) base = atomicAdd(&S.nheads, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (head) S.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
     }
-}
-
-// A warp sums one long run of equal keys: lanes stride over the records,
-// the exact 128-bit partial sums are combined by shuffles.
-__device__ __forceinline__ void finish_long(const TileParams &p, const Rec32 *recs, const uint16_t *perm, int cnt,
-                                            const uint16_t *longq, int nl, const uint64_t *rk,
-                                            unsigned long long nrk, KeyStats &st)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int q = warp; q < nl; q += nw) {
-        const int j = longq[q];
-        const uint64_t ka = recs[perm[j]].a, kb = recs[perm[j]].b;
+    __syncthreads();
+    if (S.collision) return false;
+    const int nh = (int)S.nheads;
+    for (int h = tid; h < nh; h += kSortThreads) {
+        const int j = S.heads[h];
+        const uint64_t hj = A[j] >> 16;
+        const Rec &r0 = recs[A[j] & 0xFFFF];
+        KeyVal v;
+        v.a = r0.a;
+        v.b = r0.b;
+        v.den = r0.den;
+        rec_value(r0, v.fixed, v.num, v.fl, v.fh);
+        if (j + 1 < cnt && (A[j + 1] >> 16) == hj) {
+            if (j + kLongRun < cnt && (A[j + kLongRun] >> 16) == hj) {
+                S.longq[atomicAdd(&S.nlong, 1u)] = (uint16_t)j;
+                continue;
+            }
+            uint64_t fl = 0;
+            int64_t fh = 0;
+            rec_add(r0, fl, fh, err);
+            for (int k = j + 1; k < cnt && (A[k] >> 16) == hj; ++k) {
+                const Rec &r2 = recs[A[k] & 0xFFFF];
+                rec_add(r2, fl, fh, err);
+                v.den = r2.den < v.den ? r2.den : v.den;
+            }
+            v.fixed = true;
+            v.fl = fl;
+            v.fh = fh;
+        }
+        emit(v);
+    }
+    __syncthreads();
+    const int nl = (int)S.nlong;
+    for (int q = warp; q < nl; q += kSortThreads / 32) {
+        const int j = S.longq[q];
+        const uint64_t hj = A[j] >> 16;
         uint64_t fl = 0;
         int64_t fh = 0;
-        int64_t den = recs[perm[j]].den;
+        int64_t den = recs[A[j] & 0xFFFF].den;
         for (int base = j; base < cnt; base += 32) {
             const int k = base + lane;
-            bool same = false;
-            if (k < cnt) {
-                const Rec32 &r = recs[perm[k]];
-                same = r.a == ka && r.b == kb;
-                if (same) {
-                    fx_add_double(fl, fh, r.num, st.err);
-                    den = r.den < den ? r.den : den;
-                }
+            const bool same = k < cnt && (A[k] >> 16) == hj;
+            if (same) {
+                const Rec &r = recs[A[k] & 0xFFFF];
+                rec_add(r, fl, fh, err);
+                den = r.den < den ? r.den : den;
             }
             if (__ballot_sync(0xffffffffu, same) != 0xffffffffu) break;
         }
@@ -1276,24 +1419,83 @@ __device__ __forceinline__ void finish_long(const TileParams &p, const Rec32 *re
             fx_add_fx(fl, fh, olo, ohi);
             den = od < den ? od : den;
         }
-        if (lane == 0) finish_key(p, rk, nrk, ka, kb, fx_to_double(fl, fh), den, st);
+        if (lane == 0) {
+            const Rec &r0 = recs[A[j] & 0xFFFF];
+            KeyVal v;
+            v.a = r0.a;
+            v.b = r0.b;
+            v.fixed = true;
+            v.num = 0.0;
+            v.fl = fl;
+            v.fh = fh;
+            v.den = den;
+            emit(v);
+        }
     }
+    __syncthreads();
+    return true;
+}
+
+// Exact fallback for a chunk whose hash compression collided: bucket the keys
+// by a second hash and insertion-sort each bucket by the full key (slow, and
+// only reached with probability ~cnt^2 / 2^33 per chunk).
+template <class Rec, class Emit>
+__device__ void exact_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_t &err, Emit &&emit)
+{
+    uint16_t *perm = reinterpret_cast<uint16_t *>(S.words[0]);
+    uint16_t *rnk = reinterpret_cast<uint16_t *>(S.words[0]) + kSortCap;
+    uint16_t *bkt = reinterpret_cast<uint16_t *>(S.words[0]) + 2 * kSortCap;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(S.words[1]);
+    for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    auto key = [&](int i, uint64_t &a, uint64_t &b) {
+        a = recs[i].a;
+        b = recs[i].b;
+    };
+    group_keys(cnt, kSortCap, key, perm, rnk, bkt, hist, S.warp_tot, &S.nlong);
+    const int nt = blockDim.x;
+    const int chunk = (cnt + nt - 1) / nt;
+    const int s = threadIdx.x * chunk, e = min(cnt, s + chunk);
+    for (int j = s; j < e; ++j) {
+        const Rec &r0 = recs[perm[j]];
+        if (j > 0) {
+            const Rec &rp = recs[perm[j - 1]];
+            if (rp.a == r0.a && rp.b == r0.b) continue;
+        }
+        KeyVal v;
+        v.a = r0.a;
+        v.b = r0.b;
+        v.fixed = true;
+        v.num = 0.0;
+        v.fl = 0;
+        v.fh = 0;
+        v.den = r0.den;
+        for (int k = j; k < cnt; ++k) {
+            const Rec &r2 = recs[perm[k]];
+            if (k > j && (r2.a != r0.a || r2.b != r0.b)) break;
+            rec_add(r2, v.fl, v.fh, err);
+            v.den = r2.den < v.den ? r2.den : v.den;
+        }
+        emit(v);
+    }
+    __syncthreads();
+}
+
+// One unique key into the statistics (filter + Eq. 3 term).
+__device__ __forceinline__ void finish_keyval(const TileParams &p, const uint64_t *rk, unsigned long long nrk,
+                                              const KeyVal &v, KeyStats &st)
+{
+    finish_key(p, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
 }
 
 // Shared memory of the main tile kernel: two record buffers (the next tile is
-// fetched by TMA while the current one is grouped).
+// fetched by TMA while the current one is sorted and reduced).
 struct MainSmem {
     Rec32 recs[2][kTileCap];
-    uint16_t perm[kTileCap], rnk[kTileCap], bkt[kTileCap];
-    union {
-        uint32_t hist[kTileBuckets];
-        unsigned long long red[10][32];
-    } u;
+    SortSmem S;
     uint64_t rk[2 * kRefSliceSmem];
     unsigned long long meta[4];  // current tile: offset, count, reference offset, reference count
     uint64_t bar[2];
-    unsigned int nheads, nlong, nbig;
-    uint32_t warp_tot[32];
 };
 
 size_t tile_smem_bytes() { return sizeof(MainSmem); }
@@ -1321,6 +1523,13 @@ __device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, con
     bulk_load(M.recs[buf], p.recs + m.off, (uint32_t)(m.cnt * sizeof(Rec32)), &M.bar[buf]);
 }
 
+__device__ __forceinline__ void push_oversize(const TileParams &p, uint64_t t, unsigned long long cnt)
+{
+    const unsigned idx = atomicAdd(&p.acc->n_big, 1u);
+    p.big_list[idx] = (uint32_t)t;
+    atomicMax(&p.acc->big_max, cnt);
+}
+
 // Persistent: CTA g handles tiles g, g + G, g + 2G, ...  Thread 0 keeps the
 // tile metadata two tiles ahead and the record load one tile ahead.
 __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams p)
@@ -1330,7 +1539,6 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams 
     const uint64_t G = gridDim.x;
     KeyStats st;
     st.clear();
-    for (int i = threadIdx.x; i < kTileBuckets; i += blockDim.x) M.u.hist[i] = 0;
     TileMeta nx{0, 0, 0, 0};
     if (threadIdx.x == 0) {
         mbar_init(&M.bar[0], 1);
@@ -1356,36 +1564,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams 
             nnx = tile_meta(p, t + 2 * G);  // consumed at the end of this iteration
         }
         if (cntl > (unsigned long long)kTileCap) {
-            if (threadIdx.x == 0) {
-                const unsigned idx = atomicAdd(&p.acc->n_big, 1u);
-                p.big_list[idx] = (uint32_t)t;
-                atomicMax(&p.acc->big_max, cntl);
-            }
+            if (threadIdx.x == 0) push_oversize(p, t, cntl);
         } else if (cntl > 0) {
             const int cnt = (int)cntl;
             const uint64_t *rk = M.rk;
             if (rcnt <= (unsigned long long)kRefSliceSmem) {
-                for (unsigned long long i = threadIdx.x; i < 2 * rcnt; i += blockDim.x) M.rk[i] = p.ref_keys[2 * roff + i];
+                for (unsigned long long i = threadIdx.x; i < 2 * rcnt; i += blockDim.x)
+                    M.rk[i] = p.ref_keys[2 * roff + i];
             } else {
                 rk = p.ref_keys + 2 * roff;
             }
             mbar_wait_bounded(&M.bar[buf], (phases >> buf) & 1u, p.err);
             phases ^= 1u << buf;
-            const Rec32 *recs = M.recs[buf];
-            auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                a = recs[i].a;
-                b = recs[i].b;
-            };
-            if (threadIdx.x == 0) {
-                M.nheads = 0;
-                M.nlong = 0;
-            }
-            group_keys(cnt, kTileBuckets, key, M.perm, M.rnk, M.bkt, M.u.hist, M.warp_tot, &M.nbig);
-            collect_heads(recs, M.perm, cnt, M.rnk, &M.nheads);  // rnk is free after grouping
-            __syncthreads();
-            finish_heads(p, recs, M.perm, cnt, M.rnk, (int)M.nheads, M.bkt, &M.nlong, rk, rcnt, st);
-            __syncthreads();
-            finish_long(p, recs, M.perm, cnt, M.bkt, (int)M.nlong, rk, rcnt, st);
+            const bool ok = sort_reduce_chunk(M.recs[buf], cnt, M.S, st.err,
+                                              [&](const KeyVal &v) { finish_keyval(p, rk, rcnt, v, st); });
+            if (!ok && threadIdx.x == 0) push_oversize(p, t, cntl);  // exact path for a hash collision
         }
         if (threadIdx.x == 0) {
             M.meta[0] = nx.off;
@@ -1394,9 +1587,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams 
             M.meta[3] = nx.rcnt;
             nx = nnx;
         }
-        __syncthreads();  // buffer, perm, slice and metadata ready for the next tile
+        __syncthreads();  // buffer, slice and metadata ready for the next tile
     }
-    flush_stats(p, st, M.u.red);
+    flush_stats(p, st, M.S.u.red);
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_inval(&M.bar[0]);
@@ -1417,67 +1610,46 @@ cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 
 // ------------------------------------------------------ oversize tiles
 
-// Chunked grouping for tiles above shared-memory capacity: every chunk is
-// grouped in shared memory and reduced to (key, exact fixed-point numerator,
-// min denominator) records; the reduced list is regrouped until it fits, then
-// finished like a normal tile.  Exact sums make the result independent of
-// the chunking.
-constexpr int kBigIdx = kTileCap > kBigCap ? kTileCap : kBigCap;
-static_assert(kBigBuckets * 2 >= kBigIdx, "oversize buckets must cover half a chunk");
-static_assert(kBigBuckets <= 4 * kBigThreads && kTileBuckets <= 4 * kTileThreads, "block scan capacity");
-static_assert(kTileBuckets * 2 >= kTileCap, "tile buckets must cover half a tile");
-
+// Tiles above shared-memory capacity (keys with many duplicates, or a tile
+// whose hash compression collided): each chunk is sorted and reduced to
+// (key, exact fixed-point numerator, min denominator) records; the reduced
+// list is processed again until it fits one chunk, then finished like a
+// normal tile.  Exact sums make the result independent of the chunking.
 struct BigSmem {
     union {
         Rec32 r32[kTileCap];
         Rec48 r48[kBigCap];
     } u;
-    // index arrays cover the larger of a Rec32 chunk and a Rec48 chunk
-    uint16_t perm[kBigIdx], rnk[kBigIdx], bkt[kBigIdx];
-    uint32_t hist[kBigBuckets];
+    SortSmem S;
     uint64_t rk[2 * kRefSliceSmem];
     uint64_t bar;
-    unsigned int out_count, nbig;
-    uint32_t warp_tot[32];
-    unsigned long long red[10][32];
+    unsigned int out_count;
 };
 
 size_t big_smem_bytes() { return sizeof(BigSmem); }
 
-// Reduce grouped records of one chunk into Rec48 entries appended to dst.
-template <class Rec, bool kFixed>
-__device__ void chunk_to_partials(const Rec *recs, const uint16_t *perm, int m, Rec48 *dst, unsigned int *count,
-                                  uint32_t &err)
+template <class Rec>
+__device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst, uint32_t &err)
 {
-    const int nt = blockDim.x;
-    const int chunk = (m + nt - 1) / nt;
-    const int s = threadIdx.x * chunk, e = min(m, s + chunk);
-    for (int j = s; j < e; ++j) {
-        const Rec &r0 = recs[perm[j]];
-        if (j > 0) {
-            const Rec &rp = recs[perm[j - 1]];
-            if (rp.a == r0.a && rp.b == r0.b) continue;
-        }
-        uint64_t fl = 0;
-        int64_t fh = 0;
-        int64_t den = r0.den;
-        for (int k = j; k < m; ++k) {
-            const Rec &r2 = recs[perm[k]];
-            if (k > j && (r2.a != r0.a || r2.b != r0.b)) break;
-            if constexpr (kFixed) fx_add_fx(fl, fh, r2.fx_lo, r2.fx_hi);
-            else fx_add_double(fl, fh, r2.num, err);
-            den = r2.den < den ? r2.den : den;
-        }
-        unsigned int slot = atomicAdd(count, 1u);
+    auto put = [&](const KeyVal &v) {
         Rec48 o;
-        o.a = r0.a;
-        o.b = r0.b;
-        o.fx_lo = fl;
-        o.fx_hi = fh;
-        o.den = den;
+        o.a = v.a;
+        o.b = v.b;
+        if (v.fixed) {
+            o.fx_lo = v.fl;
+            o.fx_hi = v.fh;
+        } else {
+            uint64_t fl = 0;
+            int64_t fh = 0;
+            fx_add_double(fl, fh, v.num, err);
+            o.fx_lo = fl;
+            o.fx_hi = fh;
+        }
+        o.den = v.den;
         o.pad = 0;
-        dst[slot] = o;
-    }
+        dst[atomicAdd(&M.out_count, 1u)] = o;
+    };
+    if (!sort_reduce_chunk(recs, m, M.S, err, put)) exact_reduce_chunk(recs, m, M.S, err, put);
 }
 
 __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TileParams p)
@@ -1490,7 +1662,6 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
     KeyStats st;
     st.clear();
     uint32_t phase = 0;
-    for (int i = threadIdx.x; i < kBigBuckets; i += blockDim.x) M.hist[i] = 0;
     if (threadIdx.x == 0) mbar_init(&M.bar, 1);
     __syncthreads();
     const int nt = blockDim.x;
@@ -1515,14 +1686,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
             mbar_wait_bounded(&M.bar, phase, p.err);
             phase ^= 1;
             __syncthreads();
-            const Rec32 *recs = M.u.r32;
-            auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                a = recs[i].a;
-                b = recs[i].b;
-            };
-            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.bkt, M.hist, M.warp_tot, &M.nbig);
-            chunk_to_partials<Rec32, false>(recs, M.perm, m, bufA + u, &M.out_count, st.err);
-            __syncthreads();
+            chunk_to_partials(M.u.r32, m, M, bufA + u, st.err);
             u += M.out_count;
             __syncthreads();
         }
@@ -1535,14 +1699,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
                 if (threadIdx.x == 0) M.out_count = 0;
                 for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[cs + i];
                 __syncthreads();
-                const Rec48 *recs = M.u.r48;
-                auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                    a = recs[i].a;
-                    b = recs[i].b;
-                };
-                group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.bkt, M.hist, M.warp_tot, &M.nbig);
-                chunk_to_partials<Rec48, true>(recs, M.perm, m, dst + u2, &M.out_count, st.err);
-                __syncthreads();
+                chunk_to_partials(M.u.r48, m, M, dst + u2, st.err);
                 u2 += M.out_count;
                 __syncthreads();
             }
@@ -1556,24 +1713,19 @@ __global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TilePara
             dst = tmp;
             u = u2;
         }
-        // final grouping and the energy
+        // final sort-reduce and the energy
         unsigned long long nrk;
         const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
         if (!bad) {
             const int m = (int)u;
             for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
             __syncthreads();
-            const Rec48 *recs = M.u.r48;
-            auto key = [&](int i, uint64_t &a, uint64_t &b) {
-                a = recs[i].a;
-                b = recs[i].b;
-            };
-            group_keys(m, kBigBuckets, key, M.perm, M.rnk, M.bkt, M.hist, M.warp_tot, &M.nbig);
-            reduce_groups<Rec48, true>(p, recs, M.perm, m, rk, nrk, st);
+            auto fin = [&](const KeyVal &v) { finish_keyval(p, rk, nrk, v, st); };
+            if (!sort_reduce_chunk(M.u.r48, m, M.S, st.err, fin)) exact_reduce_chunk(M.u.r48, m, M.S, st.err, fin);
         }
         __syncthreads();
     }
-    flush_stats(p, st, M.red);
+    flush_stats(p, st, M.S.u.red);
     __syncthreads();
     if (threadIdx.x == 0) mbar_inval(&M.bar);
 }
