@@ -248,7 +248,7 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     if (opts_in) o = *opts_in;
     if (o.constraint_mod > 1 && o.constraint_rem >= o.constraint_mod)
         return fail(c, PT2_ERR_INVALID, "constraint_rem must be below constraint_mod");
-    uint64_t tile_target = o.tile_target ? o.tile_target : 1536;
+    uint64_t tile_target = o.tile_target ? o.tile_target : 1152;
     if (tile_target > (uint64_t)kTileCap) return fail(c, PT2_ERR_INVALID, "tile_target above %d", kTileCap);
     const bool prof = (o.flags & PT2_FLAG_PROFILE) != 0;
     cudaStream_t st = c->stream;

@@ -1165,11 +1165,14 @@ __device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint6
 // 128-bit key (a hash collision makes the chunk fall back to an exact path)
 // and reduced by key.
 
-constexpr int kSortThreads = 1024;
+constexpr int kSortThreads = kTileThreads;
 constexpr int kSortItems = kSortCap / kSortThreads;   // items per thread, striped
 constexpr int kSortRows = kSortItems * (kSortThreads / 32);
+constexpr int kCountersPerThread = 256 * kSortRows / kSortThreads;  // scanned by each thread
 constexpr int kLongRun = 8;                            // longer runs are summed by a warp
-static_assert(kSortItems == 2, "the sort is written for two items per thread");
+static_assert(kSortItems * kSortThreads == kSortCap, "the sort holds whole items per thread");
+static_assert(kCountersPerThread % 8 == 0, "counters are scanned in 16-byte groups");
+static_assert(kBigThreads == kSortThreads, "every sorting CTA has the sort's width");
 
 struct SortSmem {
     uint64_t words[2][kSortCap];  // (hash << 16) | record index
@@ -1192,10 +1195,10 @@ __device__ __forceinline__ uint32_t key_hash32(uint64_t a, uint64_t b)
     return (uint32_t)(h >> 32);
 }
 
-// Exclusive scan of one value per thread over the block (1024 threads).
+// Exclusive scan of one value per thread over the block.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t &total)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint32_t incl = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -1205,14 +1208,14 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const uint32_t w = warp_tot[lane];
+        const uint32_t w = lane < nw ? warp_tot[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, wi, off);
             if (lane >= off) wi += t;
         }
-        warp_tot[lane] = wi - w;
+        if (lane < nw) warp_tot[lane] = wi - w;
         if (lane == 31) warp_tot[32] = wi;
     }
     __syncthreads();
@@ -1221,9 +1224,9 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
 }
 
 // One stable counting-sort pass on the 8-bit digit at `shift` of the hash.
-// Positions are striped: item it of thread t is position it * 1024 + t, and
-// row it * 32 + warp counts the items of one warp at one item index, so rows
-// in order cover positions in order.
+// Positions are striped: item it of thread t is position it * T + t (T
+// threads), and row it * T/32 + warp counts the items of one warp at one item
+// index, so rows in order cover positions in order.
 __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int cnt, int shift, SortSmem &S)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1248,21 +1251,30 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
         }
         dig[it] = d;
         rank[it] = __popc(peers & lt);
-        if (valid && rank[it] == 0) S.u.cnt16[d * kSortRows + it * 32 + warp] = (uint16_t)__popc(peers);
+        if (valid && rank[it] == 0) S.u.cnt16[d * kSortRows + it * (kSortThreads / 32) + warp] = (uint16_t)__popc(peers);
     }
     __syncthreads();
-    // exclusive scan of all counters, digit-major: thread t owns 16 consecutive entries
+    // exclusive scan of all counters, digit-major: each thread owns
+    // kCountersPerThread consecutive entries
     {
-        uint4 *base = c4 + 2 * tid;
-        uint4 q0 = base[0], q1 = base[1];
-        uint32_t v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        constexpr int nq = kCountersPerThread / 8;
+        uint4 *base = c4 + nq * tid;
+        uint32_t v[4 * nq];
+#pragma unroll
+        for (int q = 0; q < nq; ++q) {
+            const uint4 x = base[q];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
         uint32_t sum = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sum += (v[k] & 0xFFFFu) + (v[k] >> 16);
+        for (int k = 0; k < 4 * nq; ++k) sum += (v[k] & 0xFFFFu) + (v[k] >> 16);
         uint32_t total;
         uint32_t run = block_excl_scan(sum, S.warp_tot, total);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 4 * nq; ++k) {
             const uint32_t lo = v[k] & 0xFFFFu, hi = v[k] >> 16;
             const uint32_t olo = run;
             run += lo;
@@ -1270,14 +1282,14 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
             run += hi;
             v[k] = olo | (ohi << 16);
         }
-        base[0] = make_uint4(v[0], v[1], v[2], v[3]);
-        base[1] = make_uint4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+        for (int q = 0; q < nq; ++q) base[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const int pos = it * kSortThreads + tid;
-        if (pos < cnt) dst[S.u.cnt16[dig[it] * kSortRows + it * 32 + warp] + rank[it]] = w[it];
+        if (pos < cnt) dst[S.u.cnt16[dig[it] * kSortRows + it * (kSortThreads / 32) + warp] + rank[it]] = w[it];
     }
     __syncthreads();
 }
@@ -1488,10 +1500,10 @@ __device__ __forceinline__ void finish_keyval(const TileParams &p, const uint64_
     finish_key(p, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
 }
 
-// Shared memory of the main tile kernel: two record buffers (the next tile is
-// fetched by TMA while the current one is sorted and reduced).
+// Shared memory of the main tile kernel (two CTAs share an SM, so one CTA's
+// tile load and barriers overlap the other's work).
 struct MainSmem {
-    Rec32 recs[2][kTileCap];
+    Rec32 recs[kTileCap];
     SortSmem S;
     uint64_t rk[2 * kRefSliceSmem];
     unsigned long long meta[4];  // current tile: offset, count, reference offset, reference count
@@ -1516,11 +1528,11 @@ __device__ __forceinline__ TileMeta tile_meta(const TileParams &p, uint64_t t)
     return m;
 }
 
-__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, const TileMeta &m, int buf)
+__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, const TileMeta &m)
 {
     if (m.cnt == 0 || m.cnt > (unsigned long long)kTileCap) return;
     fence_proxy_async_smem();
-    bulk_load(M.recs[buf], p.recs + m.off, (uint32_t)(m.cnt * sizeof(Rec32)), &M.bar[buf]);
+    bulk_load(M.recs, p.recs + m.off, (uint32_t)(m.cnt * sizeof(Rec32)), &M.bar[0]);
 }
 
 __device__ __forceinline__ void push_oversize(const TileParams &p, uint64_t t, unsigned long long cnt)
@@ -1531,8 +1543,8 @@ __device__ __forceinline__ void push_oversize(const TileParams &p, uint64_t t, u
 }
 
 // Persistent: CTA g handles tiles g, g + G, g + 2G, ...  Thread 0 keeps the
-// tile metadata two tiles ahead and the record load one tile ahead.
-__global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams p)
+// tile metadata one tile ahead, so each tile's TMA load starts at once.
+__global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
@@ -1542,27 +1554,21 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams 
     TileMeta nx{0, 0, 0, 0};
     if (threadIdx.x == 0) {
         mbar_init(&M.bar[0], 1);
-        mbar_init(&M.bar[1], 1);
-        const TileMeta m0 = tile_meta(p, blockIdx.x);
-        nx = tile_meta(p, blockIdx.x + G);
-        issue_tile(p, M, m0, 0);
-        M.meta[0] = m0.off;
-        M.meta[1] = m0.cnt;
-        M.meta[2] = m0.roff;
-        M.meta[3] = m0.rcnt;
+        nx = tile_meta(p, blockIdx.x);
     }
-    __syncthreads();
-    uint32_t phases = 0;  // bit b: parity of the next phase of buffer b
-    int k = 0;
-    for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G, ++k) {
-        const int buf = k & 1;
+    uint32_t phase = 0;
+    for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G) {
+        if (threadIdx.x == 0) {
+            issue_tile(p, M, nx);
+            M.meta[0] = nx.off;
+            M.meta[1] = nx.cnt;
+            M.meta[2] = nx.roff;
+            M.meta[3] = nx.rcnt;
+            nx = tile_meta(p, t + G);  // consumed next iteration
+        }
+        __syncthreads();
         const unsigned long long cntl = M.meta[1];
         const unsigned long long roff = M.meta[2], rcnt = M.meta[3];
-        TileMeta nnx{0, 0, 0, 0};
-        if (threadIdx.x == 0) {
-            issue_tile(p, M, nx, buf ^ 1);
-            nnx = tile_meta(p, t + 2 * G);  // consumed at the end of this iteration
-        }
         if (cntl > (unsigned long long)kTileCap) {
             if (threadIdx.x == 0) push_oversize(p, t, cntl);
         } else if (cntl > 0) {
@@ -1574,27 +1580,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileParams 
             } else {
                 rk = p.ref_keys + 2 * roff;
             }
-            mbar_wait_bounded(&M.bar[buf], (phases >> buf) & 1u, p.err);
-            phases ^= 1u << buf;
-            const bool ok = sort_reduce_chunk(M.recs[buf], cnt, M.S, st.err,
+            mbar_wait_bounded(&M.bar[0], phase, p.err);
+            phase ^= 1u;
+            const bool ok = sort_reduce_chunk(M.recs, cnt, M.S, st.err,
                                               [&](const KeyVal &v) { finish_keyval(p, rk, rcnt, v, st); });
             if (!ok && threadIdx.x == 0) push_oversize(p, t, cntl);  // exact path for a hash collision
         }
-        if (threadIdx.x == 0) {
-            M.meta[0] = nx.off;
-            M.meta[1] = nx.cnt;
-            M.meta[2] = nx.roff;
-            M.meta[3] = nx.rcnt;
-            nx = nnx;
-        }
-        __syncthreads();  // buffer, slice and metadata ready for the next tile
+        __syncthreads();  // records, slice and metadata free for the next tile
     }
     flush_stats(p, st, M.S.u.red);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_inval(&M.bar[0]);
-        mbar_inval(&M.bar[1]);
-    }
+    if (threadIdx.x == 0) mbar_inval(&M.bar[0]);
 }
 
 cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
