@@ -1181,6 +1181,7 @@ struct SortSmem {
         unsigned long long red[10][32];   // final statistics reduction
     } u;
     uint16_t heads[kSortCap], longq[kSortCap];
+    uint16_t dbase[256];
     uint32_t warp_tot[33];
     unsigned int nheads, nlong, collision;
 };
@@ -1226,10 +1227,13 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_t
 // One stable counting-sort pass on the 8-bit digit at `shift` of the hash.
 // Positions are striped: item it of thread t is position it * T + t (T
 // threads), and row it * T/32 + warp counts the items of one warp at one item
-// index, so rows in order cover positions in order.
+// index, so rows in order cover positions in order.  Ranks within a warp come
+// from __match_any_sync; 256 threads then scan the rows of one digit each and
+// a 256-entry scan gives the digit bases.
 __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int cnt, int shift, SortSmem &S)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kSortThreads / 32;
     uint4 *c4 = reinterpret_cast<uint4 *>(S.u.cnt16);
     constexpr int n4 = 256 * kSortRows * 2 / 16;
     for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0, 0, 0, 0);
@@ -1243,53 +1247,57 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
         const bool valid = pos < cnt;
         w[it] = valid ? src[pos] : 0ull;
         const uint32_t d = (uint32_t)(w[it] >> (16 + shift)) & 0xFFu;
-        uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-        for (int bit = 0; bit < 8; ++bit) {
-            const uint32_t bm = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
-            peers &= ((d >> bit) & 1u) ? bm : ~bm;
-        }
+        // past-the-end lanes get a value no real digit has, so they match nobody
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
         dig[it] = d;
         rank[it] = __popc(peers & lt);
-        if (valid && rank[it] == 0) S.u.cnt16[d * kSortRows + it * (kSortThreads / 32) + warp] = (uint16_t)__popc(peers);
+        if (valid && rank[it] == 0) S.u.cnt16[d * kSortRows + it * kWarps + warp] = (uint16_t)__popc(peers);
     }
     __syncthreads();
-    // exclusive scan of all counters, digit-major: each thread owns
-    // kCountersPerThread consecutive entries
-    {
-        constexpr int nq = kCountersPerThread / 8;
-        uint4 *base = c4 + nq * tid;
-        uint32_t v[4 * nq];
+    // per digit: exclusive scan over its rows (vector loads), then the digit totals
+    uint32_t total_d = 0;
+    constexpr int nq = kSortRows * 2 / 16;  // uint4 per digit column
+    static_assert(kSortRows % 8 == 0, "a digit's rows fill whole 16-byte groups");
+    if (tid < 256) {
+        uint4 *col = c4 + tid * nq;
+        uint32_t run = 0;
 #pragma unroll
         for (int q = 0; q < nq; ++q) {
-            const uint4 x = base[q];
-            v[4 * q] = x.x;
-            v[4 * q + 1] = x.y;
-            v[4 * q + 2] = x.z;
-            v[4 * q + 3] = x.w;
+            uint4 x = col[q];
+            uint32_t v[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t lo = v[k] & 0xFFFFu, hi = v[k] >> 16;
+                const uint32_t olo = run;
+                run += lo;
+                v[k] = olo | (run << 16);
+                run += hi;
+            }
+            col[q] = make_uint4(v[0], v[1], v[2], v[3]);
         }
-        uint32_t sum = 0;
+        total_d = run;
+    }
+    {
+        uint32_t incl = total_d;
 #pragma unroll
-        for (int k = 0; k < 4 * nq; ++k) sum += (v[k] & 0xFFFFu) + (v[k] >> 16);
-        uint32_t total;
-        uint32_t run = block_excl_scan(sum, S.warp_tot, total);
-#pragma unroll
-        for (int k = 0; k < 4 * nq; ++k) {
-            const uint32_t lo = v[k] & 0xFFFFu, hi = v[k] >> 16;
-            const uint32_t olo = run;
-            run += lo;
-            const uint32_t ohi = run;
-            run += hi;
-            v[k] = olo | (ohi << 16);
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
         }
-#pragma unroll
-        for (int q = 0; q < nq; ++q) base[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        if (lane == 31 && warp < 8) S.warp_tot[warp] = incl;
+        __syncthreads();
+        if (tid < 256) {
+            uint32_t base = 0;
+            for (int k = 0; k < warp; ++k) base += S.warp_tot[k];
+            S.dbase[tid] = (uint16_t)(base + incl - total_d);
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const int pos = it * kSortThreads + tid;
-        if (pos < cnt) dst[S.u.cnt16[dig[it] * kSortRows + it * (kSortThreads / 32) + warp] + rank[it]] = w[it];
+        if (pos < cnt)
+            dst[S.dbase[dig[it]] + S.u.cnt16[dig[it] * kSortRows + it * kWarps + warp] + rank[it]] = w[it];
     }
     __syncthreads();
 }
@@ -1351,50 +1359,64 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
         if (pos < cnt) A[pos] = ((uint64_t)key_hash32(recs[pos].a, recs[pos].b) << 16) | (uint64_t)pos;
     }
     __syncthreads();
+    // three digit passes order the words by the low 24 hash bits; a fourth
+    // (the top 8 bits) runs only if two different keys share those 24 bits
     lsd_pass(A, B, cnt, 0, S);
     lsd_pass(B, A, cnt, 8, S);
     lsd_pass(A, B, cnt, 16, S);
-    lsd_pass(B, A, cnt, 24, S);
-    // heads of equal-hash runs; a run must also hold a single 128-bit key
+    uint64_t hmask = 0xFFFFFFull << 16;
+    A = S.words[1];
+    for (int round = 0; round < 2; ++round) {
+        // heads of equal-hash runs; a run must also hold a single 128-bit key
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = it * kSortThreads + tid;
-        bool head = false;
-        if (pos < cnt) {
-            const uint64_t wv = A[pos];
-            head = pos == 0 || (A[pos - 1] >> 16) != (wv >> 16);
-            if (!head) {
-                const Rec &r0 = recs[wv & 0xFFFF], &rp = recs[A[pos - 1] & 0xFFFF];
-                if (r0.a != rp.a || r0.b != rp.b) S.collision = 1;
+        for (int it = 0; it < kSortItems; ++it) {
+            const int pos = it * kSortThreads + tid;
+            bool head = false;
+            if (pos < cnt) {
+                const uint64_t wv = A[pos];
+                head = pos == 0 || (A[pos - 1] & hmask) != (wv & hmask);
+                if (!head) {
+                    const Rec &r0 = recs[wv & 0xFFFF], &rp = recs[A[pos - 1] & 0xFFFF];
+                    if (r0.a != rp.a || r0.b != rp.b) S.collision = 1;
+                }
             }
+            const uint32_t m = __ballot_sync(0xffffffffu, head);
+            uint32_t base = 0;
+            if (lane == 0 && m) base = atomicAdd(&S.nheads, (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (head) S.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
         }
-        const uint32_t m = __ballot_sync(0xffffffffu, head);
-        uint32_t base = 0;
-        if (lane == 0 && m) base = atomicAdd(&S.nheads, (unsigned)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (head) S.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
+        __syncthreads();
+        if (!S.collision) break;
+        if (round == 1) return false;
+        __syncthreads();
+        if (tid == 0) {
+            S.nheads = 0;
+            S.collision = 0;
+        }
+        lsd_pass(S.words[1], S.words[0], cnt, 24, S);
+        A = S.words[0];
+        hmask = 0xFFFFFFFFull << 16;
     }
-    __syncthreads();
-    if (S.collision) return false;
     const int nh = (int)S.nheads;
     for (int h = tid; h < nh; h += kSortThreads) {
         const int j = S.heads[h];
-        const uint64_t hj = A[j] >> 16;
+        const uint64_t hj = A[j] & hmask;
         const Rec &r0 = recs[A[j] & 0xFFFF];
         KeyVal v;
         v.a = r0.a;
         v.b = r0.b;
         v.den = r0.den;
         rec_value(r0, v.fixed, v.num, v.fl, v.fh);
-        if (j + 1 < cnt && (A[j + 1] >> 16) == hj) {
-            if (j + kLongRun < cnt && (A[j + kLongRun] >> 16) == hj) {
+        if (j + 1 < cnt && (A[j + 1] & hmask) == hj) {
+            if (j + kLongRun < cnt && (A[j + kLongRun] & hmask) == hj) {
                 S.longq[atomicAdd(&S.nlong, 1u)] = (uint16_t)j;
                 continue;
             }
             uint64_t fl = 0;
             int64_t fh = 0;
             rec_add(r0, fl, fh, err);
-            for (int k = j + 1; k < cnt && (A[k] >> 16) == hj; ++k) {
+            for (int k = j + 1; k < cnt && (A[k] & hmask) == hj; ++k) {
                 const Rec &r2 = recs[A[k] & 0xFFFF];
                 rec_add(r2, fl, fh, err);
                 v.den = r2.den < v.den ? r2.den : v.den;
@@ -1409,13 +1431,13 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
     const int nl = (int)S.nlong;
     for (int q = warp; q < nl; q += kSortThreads / 32) {
         const int j = S.longq[q];
-        const uint64_t hj = A[j] >> 16;
+        const uint64_t hj = A[j] & hmask;
         uint64_t fl = 0;
         int64_t fh = 0;
         int64_t den = recs[A[j] & 0xFFFF].den;
         for (int base = j; base < cnt; base += 32) {
             const int k = base + lane;
-            const bool same = k < cnt && (A[k] >> 16) == hj;
+            const bool same = k < cnt && (A[k] & hmask) == hj;
             if (same) {
                 const Rec &r = recs[A[k] & 0xFFFF];
                 rec_add(r, fl, fh, err);
