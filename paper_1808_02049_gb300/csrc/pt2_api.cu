@@ -248,7 +248,7 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
     if (opts_in) o = *opts_in;
     if (o.constraint_mod > 1 && o.constraint_rem >= o.constraint_mod)
         return fail(c, PT2_ERR_INVALID, "constraint_rem must be below constraint_mod");
-    uint64_t tile_target = o.tile_target ? o.tile_target : 1152;
+    uint64_t tile_target = o.tile_target ? o.tile_target : 576;
     if (tile_target > (uint64_t)kTileCap) return fail(c, PT2_ERR_INVALID, "tile_target above %d", kTileCap);
     const bool prof = (o.flags & PT2_FLAG_PROFILE) != 0;
     cudaStream_t st = c->stream;
@@ -357,7 +357,7 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
 
     uint64_t n_tiles_total = 0;
     uint32_t n_big_total = 0;
-    const int tile_ctas = c->sm_count;
+    const int tile_ctas = 4 * c->sm_count;
     for (size_t pi = 0; pi < passes.size(); ++pi) {
         const Pass &P = passes[pi];
         n_tiles_total += P.n_tiles;
@@ -437,7 +437,7 @@ int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *o
         n_big_total += bi.n_big;
         if (bi.n_big) {
             uint64_t cap = bi.big_max;
-            int ctas = (int)std::min<uint64_t>(bi.n_big, (uint64_t)c->sm_count);
+            int ctas = (int)std::min<uint64_t>(bi.n_big, 4ull * (uint64_t)c->sm_count);
             // keep the scratch within 2 GB (or what a single tile needs)
             while (ctas > 1 && (uint64_t)ctas * 2 * cap * sizeof(Rec48) > (2ull << 30)) ctas /= 2;
             if ((rc = ensure(c, c->scratch, (size_t)ctas * 2 * cap * sizeof(Rec48), "oversize scratch"))) return rc;

@@ -13,14 +13,14 @@ constexpr int kClassBits = 12;               // alpha-hash classes used to form 
 constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
 constexpr int kGenBatch = 8;                 // terms whose slots a lane requests before storing any
-constexpr int kTileThreads = 512;            // tile sort-reduce CTA (two per SM)
-constexpr int kTileCap = 1536;               // records a tile CTA sorts in shared memory
-constexpr int kSortCap = 1536;               // records one in-shared-memory sort handles
+constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per SM)
+constexpr int kTileCap = 768;                // records a tile CTA sorts in shared memory
+constexpr int kSortCap = 768;                // records one in-shared-memory sort handles
 constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
-constexpr uint64_t kMaxTilesPerPass = 1600000;  // keeps the tile cursors (8 B each) resident in L2
+constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (8 B each) resident in L2
 constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
-constexpr int kBigThreads = 512;
-constexpr int kBigCap = 1536;                // Rec48 records sorted per chunk (oversize path)
+constexpr int kBigThreads = 256;
+constexpr int kBigCap = 768;                 // Rec48 records sorted per chunk (oversize path)
 
 // Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is
 // assembled from) are int64 multiples of 2^-48 Ha; numerator and energy sums

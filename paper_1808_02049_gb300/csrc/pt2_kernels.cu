@@ -1566,7 +1566,7 @@ __device__ __forceinline__ void push_oversize(const TileParams &p, uint64_t t, u
 
 // Persistent: CTA g handles tiles g, g + G, g + 2G, ...  Thread 0 keeps the
 // tile metadata one tile ahead, so each tile's TMA load starts at once.
-__global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams p)
+__global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
@@ -1670,7 +1670,7 @@ __device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst
     if (!sort_reduce_chunk(recs, m, M.S, err, put)) exact_reduce_chunk(recs, m, M.S, err, put);
 }
 
-__global__ void __launch_bounds__(kBigThreads, 1) big_tile_kernel(const TileParams p)
+__global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BigSmem &M = *reinterpret_cast<BigSmem *>(smem_raw);

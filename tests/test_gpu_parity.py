@@ -104,11 +104,11 @@ def test_run_is_bit_identical_across_runs(ctx, cfg0):
     assert a == {**b, "seconds": a["seconds"]}
 
 
-@pytest.mark.parametrize("tile_target", [16, 256, 1536])
+@pytest.mark.parametrize("tile_target", [16, 256, 768])
 def test_tile_sizes_and_oversize_path(ctx, cfg0, tile_target):
     got = ctx.run(cfg0["rid"], tile_target=tile_target)
     assert_same_result(got, cfg0["ref"])
-    if tile_target == 1536:
+    if tile_target == 768:
         assert got["n_oversize"] > 0  # tiles above shared-memory capacity took the chunked path
 
 
@@ -116,7 +116,7 @@ def test_e2_is_bit_identical_for_any_tiling_and_pass_plan(ctx, cfg0):
     # numerators and the energy are summed exactly in fixed point, so the
     # result cannot depend on how terms are split into passes and tiles
     base = ctx.run(cfg0["rid"])
-    for kw in [dict(tile_target=16), dict(tile_target=1536), dict(pass_budget_bytes=12 << 20),
+    for kw in [dict(tile_target=16), dict(tile_target=768), dict(pass_budget_bytes=12 << 20),
                dict(pass_budget_bytes=40 << 20, tile_target=100)]:
         got = ctx.run(cfg0["rid"], **kw)
         assert got["e2"] == base["e2"], kw
