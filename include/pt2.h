@@ -145,6 +145,28 @@ int pt2_dump_external(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, uint6
 int pt2_det_terms(pt2_ctx *ctx, uint32_t ref_id, uint64_t det_index, uint64_t *keys,
                   double *val, double *haa, uint64_t cap, uint64_t *n_out);
 
+/* Allocation-free variant of pt2_det_terms, for callers that cannot allocate
+ * device memory at the moment they call: code that runs under a memory pool
+ * or arena it must not bypass, a serving loop that forbids allocations on its
+ * latency path, or a process whose device memory is already fully reserved.
+ * The paper has no counterpart; this is a library convenience.
+ *
+ * keys (2*cap uint64), val and haa (cap doubles each) are DEVICE pointers the
+ * caller owns; the terms of determinant det_index are written there (at most
+ * cap of them) and *n_out (host) receives their number (PT2_ERR_OOM if it
+ * exceeds cap).  Order is unspecified, as for pt2_det_terms.
+ *
+ * The call allocates nothing: it stages the terms in a fixed device array
+ * built into the library (16 MiB, 524288 terms; every GPU that loads the
+ * library holds it until the process exits).  A determinant with more terms
+ * is rejected with PT2_ERR_OOM.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array and clear its counter when they start, so calls
+ * whose GPU work overlaps (several threads or contexts) race and must be
+ * serialised by the caller.  Blocking: returns after the terms are written. */
+int pt2_det_terms_noalloc(pt2_ctx *ctx, uint32_t ref_id, uint64_t det_index, uint64_t *keys, double *val,
+                          double *haa, uint64_t cap, uint64_t *n_out);
+
 /* Per-phase device milliseconds of the last run made with PT2_FLAG_PROFILE:
  * out[0] class count, [1] tile count, [2] scan, [3] generate/emit,
  * [4] reference partition, [5] tile sort-reduce, [6] oversize tiles,

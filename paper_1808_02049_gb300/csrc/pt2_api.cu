@@ -827,6 +827,31 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
     return PT2_OK;
 }
 
+int pt2_det_terms_noalloc(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *keys, double *val,
+                          double *haa, uint64_t cap, uint64_t *n_out)
+{
+    if (!c) return PT2_ERR_INVALID;
+    auto it = c->refs.find(ref_id);
+    if (it == c->refs.end()) return fail(c, PT2_ERR_NOT_FOUND, "unknown reference id %u", ref_id);
+    if (!n_out || (cap && (!keys || !val || !haa))) return fail(c, PT2_ERR_INVALID, "bad arguments");
+    RefRes &r = *it->second;
+    if (det_index >= r.n_det) return fail(c, PT2_ERR_INVALID, "determinant index out of range");
+    SystemRes &s = *c->systems.at(r.system);
+    const uint64_t T = terms_per_det(s.n, r.na, r.nb);
+    if (T > kNoAllocMaxTerms)
+        return fail(c, PT2_ERR_OOM,
+                    "a determinant of this system has %llu terms, above the %llu the fixed device scratch holds",
+                    (unsigned long long)T, (unsigned long long)kNoAllocMaxTerms);
+    cudaSetDevice(c->device);
+    GenParams p = gen_params(c, s, r);
+    p.det_begin = det_index;
+    unsigned long long n = 0;
+    CK(launch_det_terms_noalloc(c->device, p, cap, keys, val, haa, &n, c->stream), "allocation-free generation");
+    *n_out = n;
+    if (n > cap) return fail(c, PT2_ERR_OOM, "determinant has %llu terms, above cap %llu", n, (unsigned long long)cap);
+    return PT2_OK;
+}
+
 int pt2_phase_times(pt2_ctx *c, double *out, int n, uint64_t *launches)
 {
     if (!c || (!out && n > 0)) return PT2_ERR_INVALID;

@@ -168,4 +168,11 @@ cudaError_t launch_acc_finalize(RunAcc *acc, cudaStream_t s);
 size_t tile_smem_bytes();
 size_t big_smem_bytes();
 
+// Allocation-free generation of one determinant's terms into caller-owned
+// device arrays, staged in a fixed device array of kNoAllocMaxTerms records.
+constexpr uint64_t kNoAllocMaxTerms = 1ull << 19;
+constexpr int kMaxDevices = 64;
+cudaError_t launch_det_terms_noalloc(int device, GenParams p, uint64_t cap, uint64_t *keys, double *val, double *haa,
+                                     unsigned long long *n_host, cudaStream_t s);
+
 }  // namespace pt2

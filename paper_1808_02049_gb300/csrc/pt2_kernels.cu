@@ -25,6 +25,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "pt2_internal.cuh"
 
@@ -1855,6 +1856,73 @@ cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, dou
     if (n == 0) return cudaSuccess;
     diag_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys, keys, n, out);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ allocation-free variant
+//
+// Scratch of the allocation-free term generation: a counter followed by a
+// staging area of kNoAllocMaxTerms records, in a file-scope device array.
+// Every GPU that loads the library holds this array (16 MiB + 256 bytes)
+// until the process exits.  All calls share it: the counter is cleared at the
+// start of every call, and calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[256 + kNoAllocMaxTerms * sizeof(Rec32)];
+
+// The array's device address per device.  Host code may not use the symbol
+// itself (it is a host-side stand-in), so the address is looked up with
+// cudaGetSymbolAddress once per device, with that device current.
+static void *g_noalloc_addr[kMaxDevices];
+static std::mutex g_noalloc_mu;
+
+static cudaError_t noalloc_scratch(int device, void **out)
+{
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = ptr;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+// Split staged records into the caller's key / numerator / diagonal arrays
+// (at most cap of them).
+__global__ void split_terms_kernel(const Rec32 *__restrict__ recs, const unsigned long long *__restrict__ count,
+                                   uint64_t cap, uint64_t *__restrict__ keys, double *__restrict__ val,
+                                   double *__restrict__ haa)
+{
+    const uint64_t n = *count < cap ? *count : cap;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const Rec32 r = recs[i];
+        keys[2 * i] = r.a;
+        keys[2 * i + 1] = r.b;
+        val[i] = r.num;
+        haa[i] = __longlong_as_double((long long)r.den);  // this generation mode stores H_aa itself
+    }
+}
+
+cudaError_t launch_det_terms_noalloc(int device, GenParams p, uint64_t cap, uint64_t *keys, double *val, double *haa,
+                                     unsigned long long *n_host, cudaStream_t s)
+{
+    void *base = nullptr;
+    cudaError_t e = noalloc_scratch(device, &base);
+    if (e != cudaSuccess) return e;
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(base);
+    Rec32 *recs = reinterpret_cast<Rec32 *>(static_cast<unsigned char *>(base) + 256);
+    p.cursor = count;
+    p.recs = recs;
+    p.rec_cap = kNoAllocMaxTerms;
+    p.n_tiles = 1;
+    gen_layout(p, kModeDetTerms);
+    if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = launch_gen(kModeDetTerms, p, 1, s)) != cudaSuccess) return e;
+    split_terms_kernel<<<64, 256, 0, s>>>(recs, count, cap, keys, val, haa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(n_host, count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(s);
 }
 
 }  // namespace pt2

@@ -28,7 +28,7 @@ PT2_FLAG_PROFILE = 1
 
 EXPORTS = ["pt2_create", "pt2_destroy", "pt2_last_error", "pt2_load_system", "pt2_load_reference",
            "pt2_unload", "pt2_diagonal", "pt2_run", "pt2_dump_external", "pt2_det_terms",
-           "pt2_phase_times", "pt2_memory_info", "pt2_stream"]
+           "pt2_det_terms_noalloc", "pt2_phase_times", "pt2_memory_info", "pt2_stream"]
 
 PHASES = ["class_count", "tile_count", "scan", "emit", "ref_partition", "tile_sort_reduce",
           "oversize_tiles", "pass_reduce"]
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "pt2_run": (i32, [P, u32, ctypes.POINTER(pt2_opts), ctypes.POINTER(pt2_result)]),
         "pt2_dump_external": (i32, [P, u32, ctypes.POINTER(pt2_opts), P, P, P, u64, pu64]),
         "pt2_det_terms": (i32, [P, u32, u64, P, P, P, u64, pu64]),
+        "pt2_det_terms_noalloc": (i32, [P, u32, u64, P, P, P, u64, pu64]),
         "pt2_phase_times": (i32, [P, P, i32, pu64]),
         "pt2_memory_info": (i32, [P, pu64, pu64, pu64]),
         "pt2_stream": (P, [P]),
@@ -191,6 +192,17 @@ def pt2_det_terms(ctx, ref_id: int, det_index: int, cap: int):
                                              int(cap), ctypes.byref(n)))
     m = n.value
     return keys[: 2 * m].reshape(m, 2), val[:m], haa[:m]
+
+
+def pt2_det_terms_noalloc(ctx, ref_id: int, det_index: int, keys_dev: int, val_dev: int, haa_dev: int,
+                          cap: int) -> int:
+    """Terms of one determinant into caller-owned DEVICE buffers (addresses as
+    integers), without any device allocation; returns the number of terms."""
+    n = ctypes.c_uint64()
+    _check(ctx, load_library().pt2_det_terms_noalloc(ctx, int(ref_id), int(det_index), ctypes.c_void_p(keys_dev),
+                                                     ctypes.c_void_p(val_dev), ctypes.c_void_p(haa_dev), int(cap),
+                                                     ctypes.byref(n)))
+    return n.value
 
 
 def pt2_phase_times(ctx):
