@@ -107,7 +107,8 @@ typedef struct {
     uint32_t flags;             /* PT2_FLAG_* below */
 } pt2_opts;
 
-#define PT2_FLAG_PROFILE 1u  /* record per-phase device times (pt2_phase_times) */
+#define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times) */
+#define PT2_FLAG_AUTOTUNE 2u  /* pt2_batch_create: tune the tile target per size class first */
 
 typedef struct {
     double e2;                /* the PT2 energy, Hartree */
@@ -136,6 +137,65 @@ int pt2_run(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, pt2_result *out
  * *n_out receives |S| (PT2_ERR_OOM if it exceeds cap).  Parity aid. */
 int pt2_dump_external(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, uint64_t *keys,
                       double *num, double *haa, uint64_t cap, uint64_t *n_out);
+
+/* ------------------------------------------------------------------ batches
+ *
+ * Many independent solves of uneven size (different systems, orbital counts,
+ * reference sizes) run together: their memory-bounded passes (Algorithm 2)
+ * are packed into steps, and every step runs one pass of each of its
+ * instances with a single launch of every kernel.  pt2_batch_create plans the
+ * batch (one work-list launch over all instances), allocates its workspace
+ * and captures all steps into one CUDA graph; pt2_batch_run replays it.
+ * Results are bit-identical to pt2_run of each instance alone. */
+
+/* Plan and capture a batch of n loaded references (n <= 256).  opts applies
+ * to every instance (NULL: defaults); with PT2_FLAG_AUTOTUNE the tile target
+ * of each size class present is tuned first (pt2_autotune). */
+int pt2_batch_create(pt2_ctx *ctx, uint32_t n, const uint32_t *ref_ids, const pt2_opts *opts,
+                     uint32_t *batch_id);
+
+/* Run a created batch (blocking); results: n entries in creation order.
+ * results[i].seconds is the device time of the whole batch. */
+int pt2_batch_run(pt2_ctx *ctx, uint32_t batch_id, pt2_result *results);
+
+/* Steps, total generated terms and kernel launches of one batch run. */
+int pt2_batch_info(pt2_ctx *ctx, uint32_t batch_id, uint32_t *n_steps, uint64_t *n_terms, uint64_t *launches);
+
+/* Release a batch and its device memory. */
+int pt2_batch_destroy(pt2_ctx *ctx, uint32_t batch_id);
+
+/* Autotuner: time every candidate tile target (the terms per hash tile, which
+ * sets the bucket count of each pass and the in-shared-memory sort size) on
+ * one reference and remember the fastest for the reference's size class
+ * (decades of generated terms); later plans of that class use it.  The energy
+ * does not depend on the choice. */
+int pt2_autotune(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, uint32_t *best_tile_target);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * Continuous batching: submitted solves queue, are admitted while fewer than
+ * 256 are in flight, planned (work-list launch) and then advance one pass per
+ * engine step together with every other admitted solve whose next pass fits
+ * the step's memory budget; finished solves leave and waiting ones join
+ * between steps.  A background host thread of the context runs the engine;
+ * systems and references stay resident, and a reference with requests in
+ * flight cannot be unloaded (PT2_ERR_BUSY).  Each result is bit-identical to
+ * pt2_run of the same reference alone. */
+
+/* Queue a solve of a loaded reference; *ticket identifies it. */
+int pt2_submit(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, uint64_t *ticket);
+
+/* PT2_ERR_BUSY while the request runs; otherwise its status, with the result
+ * in *out (seconds = latency from submission to completion).  A finished
+ * ticket is reported once and then forgotten (PT2_ERR_NOT_FOUND after). */
+int pt2_poll(pt2_ctx *ctx, uint64_t ticket, pt2_result *out);
+
+/* Like pt2_poll, but first wait up to timeout_ns for the request to finish;
+ * PT2_ERR_TIMEOUT if it is still running then. */
+int pt2_wait(pt2_ctx *ctx, uint64_t ticket, uint64_t timeout_ns, pt2_result *out);
+
+/* Requests waiting for admission, in flight, and engine steps run so far. */
+int pt2_server_stats(pt2_ctx *ctx, uint64_t *pending, uint64_t *active, uint64_t *steps);
 
 /* Generate the terms of one reference determinant (index in the caller's
  * original order): every single and double excitation D_a with its numerator

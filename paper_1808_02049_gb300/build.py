@@ -12,8 +12,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpt2.so")
-SOURCES = ["pt2_api.cu", "pt2_kernels.cu"]
-HEADERS = [os.path.join(CSRC, "pt2_internal.cuh"), os.path.join(ROOT, "include", "pt2.h")]
+SOURCES = ["pt2_api.cu", "pt2_engine.cu", "pt2_kernels.cu"]
+HEADERS = [os.path.join(CSRC, "pt2_internal.cuh"), os.path.join(CSRC, "pt2_runtime.h"),
+           os.path.join(ROOT, "include", "pt2.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

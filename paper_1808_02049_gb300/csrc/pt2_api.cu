@@ -11,57 +11,15 @@
 #include <string>
 #include <vector>
 
-#include "pt2.h"
-#include "pt2_internal.cuh"
+#include "pt2_runtime.h"
 
 using namespace pt2;
 
 namespace {
-
 thread_local std::string g_create_error;
-
-struct DevBuf {
-    void *ptr = nullptr;
-    size_t bytes = 0;
-};
-
-struct SystemRes {
-    int n = 0;
-    DevBuf h, eri, J, WS, Jx, WSx, hdx;
-    int refs = 0;  // references using this system
-};
-
-struct RefRes {
-    uint32_t system = 0;
-    uint64_t n_det = 0;
-    int na = 0, nb = 0;
-    double e0 = 0.0;
-    DevBuf keys, coef, hii, d0;
-};
-
-constexpr int kPhases = 8;
-
 }  // namespace
 
-struct pt2_ctx {
-    int device = 0;
-    int sm_count = 0;
-    cudaStream_t stream = nullptr;
-    uint64_t budget = 0, used = 0;
-    std::string err;
-    uint32_t next_id = 1;
-    std::map<uint32_t, std::unique_ptr<SystemRes>> systems;
-    std::map<uint32_t, std::unique_ptr<RefRes>> refs;
-    DevBuf hash;
-    // run workspace (grow-only)
-    DevBuf class_counts, tile_counts, tile_off, cursor, scan_tmp, recs, ref_tile, ref_count, ref_off, ref_cursor,
-        ref_keys, big_list, scratch, acc, err_word, dump_keys, dump_num, dump_haa, dump_count;
-    cudaEvent_t ev[2 * kPhases + 2] = {};
-    double phase_ms[kPhases] = {};
-    uint64_t launches = 0;
-};
-
-namespace {
+namespace pt2 {
 
 int fail(pt2_ctx *c, int code, const char *fmt, ...)
 {
@@ -80,11 +38,6 @@ int cuda_fail(pt2_ctx *c, cudaError_t e, const char *what)
     return fail(c, PT2_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
-    } while (0)
 
 int dev_alloc(pt2_ctx *c, DevBuf &b, size_t bytes, const char *what)
 {
@@ -119,6 +72,7 @@ int ensure(pt2_ctx *c, DevBuf &b, size_t bytes, const char *what)
 {
     if (b.bytes >= bytes && b.ptr) return PT2_OK;
     dev_free(c, b);
+    c->ws_gen++;
     return dev_alloc(c, b, bytes, what);
 }
 
@@ -194,27 +148,6 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     return p;
 }
 
-// Launch the generator over all determinants in slices (grid.x limit).
-cudaError_t gen_all(pt2_ctx *c, GenMode mode, GenParams p, uint64_t n_det)
-{
-    gen_layout(p, mode);
-    const uint64_t slice = 1ull << 30;
-    for (uint64_t b = 0; b < n_det; b += slice) {
-        p.det_begin = b;
-        uint64_t m = std::min(slice, n_det - b);
-        cudaError_t e = launch_gen(mode, p, m, c->stream);
-        c->launches++;
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-struct Pass {
-    uint32_t c_lo, c_hi;
-    uint64_t records;
-    uint64_t n_tiles;
-};
-
 int status_of_err(pt2_ctx *c, uint32_t err)
 {
     if (!err) return PT2_OK;
@@ -229,280 +162,7 @@ int status_of_err(pt2_ctx *c, uint32_t err)
     return fail(c, PT2_ERR_CUDA, "device error bits 0x%x", err);
 }
 
-struct DumpTarget {
-    uint64_t *keys = nullptr;
-    double *num = nullptr, *haa = nullptr;
-    uint64_t cap = 0;
-    uint64_t n_out = 0;
-};
-
-int run_impl(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts_in, pt2_result *out, DumpTarget *dump)
-{
-    auto it = c->refs.find(ref_id);
-    if (it == c->refs.end()) return fail(c, PT2_ERR_NOT_FOUND, "unknown reference id %u", ref_id);
-    if (!out) return fail(c, PT2_ERR_INVALID, "result pointer is NULL");
-    RefRes &r = *it->second;
-    SystemRes &s = *c->systems.at(r.system);
-    pt2_opts o;
-    memset(&o, 0, sizeof o);
-    if (opts_in) o = *opts_in;
-    if (o.constraint_mod > 1 && o.constraint_rem >= o.constraint_mod)
-        return fail(c, PT2_ERR_INVALID, "constraint_rem must be below constraint_mod");
-    uint64_t tile_target = o.tile_target ? o.tile_target : 576;
-    if (tile_target > (uint64_t)kTileCap) return fail(c, PT2_ERR_INVALID, "tile_target above %d", kTileCap);
-    const bool prof = (o.flags & PT2_FLAG_PROFILE) != 0;
-    cudaStream_t st = c->stream;
-    c->launches = 0;
-    for (double &x : c->phase_ms) x = 0.0;
-    int rc;
-
-    // fixed workspace
-    if ((rc = ensure(c, c->class_counts, kNumClasses * 8, "class counts"))) return rc;
-    if ((rc = ensure(c, c->acc, sizeof(RunAcc), "accumulator"))) return rc;
-    if ((rc = ensure(c, c->ref_tile, r.n_det * 4, "reference tiles"))) return rc;
-    if ((rc = ensure(c, c->ref_keys, r.n_det * 16, "reference slices"))) return rc;
-    if (dump) {
-        if ((rc = ensure(c, c->dump_count, 16, "dump count"))) return rc;
-        if ((rc = ensure(c, c->dump_keys, std::max<uint64_t>(dump->cap, 1) * 16, "dump keys"))) return rc;
-        if ((rc = ensure(c, c->dump_num, std::max<uint64_t>(dump->cap, 1) * 8, "dump num"))) return rc;
-        if ((rc = ensure(c, c->dump_haa, std::max<uint64_t>(dump->cap, 1) * 8, "dump haa"))) return rc;
-        CK(cudaMemsetAsync(c->dump_count.ptr, 0, 8, st), "memset");
-    }
-    RunAcc *acc = (RunAcc *)c->acc.ptr;
-    uint32_t *errw = (uint32_t *)c->err_word.ptr;
-
-    CK(cudaEventRecord(c->ev[0], st), "event");
-    CK(cudaMemsetAsync(errw, 0, 4, st), "memset");
-    CK(launch_acc_init(acc, st), "acc init");
-    c->launches++;
-
-    // ---- work list: terms per alpha-hash class
-    GenParams gp = gen_params(c, s, r);
-    gp.cons_mod = o.constraint_mod > 1 ? o.constraint_mod : 1;
-    gp.cons_rem = o.constraint_mod > 1 ? o.constraint_rem : 0;
-    gp.class_counts = (unsigned long long *)c->class_counts.ptr;
-    CK(cudaMemsetAsync(c->class_counts.ptr, 0, kNumClasses * 8, st), "memset");
-    CK(gen_all(c, kModeClassCount, gp, r.n_det), "class count kernel");
-    std::vector<unsigned long long> cls(kNumClasses);
-    CK(cudaMemcpyAsync(cls.data(), c->class_counts.ptr, kNumClasses * 8, cudaMemcpyDeviceToHost, st), "copy");
-    CK(cudaEventRecord(c->ev[1], st), "event");
-    CK(cudaStreamSynchronize(st), "sync");
-    if (prof) {
-        float ms = 0;
-        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-        c->phase_ms[0] += ms;
-    }
-
-    // ---- plan passes under the memory budget
-    uint64_t total = 0;
-    for (auto x : cls) total += x;
-    uint64_t pass_budget = o.pass_budget_bytes;
-    if (!pass_budget) {
-        // the pass workspace a previous run left allocated is reused, so it counts as available
-        const DevBuf *ws[] = {&c->tile_counts, &c->tile_off, &c->cursor,   &c->scan_tmp, &c->ref_count,
-                              &c->ref_off,     &c->ref_cursor, &c->big_list, &c->scratch,  &c->recs};
-        uint64_t held = 0;
-        for (const DevBuf *b : ws) held += b->bytes;
-        const uint64_t fixed = c->used - held;
-        const uint64_t reserve = (2ull << 30) + (64ull << 20);  // oversize scratch and slack
-        pass_budget = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
-    }
-    // per record: 32 bytes plus about 60 bytes of tile bookkeeping per tile
-    const double per_rec = sizeof(Rec32) + 60.0 / (double)tile_target;
-    uint64_t max_rec = (uint64_t)((double)pass_budget / per_rec);
-    // Emission scatters every term to a random tile through an atomic cursor;
-    // when the cursors of a pass no longer fit in L2 those atomics go to DRAM,
-    // so a default pass holds at most kMaxTilesPerPass tiles.
-    if (!o.pass_budget_bytes) max_rec = std::min<uint64_t>(max_rec, kMaxTilesPerPass * tile_target);
-    // Random 32-byte writes spread over a larger footprint run slower (address
-    // translation reach), so a default pass also stays below kMaxPassBytes.
-    if (!o.pass_budget_bytes) max_rec = std::min<uint64_t>(max_rec, kMaxPassBytes / sizeof(Rec32));
-    if (max_rec < 1024)
-        return fail(c, PT2_ERR_OOM, "pass budget of %llu bytes is too small (context budget %llu, in use %llu)",
-                    (unsigned long long)pass_budget, (unsigned long long)c->budget, (unsigned long long)c->used);
-    std::vector<Pass> passes;
-    {
-        Pass cur{0, 0, 0, 0};
-        for (int k = 0; k < kNumClasses; ++k) {
-            if (cls[k] > max_rec)
-                return fail(c, PT2_ERR_OOM,
-                            "alpha class %d holds %llu terms, above the %llu a pass can hold; raise the budget", k,
-                            (unsigned long long)cls[k], (unsigned long long)max_rec);
-            if (cur.records + cls[k] > max_rec) {
-                cur.c_hi = k;
-                passes.push_back(cur);
-                cur = Pass{(uint32_t)k, 0, 0, 0};
-            }
-            cur.records += cls[k];
-        }
-        cur.c_hi = kNumClasses;
-        if (cur.records > 0 || passes.empty()) passes.push_back(cur);
-    }
-    uint64_t max_tiles = 1, max_records = 1;
-    for (auto &p : passes) {
-        p.n_tiles = std::max<uint64_t>(1, (p.records + tile_target - 1) / tile_target);
-        max_tiles = std::max(max_tiles, p.n_tiles);
-        max_records = std::max(max_records, p.records);
-    }
-    if (max_tiles >= 0xFFFFFFFFull) return fail(c, PT2_ERR_INVALID, "too many tiles in one pass");
-    if ((rc = ensure(c, c->tile_counts, max_tiles * 4, "tile counts"))) return rc;
-    if ((rc = ensure(c, c->tile_off, (max_tiles + 1) * 8, "tile offsets"))) return rc;
-    if ((rc = ensure(c, c->cursor, max_tiles * 8, "tile cursors"))) return rc;
-    if ((rc = ensure(c, c->scan_tmp, scan_tmp_elems(max_tiles) * 8 * 2, "scan scratch"))) return rc;
-    if ((rc = ensure(c, c->ref_count, max_tiles * 4, "reference counts"))) return rc;
-    if ((rc = ensure(c, c->ref_off, (max_tiles + 1) * 8, "reference offsets"))) return rc;
-    if ((rc = ensure(c, c->ref_cursor, max_tiles * 8, "reference cursors"))) return rc;
-    if ((rc = ensure(c, c->big_list, max_tiles * 4, "oversize list"))) return rc;
-    if ((rc = ensure(c, c->recs, max_records * sizeof(Rec32), "term records"))) return rc;
-
-    uint64_t n_tiles_total = 0;
-    uint32_t n_big_total = 0;
-    const int tile_ctas = 4 * c->sm_count;
-    for (size_t pi = 0; pi < passes.size(); ++pi) {
-        const Pass &P = passes[pi];
-        n_tiles_total += P.n_tiles;
-        cudaEvent_t *E = &c->ev[2];
-        // tile counts
-        if (prof) CK(cudaEventRecord(E[0], st), "event");
-        GenParams g = gp;
-        g.class_lo = P.c_lo;
-        g.class_hi = P.c_hi;
-        g.n_tiles = P.n_tiles;
-        g.tile_counts = (uint32_t *)c->tile_counts.ptr;
-        g.cursor = (unsigned long long *)c->cursor.ptr;
-        g.recs = (Rec32 *)c->recs.ptr;
-        g.rec_cap = P.records;
-        CK(cudaMemsetAsync(g.tile_counts, 0, P.n_tiles * 4, st), "memset");
-        CK(gen_all(c, kModeTileCount, g, r.n_det), "tile count kernel");
-        if (prof) CK(cudaEventRecord(E[1], st), "event");
-        CK(launch_scan_u32_to_u64(g.tile_counts, (unsigned long long *)c->tile_off.ptr, P.n_tiles,
-                                  (unsigned long long *)c->scan_tmp.ptr, st),
-           "scan");
-        c->launches += 3;
-        CK(cudaMemcpyAsync(c->cursor.ptr, c->tile_off.ptr, P.n_tiles * 8, cudaMemcpyDeviceToDevice, st), "copy");
-        if (prof) CK(cudaEventRecord(E[2], st), "event");
-        CK(gen_all(c, kModeEmit, g, r.n_det), "emit kernel");
-        if (prof) CK(cudaEventRecord(E[3], st), "event");
-        // reference slices of the pass
-        RefPartParams rp;
-        rp.keys = (const uint64_t *)r.keys.ptr;
-        rp.n_det = r.n_det;
-        rp.hash = (const HashTables *)c->hash.ptr;
-        rp.class_lo = P.c_lo;
-        rp.class_hi = P.c_hi;
-        rp.cons_mod = gp.cons_mod;
-        rp.cons_rem = gp.cons_rem;
-        rp.n_tiles = P.n_tiles;
-        rp.ref_tile = (uint32_t *)c->ref_tile.ptr;
-        rp.ref_count = (uint32_t *)c->ref_count.ptr;
-        rp.ref_cursor = (unsigned long long *)c->ref_cursor.ptr;
-        rp.ref_keys_out = (uint64_t *)c->ref_keys.ptr;
-        CK(cudaMemsetAsync(rp.ref_count, 0, P.n_tiles * 4, st), "memset");
-        CK(launch_ref_partition(rp, 0, st), "reference tiles");
-        CK(launch_scan_u32_to_u64(rp.ref_count, (unsigned long long *)c->ref_off.ptr, P.n_tiles,
-                                  (unsigned long long *)c->scan_tmp.ptr + scan_tmp_elems(max_tiles), st),
-           "scan");
-        CK(cudaMemcpyAsync(rp.ref_cursor, c->ref_off.ptr, P.n_tiles * 8, cudaMemcpyDeviceToDevice, st), "copy");
-        CK(launch_ref_partition(rp, 1, st), "reference scatter");
-        CK(launch_sort_slices((const unsigned long long *)c->ref_off.ptr, (uint64_t *)c->ref_keys.ptr, P.n_tiles, st),
-           "reference sort");
-        c->launches += 6;
-        if (prof) CK(cudaEventRecord(E[4], st), "event");
-        // tiles
-        TileParams tp;
-        memset(&tp, 0, sizeof tp);
-        tp.recs = (const Rec32 *)c->recs.ptr;
-        tp.tile_off = (const unsigned long long *)c->tile_off.ptr;
-        tp.ref_off = (const unsigned long long *)c->ref_off.ptr;
-        tp.ref_keys = (const uint64_t *)c->ref_keys.ptr;
-        tp.n_tiles = P.n_tiles;
-        tp.e0 = r.e0;
-        tp.acc = acc;
-        tp.big_list = (uint32_t *)c->big_list.ptr;
-        tp.err = errw;
-        if (dump) {
-            tp.dump_keys = (uint64_t *)c->dump_keys.ptr;
-            tp.dump_num = (double *)c->dump_num.ptr;
-            tp.dump_haa = (double *)c->dump_haa.ptr;
-            tp.dump_count = (unsigned long long *)c->dump_count.ptr;
-            tp.dump_cap = dump->cap;
-        }
-        CK(launch_tiles(tp, tile_ctas, st), "tile kernel");
-        c->launches++;
-        if (prof) CK(cudaEventRecord(E[5], st), "event");
-        // oversize tiles: size the scratch from what the tile kernel found
-        RunAcc bi;
-        CK(cudaMemcpyAsync(&bi, acc, sizeof bi, cudaMemcpyDeviceToHost, st), "copy");
-        CK(cudaStreamSynchronize(st), "sync");
-        n_big_total += bi.n_big;
-        if (bi.n_big) {
-            uint64_t cap = bi.big_max;
-            int ctas = (int)std::min<uint64_t>(bi.n_big, 4ull * (uint64_t)c->sm_count);
-            // keep the scratch within 2 GB (or what a single tile needs)
-            while (ctas > 1 && (uint64_t)ctas * 2 * cap * sizeof(Rec48) > (2ull << 30)) ctas /= 2;
-            if ((rc = ensure(c, c->scratch, (size_t)ctas * 2 * cap * sizeof(Rec48), "oversize scratch"))) return rc;
-            tp.scratch = (Rec48 *)c->scratch.ptr;
-            tp.scratch_cap = cap;
-            CK(launch_big_tiles(tp, ctas, st), "oversize tile kernel");
-            c->launches++;
-        }
-        if (prof) CK(cudaEventRecord(E[6], st), "event");
-        CK(launch_pass_finish(tp.tile_off, P.n_tiles, P.records, acc, errw, st), "pass finish");
-        c->launches++;
-        if (prof) {
-            CK(cudaEventRecord(E[7], st), "event");
-            CK(cudaEventSynchronize(E[7]), "sync");
-            float ms;
-            for (int k = 0; k < 7; ++k) {
-                cudaEventElapsedTime(&ms, E[k], E[k + 1]);
-                c->phase_ms[k + 1] += ms;
-            }
-        }
-    }
-    CK(launch_acc_finalize(acc, st), "finalize");
-    c->launches++;
-    RunAcc h;
-    uint32_t err = 0;
-    CK(cudaMemcpyAsync(&h, acc, sizeof h, cudaMemcpyDeviceToHost, st), "copy");
-    CK(cudaMemcpyAsync(&err, errw, 4, cudaMemcpyDeviceToHost, st), "copy");
-    CK(cudaEventRecord(c->ev[1], st), "event");
-    CK(cudaStreamSynchronize(st), "sync");
-    float ms = 0;
-    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-    err |= h.err;
-    if ((rc = status_of_err(c, err))) return rc;
-    memset(out, 0, sizeof *out);
-    out->e2 = h.e2;
-    out->n_terms = h.n_terms;
-    out->n_unique = h.n_unique;
-    out->n_in_ref = h.n_in_ref;
-    out->n_external = h.n_ext;
-    out->digest_sum = h.dsum;
-    out->digest_xor = h.dxor;
-    out->min_abs_denom = h.min_abs_den;
-    out->n_pos_denom = h.n_pos;
-    out->n_passes = (uint32_t)passes.size();
-    out->n_tiles = (uint32_t)std::min<uint64_t>(n_tiles_total, 0xFFFFFFFFull);
-    out->n_oversize = n_big_total;
-    out->seconds = ms * 1e-3;
-    if (h.n_terms != total)
-        return fail(c, PT2_ERR_CUDA, "generated %llu terms, planned %llu", (unsigned long long)h.n_terms,
-                    (unsigned long long)total);
-    if (dump) {
-        unsigned long long nd = 0;
-        CK(cudaMemcpy(&nd, c->dump_count.ptr, 8, cudaMemcpyDeviceToHost), "copy");
-        dump->n_out = nd;
-        if (nd > dump->cap)
-            return fail(c, PT2_ERR_OOM, "external set has %llu keys, above the dump capacity %llu", nd,
-                        (unsigned long long)dump->cap);
-        CK(cudaMemcpy(dump->keys, c->dump_keys.ptr, nd * 16, cudaMemcpyDeviceToHost), "copy");
-        CK(cudaMemcpy(dump->num, c->dump_num.ptr, nd * 8, cudaMemcpyDeviceToHost), "copy");
-        CK(cudaMemcpy(dump->haa, c->dump_haa.ptr, nd * 8, cudaMemcpyDeviceToHost), "copy");
-    }
-    return PT2_OK;
-}
-
-}  // namespace
+}  // namespace pt2
 
 // ===================================================================== ABI
 
@@ -524,6 +184,8 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
     if (prop.major < 10)
         return fail(nullptr, PT2_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a", device,
                     prop.major, prop.minor);
+    e = init_kernel_attributes();
+    if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
     auto c = std::make_unique<pt2_ctx>();
     c->device = device;
     c->sm_count = prop.multiProcessorCount;
@@ -561,15 +223,19 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
 void pt2_destroy(pt2_ctx *c)
 {
     if (!c) return;
+    server_stop(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    batches_release(c);
     for (auto &kv : c->refs) free_ref(c, *kv.second);
     for (auto &kv : c->systems) free_system(c, *kv.second);
-    DevBuf *bufs[] = {&c->hash,      &c->class_counts, &c->tile_counts, &c->tile_off, &c->cursor,
-                      &c->scan_tmp,  &c->recs,         &c->ref_tile,    &c->ref_count, &c->ref_off,
-                      &c->ref_cursor, &c->ref_keys,    &c->big_list,    &c->scratch,  &c->acc,
-                      &c->err_word,  &c->dump_keys,    &c->dump_num,    &c->dump_haa, &c->dump_count};
+    DevBuf *bufs[] = {&c->hash,     &c->class_counts, &c->tile_counts, &c->tile_off,   &c->cursor,
+                      &c->scan_tmp, &c->recs,         &c->ref_tile,    &c->ref_count,  &c->ref_off,
+                      &c->ref_cursor, &c->ref_keys,   &c->big_list,    &c->big_max,    &c->scratch,
+                      &c->acc,      &c->err_word,     &c->steps,       &c->gen_tab,    &c->dump_keys,
+                      &c->dump_num, &c->dump_haa,     &c->dump_count};
     for (DevBuf *b : bufs) dev_free(c, *b);
+    if (c->steps_pinned) cudaFreeHost(c->steps_pinned);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -712,9 +378,11 @@ int pt2_unload(pt2_ctx *c, uint32_t id)
     if (!c) return PT2_ERR_INVALID;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    std::lock_guard<std::recursive_mutex> lock(c->exec);
     auto ri = c->refs.find(id);
     if (ri != c->refs.end()) {
         RefRes &r = *ri->second;
+        if (r.busy) return fail(c, PT2_ERR_BUSY, "reference %u has requests in the serving engine", id);
         free_ref(c, r);
         c->systems.at(r.system)->refs--;
         c->refs.erase(ri);
@@ -760,30 +428,6 @@ int pt2_diagonal(pt2_ctx *c, uint32_t system_id, uint64_t n, const uint64_t *key
     return PT2_OK;
 }
 
-int pt2_run(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, pt2_result *out)
-{
-    if (!c) return PT2_ERR_INVALID;
-    cudaSetDevice(c->device);
-    return run_impl(c, ref_id, opts, out, nullptr);
-}
-
-int pt2_dump_external(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, uint64_t *keys, double *num, double *haa,
-                      uint64_t cap, uint64_t *n_out)
-{
-    if (!c) return PT2_ERR_INVALID;
-    if ((cap && (!keys || !num || !haa)) || !n_out) return fail(c, PT2_ERR_INVALID, "bad arguments");
-    cudaSetDevice(c->device);
-    DumpTarget d;
-    d.keys = keys;
-    d.num = num;
-    d.haa = haa;
-    d.cap = cap;
-    pt2_result res;
-    int rc = run_impl(c, ref_id, opts, &res, &d);
-    *n_out = d.n_out;
-    return rc;
-}
-
 int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *keys, double *val, double *haa,
                   uint64_t cap, uint64_t *n_out)
 {
@@ -794,6 +438,7 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
     RefRes &r = *it->second;
     if (det_index >= r.n_det) return fail(c, PT2_ERR_INVALID, "determinant index out of range");
     SystemRes &s = *c->systems.at(r.system);
+    std::lock_guard<std::recursive_mutex> lock(c->exec);
     cudaSetDevice(c->device);
     const uint64_t T = terms_per_det(s.n, r.na, r.nb);
     int rc;
@@ -808,7 +453,7 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
     gen_layout(p, kModeDetTerms);
     CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, c->stream), "memset");
     CK(cudaMemsetAsync(c->cursor.ptr, 0, 8, c->stream), "memset");
-    CK(launch_gen(kModeDetTerms, p, 1, c->stream), "generator");
+    CK(launch_gen_single(kModeDetTerms, p, nullptr, nullptr, c->stream), "generator");
     unsigned long long n = 0;
     CK(cudaMemcpyAsync(&n, c->cursor.ptr, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -842,6 +487,7 @@ int pt2_det_terms_noalloc(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint6
         return fail(c, PT2_ERR_OOM,
                     "a determinant of this system has %llu terms, above the %llu the fixed device scratch holds",
                     (unsigned long long)T, (unsigned long long)kNoAllocMaxTerms);
+    std::lock_guard<std::recursive_mutex> lock(c->exec);
     cudaSetDevice(c->device);
     GenParams p = gen_params(c, s, r);
     p.det_begin = det_index;

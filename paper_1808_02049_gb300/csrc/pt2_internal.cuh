@@ -21,6 +21,8 @@ constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (8 B e
 constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
 constexpr int kBigThreads = 256;
 constexpr int kBigCap = 768;                 // Rec48 records sorted per chunk (oversize path)
+constexpr uint64_t kBigScratch = 16384;      // partial records per buffer of one oversize CTA
+constexpr int kMaxBatch = 256;               // instances in one step
 
 // Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is
 // assembled from) are int64 multiples of 2^-48 Ha; numerator and energy sums
@@ -88,9 +90,10 @@ struct GenParams {
     // pass selection
     uint32_t class_lo, class_hi;  // classes [lo, hi) belong to the pass
     uint64_t cons_mod, cons_rem;  // alpha % mod == rem (mod <= 1: none)
-    uint64_t n_tiles;
+    uint64_t n_tiles;                  // tiles of this instance in the pass
+    uint64_t tile_base;                // first global tile index of this instance
     // outputs
-    unsigned long long *class_counts;  // kNumClasses
+    unsigned long long *class_counts;  // kNumClasses (this instance's slice)
     uint32_t *tile_counts;             // n_tiles
     unsigned long long *cursor;        // n_tiles
     Rec32 *recs;
@@ -99,6 +102,17 @@ struct GenParams {
     // dynamic shared memory layout (byte offsets)
     int smem_sa, smem_sb, smem_pairs, smem_vec, smem_hist, smem_bytes;
     int n_sa, n_sb;                    // singles per determinant: na*(n-na), nb*(n-nb)
+};
+
+// A launch of the generator over several instances: CTA g (global index
+// cta_offset + blockIdx.x) belongs to the instance with
+// det_base[i] <= g < det_base[i + 1] and handles its determinant
+// params[i].det_begin + g - det_base[i].
+struct GenBatch {
+    const GenParams *params;
+    const unsigned long long *det_base;  // n_inst + 1
+    int n_inst;
+    unsigned long long cta_offset;
 };
 
 // Run accumulator: every field is an exact integer reduction.
@@ -114,15 +128,21 @@ struct RunAcc {
     unsigned long long big_max;  // largest oversize tile of the last pass
 };
 
+// Tiles of a step cover several instances: tile t belongs to the instance
+// with tile_base[i] <= t < tile_base[i + 1].
 struct TileParams {
     const Rec32 *recs;
     const unsigned long long *tile_off;  // n_tiles + 1
     const unsigned long long *ref_off;   // n_tiles + 1
     const uint64_t *ref_keys;            // 2 * (refs in pass), grouped by tile, sorted per tile
-    uint64_t n_tiles;
-    double e0;
-    RunAcc *acc;
-    uint32_t *big_list;
+    uint64_t n_tiles;                    // over all instances
+    const unsigned long long *tile_base; // n_inst + 1
+    const double *e0;                    // per instance
+    RunAcc *const *acc;                  // per instance
+    unsigned int *n_big;                 // per instance: oversize tiles of the pass
+    unsigned long long *big_max;         // largest oversize tile (diagnostic)
+    int n_inst;
+    uint32_t *big_list;                  // oversize tiles of instance i start at tile_base[i]
     uint32_t *err;
     // dump of the external set (optional)
     uint64_t *dump_keys;
@@ -134,14 +154,15 @@ struct TileParams {
     unsigned long long scratch_cap;
 };
 
+// Reference determinants of a step: global index g belongs to the instance
+// with ref_base[i] <= g < ref_base[i + 1] (keys, pass and tiles from params[i]).
 struct RefPartParams {
-    const uint64_t *keys;  // 2 * n_det (input order)
-    uint64_t n_det;
+    const GenParams *params;
+    const unsigned long long *ref_base;  // n_inst + 1
+    int n_inst;
+    uint64_t n_total;
     const HashTables *hash;
-    uint32_t class_lo, class_hi;
-    uint64_t cons_mod, cons_rem;
-    uint64_t n_tiles;
-    uint32_t *ref_tile;             // n_det: tile or UINT32_MAX
+    uint32_t *ref_tile;             // n_total: global tile or UINT32_MAX
     uint32_t *ref_count;            // n_tiles
     unsigned long long *ref_cursor; // n_tiles (initialised to offsets)
     uint64_t *ref_keys_out;         // 2 * refs in pass
@@ -150,7 +171,9 @@ struct RefPartParams {
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `s` and return the launch error (cudaSuccess if ok).
 void gen_layout(GenParams &p, GenMode mode);  // fills the smem_* fields from n_sa, n_sb
-cudaError_t launch_gen(GenMode mode, const GenParams &p, uint64_t n_dets, cudaStream_t s);
+cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int smem_bytes, cudaStream_t s);
+cudaError_t launch_gen_single(GenMode mode, const GenParams &p, GenParams *d_params, unsigned long long *d_base,
+                              cudaStream_t s);  // one determinant (parity aid); d_* are 1- and 2-entry scratch
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s);
 cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s);
 cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint64_t n,
@@ -161,10 +184,12 @@ cudaError_t launch_sort_slices(const unsigned long long *ref_off, uint64_t *ref_
                                cudaStream_t s);
 cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s);
 cudaError_t launch_big_tiles(const TileParams &p, int n_ctas, cudaStream_t s);
-cudaError_t launch_pass_finish(const unsigned long long *tile_off, uint64_t n_tiles,
-                               unsigned long long expected_terms, RunAcc *acc, uint32_t *err, cudaStream_t s);
-cudaError_t launch_acc_init(RunAcc *acc, cudaStream_t s);
-cudaError_t launch_acc_finalize(RunAcc *acc, cudaStream_t s);
+cudaError_t launch_pass_finish(const unsigned long long *tile_off, const unsigned long long *tile_base, int n_inst,
+                               const unsigned long long *expected, RunAcc *const *acc, unsigned int *n_big,
+                               uint32_t *err, cudaStream_t s);
+cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s);
+cudaError_t launch_acc_finalize(RunAcc *acc, int n, cudaStream_t s);
+cudaError_t init_kernel_attributes();  // once per process and device, before any capture
 size_t tile_smem_bytes();
 size_t big_smem_bytes();
 

@@ -354,9 +354,9 @@ __device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step,
         slot[u] = 0;
         if (ok[u]) {
             if constexpr (MODE == kModeTileCount) {
-                atomicAdd(&p.tile_counts[__umul64hi(zt, p.n_tiles)], 1u);
+                atomicAdd(&p.tile_counts[p.tile_base + __umul64hi(zt, p.n_tiles)], 1u);
             } else if constexpr (MODE == kModeEmit) {
-                slot[u] = atomicAdd(&p.cursor[__umul64hi(zt, p.n_tiles)], 1ull);
+                slot[u] = atomicAdd(&p.cursor[p.tile_base + __umul64hi(zt, p.n_tiles)], 1ull);
             } else {
                 slot[u] = atomicAdd(&p.cursor[0], 1ull);
             }
@@ -383,8 +383,10 @@ __device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step,
     }
 }
 
+// All singles and doubles of determinant `det` of one instance (the body of
+// both generator kernels).
 template <int MODE>
-__global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
+__device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     GenFixed &F = *reinterpret_cast<GenFixed *>(smem);
@@ -404,7 +406,6 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
     constexpr bool kVal = MODE == kModeEmit || MODE == kModeDetTerms;
     const int N = p.sys.n;
     const int na = p.na, nb = p.nb, nva = N - na, nvb = N - nb;
-    const uint64_t det = p.det_begin + blockIdx.x;
     const double *__restrict__ eri = p.sys.eri;
     const int64_t *__restrict__ Jx = p.sys.Jx;
     const int64_t *__restrict__ WSx = p.sys.WSx;
@@ -709,6 +710,34 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenParams p)
     }
 }
 
+// Generator over the determinants of several instances (one CTA each).
+template <int MODE>
+__global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenBatch b)
+{
+    __shared__ GenParams sp;
+    __shared__ unsigned long long sdet;
+    if (threadIdx.x == 0) {
+        const unsigned long long g = b.cta_offset + blockIdx.x;
+        int lo = 0, hi = b.n_inst;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (b.det_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        sp = b.params[lo];
+        sdet = sp.det_begin + (g - b.det_base[lo]);
+    }
+    __syncthreads();
+    gen_body<MODE>(sp, sdet);
+}
+
+// Generator for one determinant with its parameters passed by value.
+template <int MODE>
+__global__ void __launch_bounds__(kGenThreads, 3) gen_kernel_one(const GenParams p)
+{
+    gen_body<MODE>(p, p.det_begin);
+}
+
 // ============================================================= diagonal
 
 __global__ void diag_kernel(const SysDev sys, const uint64_t *__restrict__ keys, uint64_t n,
@@ -851,41 +880,58 @@ cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, 
 
 // ===================================================== reference partition
 
+__device__ __forceinline__ int ref_instance(const RefPartParams &p, uint64_t g)
+{
+    int lo = 0, hi = p.n_inst;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.ref_base[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void ref_tile_kernel(const RefPartParams p)
 {
-    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= p.n_det) return;
-    uint64_t A = p.keys[2 * i], B = p.keys[2 * i + 1];
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= p.n_total) return;
+    const int inst = ref_instance(p, g);
+    const GenParams &q = p.params[inst];
+    const uint64_t i = g - p.ref_base[inst];
+    const uint64_t A = q.keys[2 * i], B = q.keys[2 * i + 1];
     uint64_t zc = 0, zt = 0;
     for (uint64_t x = A; x; x &= x - 1) {
-        int q = __ffsll((long long)x) - 1;
-        zc ^= p.hash->zc[q];
-        zt ^= p.hash->zta[q];
+        int k = __ffsll((long long)x) - 1;
+        zc ^= p.hash->zc[k];
+        zt ^= p.hash->zta[k];
     }
     for (uint64_t x = B; x; x &= x - 1) zt ^= p.hash->ztb[__ffsll((long long)x) - 1];
-    uint32_t cl = class_of(zc);
+    const uint32_t cl = class_of(zc);
     uint32_t t = 0xFFFFFFFFu;
-    if (cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, A)) {
-        t = (uint32_t)__umul64hi(zt, p.n_tiles);
+    if (cl >= q.class_lo && cl < q.class_hi && cons_ok(q.cons_mod, q.cons_rem, A)) {
+        t = (uint32_t)(q.tile_base + __umul64hi(zt, q.n_tiles));
         atomicAdd(&p.ref_count[t], 1u);
     }
-    p.ref_tile[i] = t;
+    p.ref_tile[g] = t;
 }
 
 __global__ void ref_scatter_kernel(const RefPartParams p)
 {
-    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (i >= p.n_det) return;
-    uint32_t t = p.ref_tile[i];
+    const uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (g >= p.n_total) return;
+    const uint32_t t = p.ref_tile[g];
     if (t == 0xFFFFFFFFu) return;
-    unsigned long long slot = atomicAdd(&p.ref_cursor[t], 1ull);
-    p.ref_keys_out[2 * slot] = p.keys[2 * i];
-    p.ref_keys_out[2 * slot + 1] = p.keys[2 * i + 1];
+    const int inst = ref_instance(p, g);
+    const GenParams &q = p.params[inst];
+    const uint64_t i = g - p.ref_base[inst];
+    const unsigned long long slot = atomicAdd(&p.ref_cursor[t], 1ull);
+    p.ref_keys_out[2 * slot] = q.keys[2 * i];
+    p.ref_keys_out[2 * slot + 1] = q.keys[2 * i + 1];
 }
 
 cudaError_t launch_ref_partition(const RefPartParams &p, int phase, cudaStream_t s)
 {
-    unsigned g = (unsigned)((p.n_det + 255) / 256);
+    const unsigned g = (unsigned)((p.n_total + 255) / 256);
     if (g == 0) return cudaSuccess;
     if (phase == 0) ref_tile_kernel<<<g, 256, 0, s>>>(p);
     else ref_scatter_kernel<<<g, 256, 0, s>>>(p);
@@ -1053,7 +1099,7 @@ __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long 
 
 // One unique key: explicit filter against the reference slice, then the
 // Epstein-Nesbet term num^2 / (E0 - H_aa) of Eq. 3, added exactly.
-__device__ __forceinline__ void finish_key(const TileParams &p, const uint64_t *rk, unsigned long long nrk,
+__device__ __forceinline__ void finish_key(const TileParams &p, double e0, const uint64_t *rk, unsigned long long nrk,
                                            uint64_t a, uint64_t b, double num, int64_t den, KeyStats &st)
 {
     st.n_unique++;
@@ -1076,13 +1122,13 @@ __device__ __forceinline__ void finish_key(const TileParams &p, const uint64_t *
             p.dump_keys[2 * slot] = a;
             p.dump_keys[2 * slot + 1] = b;
             p.dump_num[slot] = num;
-            p.dump_haa[slot] = p.e0 - d;
+            p.dump_haa[slot] = e0 - d;
         }
     }
 }
 
-// Sum the per-thread statistics of the CTA and add them to the run total.
-__device__ void flush_stats(const TileParams &p, KeyStats st, unsigned long long (*red)[32])
+// Sum the per-thread statistics of the CTA and add them to an instance's total.
+__device__ void flush_stats(const TileParams &p, RunAcc *acc, KeyStats st, unsigned long long (*red)[32])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -1127,7 +1173,6 @@ __device__ void flush_stats(const TileParams &p, KeyStats st, unsigned long long
             np += red[8][w];
             er |= red[9][w];
         }
-        RunAcc *acc = p.acc;
         unsigned long long old = atomicAdd(&acc->e2_lo, (unsigned long long)lo);
         unsigned long long carry = (old + lo) < old ? 1ull : 0ull;
         atomicAdd((unsigned long long *)&acc->e2_hi, (unsigned long long)hi + carry);
@@ -1517,10 +1562,10 @@ __device__ void exact_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32
 }
 
 // One unique key into the statistics (filter + Eq. 3 term).
-__device__ __forceinline__ void finish_keyval(const TileParams &p, const uint64_t *rk, unsigned long long nrk,
-                                              const KeyVal &v, KeyStats &st)
+__device__ __forceinline__ void finish_keyval(const TileParams &p, double e0, const uint64_t *rk,
+                                              unsigned long long nrk, const KeyVal &v, KeyStats &st)
 {
-    finish_key(p, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
+    finish_key(p, e0, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
 }
 
 // Shared memory of the main tile kernel (two CTAs share an SM, so one CTA's
@@ -1530,6 +1575,8 @@ struct MainSmem {
     SortSmem S;
     uint64_t rk[2 * kRefSliceSmem];
     unsigned long long meta[4];  // current tile: offset, count, reference offset, reference count
+    unsigned long long tb[kMaxBatch + 1];
+    double e0[kMaxBatch];
     uint64_t bar[2];
 };
 
@@ -1558,20 +1605,36 @@ __device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, con
     bulk_load(M.recs, p.recs + m.off, (uint32_t)(m.cnt * sizeof(Rec32)), &M.bar[0]);
 }
 
-__device__ __forceinline__ void push_oversize(const TileParams &p, uint64_t t, unsigned long long cnt)
+__device__ __forceinline__ void push_oversize(const TileParams &p, int inst, uint64_t t, unsigned long long cnt)
 {
-    const unsigned idx = atomicAdd(&p.acc->n_big, 1u);
-    p.big_list[idx] = (uint32_t)t;
-    atomicMax(&p.acc->big_max, cnt);
+    const unsigned idx = atomicAdd(&p.n_big[inst], 1u);
+    p.big_list[p.tile_base[inst] + idx] = (uint32_t)t;
+    atomicMax(p.big_max, cnt);
+}
+
+// Instance of global tile t (tile_base is in shared memory).
+__device__ __forceinline__ int tile_instance(const unsigned long long *tb, int n_inst, uint64_t t)
+{
+    int lo = 0, hi = n_inst;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tb[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Persistent: CTA g handles tiles g, g + G, g + 2G, ...  Thread 0 keeps the
 // tile metadata one tile ahead, so each tile's TMA load starts at once.
+// Tiles of one instance are consecutive, so a CTA's statistics are flushed
+// to an instance's accumulator when its tiles move on to the next instance.
 __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
     const uint64_t G = gridDim.x;
+    for (int i = threadIdx.x; i <= p.n_inst; i += blockDim.x) M.tb[i] = p.tile_base[i];
+    for (int i = threadIdx.x; i < p.n_inst; i += blockDim.x) M.e0[i] = p.e0[i];
     KeyStats st;
     st.clear();
     TileMeta nx{0, 0, 0, 0};
@@ -1579,8 +1642,18 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
         mbar_init(&M.bar[0], 1);
         nx = tile_meta(p, blockIdx.x);
     }
+    __syncthreads();
+    int cur = tile_instance(M.tb, p.n_inst, blockIdx.x);
+    bool dirty = false;
     uint32_t phase = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G) {
+        const int inst = tile_instance(M.tb, p.n_inst, t);
+        if (inst != cur) {  // uniform across the CTA
+            if (dirty) flush_stats(p, p.acc[cur], st, M.S.u.red);
+            st.clear();
+            dirty = false;
+            cur = inst;
+        }
         if (threadIdx.x == 0) {
             issue_tile(p, M, nx);
             M.meta[0] = nx.off;
@@ -1593,9 +1666,10 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
         const unsigned long long cntl = M.meta[1];
         const unsigned long long roff = M.meta[2], rcnt = M.meta[3];
         if (cntl > (unsigned long long)kTileCap) {
-            if (threadIdx.x == 0) push_oversize(p, t, cntl);
+            if (threadIdx.x == 0) push_oversize(p, inst, t, cntl);
         } else if (cntl > 0) {
             const int cnt = (int)cntl;
+            const double e0 = M.e0[inst];
             const uint64_t *rk = M.rk;
             if (rcnt <= (unsigned long long)kRefSliceSmem) {
                 for (unsigned long long i = threadIdx.x; i < 2 * rcnt; i += blockDim.x)
@@ -1606,12 +1680,13 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
             mbar_wait_bounded(&M.bar[0], phase, p.err);
             phase ^= 1u;
             const bool ok = sort_reduce_chunk(M.recs, cnt, M.S, st.err,
-                                              [&](const KeyVal &v) { finish_keyval(p, rk, rcnt, v, st); });
-            if (!ok && threadIdx.x == 0) push_oversize(p, t, cntl);  // exact path for a hash collision
+                                              [&](const KeyVal &v) { finish_keyval(p, e0, rk, rcnt, v, st); });
+            if (!ok && threadIdx.x == 0) push_oversize(p, inst, t, cntl);  // exact path for a hash collision
+            dirty = true;
         }
         __syncthreads();  // records, slice and metadata free for the next tile
     }
-    flush_stats(p, st, M.S.u.red);
+    if (dirty) flush_stats(p, p.acc[cur], st, M.S.u.red);
     __syncthreads();
     if (threadIdx.x == 0) mbar_inval(&M.bar[0]);
 }
@@ -1620,8 +1695,6 @@ cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 {
     if (p.n_tiles == 0) return cudaSuccess;
     size_t sm = tile_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     unsigned g = (unsigned)(p.n_tiles < (uint64_t)n_ctas ? p.n_tiles : (uint64_t)n_ctas);
     tile_kernel<<<g, kTileThreads, sm, s>>>(p);
     return cudaGetLastError();
@@ -1671,115 +1744,130 @@ __device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst
     if (!sort_reduce_chunk(recs, m, M.S, err, put)) exact_reduce_chunk(recs, m, M.S, err, put);
 }
 
+// Persistent over the oversize tiles of every instance, instance by
+// instance, so each CTA flushes its statistics once per instance.  The
+// partial lists live in a fixed per-CTA scratch of two buffers of
+// scratch_cap records; a tile whose partials outgrow it sets kErrScratch.
 __global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BigSmem &M = *reinterpret_cast<BigSmem *>(smem_raw);
     Rec48 *bufA = p.scratch + (size_t)blockIdx.x * 2 * p.scratch_cap;
     Rec48 *bufB = bufA + p.scratch_cap;
-    const unsigned int nbig = p.acc->n_big;
-    KeyStats st;
-    st.clear();
     uint32_t phase = 0;
     if (threadIdx.x == 0) mbar_init(&M.bar, 1);
     __syncthreads();
     const int nt = blockDim.x;
-    for (unsigned int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
-        const uint64_t t = p.big_list[idx];
-        const unsigned long long off = p.tile_off[t];
-        const unsigned long long cnt = p.tile_off[t + 1] - off;
-        bool bad = false;
-        if (cnt > p.scratch_cap) {
-            if (threadIdx.x == 0) atomicOr(p.err, kErrScratch);
-            bad = true;
-        }
-        // round 1: Rec32 chunks -> reduced Rec48 in bufA
-        unsigned long long u = 0;
-        for (unsigned long long cs = 0; !bad && cs < cnt; cs += kTileCap) {
-            const int m = (int)min((unsigned long long)kTileCap, cnt - cs);
-            if (threadIdx.x == 0) {
-                fence_proxy_async_smem();
-                bulk_load(M.u.r32, p.recs + off + cs, (uint32_t)(m * sizeof(Rec32)), &M.bar);
-                M.out_count = 0;
-            }
-            mbar_wait_bounded(&M.bar, phase, p.err);
-            phase ^= 1;
-            __syncthreads();
-            chunk_to_partials(M.u.r32, m, M, bufA + u, st.err);
-            u += M.out_count;
-            __syncthreads();
-        }
-        // further rounds until the reduced list fits one chunk
-        Rec48 *src = bufA, *dst = bufB;
-        while (!bad && u > (unsigned long long)kBigCap) {
-            unsigned long long u2 = 0;
-            for (unsigned long long cs = 0; cs < u; cs += kBigCap) {
-                const int m = (int)min((unsigned long long)kBigCap, u - cs);
-                if (threadIdx.x == 0) M.out_count = 0;
-                for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[cs + i];
+    for (int inst = 0; inst < p.n_inst; ++inst) {
+        const unsigned int nbig = p.n_big[inst];
+        if ((unsigned)blockIdx.x >= nbig) continue;  // uniform: nothing of this instance for this CTA
+        const double e0 = p.e0[inst];
+        KeyStats st;
+        st.clear();
+        for (unsigned int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
+            const uint64_t t = p.big_list[p.tile_base[inst] + idx];
+            const unsigned long long off = p.tile_off[t];
+            const unsigned long long cnt = p.tile_off[t + 1] - off;
+            bool bad = false;
+            // round 1: Rec32 chunks -> reduced Rec48 in bufA
+            unsigned long long u = 0;
+            for (unsigned long long cs = 0; !bad && cs < cnt; cs += kTileCap) {
+                const int m = (int)min((unsigned long long)kTileCap, cnt - cs);
+                if (u + (unsigned long long)m > p.scratch_cap) {  // uniform
+                    if (threadIdx.x == 0) atomicOr(p.err, kErrScratch);
+                    bad = true;
+                    break;
+                }
+                if (threadIdx.x == 0) {
+                    fence_proxy_async_smem();
+                    bulk_load(M.u.r32, p.recs + off + cs, (uint32_t)(m * sizeof(Rec32)), &M.bar);
+                    M.out_count = 0;
+                }
+                mbar_wait_bounded(&M.bar, phase, p.err);
+                phase ^= 1;
                 __syncthreads();
-                chunk_to_partials(M.u.r48, m, M, dst + u2, st.err);
-                u2 += M.out_count;
+                chunk_to_partials(M.u.r32, m, M, bufA + u, st.err);
+                u += M.out_count;
                 __syncthreads();
             }
-            if (u2 >= u) {
-                if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
-                bad = true;
-                break;
+            // further rounds until the reduced list fits one chunk
+            Rec48 *src = bufA, *dst = bufB;
+            while (!bad && u > (unsigned long long)kBigCap) {
+                unsigned long long u2 = 0;
+                for (unsigned long long cs = 0; cs < u; cs += kBigCap) {
+                    const int m = (int)min((unsigned long long)kBigCap, u - cs);
+                    if (threadIdx.x == 0) M.out_count = 0;
+                    for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[cs + i];
+                    __syncthreads();
+                    chunk_to_partials(M.u.r48, m, M, dst + u2, st.err);
+                    u2 += M.out_count;
+                    __syncthreads();
+                }
+                if (u2 >= u) {
+                    if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
+                    bad = true;
+                    break;
+                }
+                Rec48 *tmp = src;
+                src = dst;
+                dst = tmp;
+                u = u2;
             }
-            Rec48 *tmp = src;
-            src = dst;
-            dst = tmp;
-            u = u2;
-        }
-        // final sort-reduce and the energy
-        unsigned long long nrk;
-        const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
-        if (!bad) {
-            const int m = (int)u;
-            for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
+            // final sort-reduce and the energy
+            unsigned long long nrk;
+            const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
+            if (!bad) {
+                const int m = (int)u;
+                for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
+                __syncthreads();
+                auto fin = [&](const KeyVal &v) { finish_keyval(p, e0, rk, nrk, v, st); };
+                if (!sort_reduce_chunk(M.u.r48, m, M.S, st.err, fin))
+                    exact_reduce_chunk(M.u.r48, m, M.S, st.err, fin);
+            }
             __syncthreads();
-            auto fin = [&](const KeyVal &v) { finish_keyval(p, rk, nrk, v, st); };
-            if (!sort_reduce_chunk(M.u.r48, m, M.S, st.err, fin)) exact_reduce_chunk(M.u.r48, m, M.S, st.err, fin);
         }
+        flush_stats(p, p.acc[inst], st, M.S.u.red);
         __syncthreads();
     }
-    flush_stats(p, st, M.S.u.red);
-    __syncthreads();
     if (threadIdx.x == 0) mbar_inval(&M.bar);
 }
 
 cudaError_t launch_big_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 {
     if (n_ctas <= 0) return cudaSuccess;
-    size_t sm = big_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(big_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    big_tile_kernel<<<n_ctas, kBigThreads, sm, s>>>(p);
+    big_tile_kernel<<<n_ctas, kBigThreads, big_smem_bytes(), s>>>(p);
     return cudaGetLastError();
 }
 
 // ========================================================= pass bookkeeping
 
-__global__ void pass_finish_kernel(const unsigned long long *__restrict__ tile_off, uint64_t n_tiles,
-                                   unsigned long long expected, RunAcc *acc, uint32_t *err)
+// Per instance: count the pass's records, compare them with the plan and
+// reset the oversize counter for the next pass.
+__global__ void pass_finish_kernel(const unsigned long long *__restrict__ tile_off,
+                                   const unsigned long long *__restrict__ tile_base, int n_inst,
+                                   const unsigned long long *__restrict__ expected, RunAcc *const *acc,
+                                   unsigned int *n_big, uint32_t *err)
 {
-    unsigned long long got = tile_off[n_tiles];
-    acc->n_terms += got;
-    if (got != expected) atomicOr(err, kErrCount);
-    acc->n_big = 0;
-    acc->big_max = 0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const unsigned long long got = tile_off[tile_base[i + 1]] - tile_off[tile_base[i]];
+    acc[i]->n_terms += got;
+    if (got != expected[i]) atomicOr(err, kErrCount);
+    n_big[i] = 0;
 }
 
-cudaError_t launch_pass_finish(const unsigned long long *tile_off, uint64_t n_tiles,
-                               unsigned long long expected_terms, RunAcc *acc, uint32_t *err, cudaStream_t s)
+cudaError_t launch_pass_finish(const unsigned long long *tile_off, const unsigned long long *tile_base, int n_inst,
+                               const unsigned long long *expected, RunAcc *const *acc, unsigned int *n_big,
+                               uint32_t *err, cudaStream_t s)
 {
-    pass_finish_kernel<<<1, 1, 0, s>>>(tile_off, n_tiles, expected_terms, acc, err);
+    pass_finish_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(tile_off, tile_base, n_inst, expected, acc, n_big, err);
     return cudaGetLastError();
 }
 
-__global__ void acc_init_kernel(RunAcc *acc)
+__global__ void acc_init_kernel(RunAcc *acc, int n)
 {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
     RunAcc a;
     a.e2_lo = 0;
     a.e2_hi = 0;
@@ -1790,24 +1878,27 @@ __global__ void acc_init_kernel(RunAcc *acc)
     a.err = 0;
     a.n_big = 0;
     a.big_max = 0;
-    *acc = a;
+    acc[i] = a;
 }
 
-cudaError_t launch_acc_init(RunAcc *acc, cudaStream_t s)
+cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s)
 {
-    acc_init_kernel<<<1, 1, 0, s>>>(acc);
+    acc_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(acc, n);
     return cudaGetLastError();
 }
 
-__global__ void acc_finalize_kernel(RunAcc *acc)
+__global__ void acc_finalize_kernel(RunAcc *acc, int n)
 {
-    acc->e2 = fx_to_double(acc->e2_lo, acc->e2_hi);
-    acc->min_abs_den = acc->min_den == ~0ull ? INFINITY : u128_to_double(acc->min_den, 0, kDenShift, false);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    acc[i].e2 = fx_to_double(acc[i].e2_lo, acc[i].e2_hi);
+    acc[i].min_abs_den =
+        acc[i].min_den == ~0ull ? INFINITY : u128_to_double(acc[i].min_den, 0, kDenShift, false);
 }
 
-cudaError_t launch_acc_finalize(RunAcc *acc, cudaStream_t s)
+cudaError_t launch_acc_finalize(RunAcc *acc, int n, cudaStream_t s)
 {
-    acc_finalize_kernel<<<1, 1, 0, s>>>(acc);
+    acc_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(acc, n);
     return cudaGetLastError();
 }
 
@@ -1830,25 +1921,49 @@ void gen_layout(GenParams &p, GenMode mode)
     p.smem_bytes = (int)off;
 }
 
-cudaError_t launch_gen(GenMode mode, const GenParams &p, uint64_t n_dets, cudaStream_t s)
+cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int smem_bytes, cudaStream_t s)
 {
-    if (n_dets == 0) return cudaSuccess;
-    const void *fn = nullptr;
+    if (n_ctas == 0) return cudaSuccess;
     switch (mode) {
-    case kModeClassCount: fn = (const void *)gen_kernel<kModeClassCount>; break;
-    case kModeTileCount: fn = (const void *)gen_kernel<kModeTileCount>; break;
-    case kModeEmit: fn = (const void *)gen_kernel<kModeEmit>; break;
-    case kModeDetTerms: fn = (const void *)gen_kernel<kModeDetTerms>; break;
-    }
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
-    if (e != cudaSuccess) return e;
-    switch (mode) {
-    case kModeClassCount: gen_kernel<kModeClassCount><<<(unsigned)n_dets, kGenThreads, p.smem_bytes, s>>>(p); break;
-    case kModeTileCount: gen_kernel<kModeTileCount><<<(unsigned)n_dets, kGenThreads, p.smem_bytes, s>>>(p); break;
-    case kModeEmit: gen_kernel<kModeEmit><<<(unsigned)n_dets, kGenThreads, p.smem_bytes, s>>>(p); break;
-    case kModeDetTerms: gen_kernel<kModeDetTerms><<<(unsigned)n_dets, kGenThreads, p.smem_bytes, s>>>(p); break;
+    case kModeClassCount: gen_kernel<kModeClassCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeTileCount: gen_kernel<kModeTileCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeEmit: gen_kernel<kModeEmit><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_gen_single(GenMode mode, const GenParams &p, GenParams *, unsigned long long *, cudaStream_t s)
+{
+    if (mode != kModeDetTerms) return cudaErrorInvalidValue;
+    gen_kernel_one<kModeDetTerms><<<1, kGenThreads, p.smem_bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+// Largest dynamic shared memory any generator layout needs (n_orb = 64).
+static int gen_smem_max()
+{
+    GenParams p;
+    p.n_sa = 32 * 32;
+    p.n_sb = 32 * 32;
+    gen_layout(p, kModeClassCount);
+    return p.smem_bytes;
+}
+
+cudaError_t init_kernel_attributes()
+{
+    const int g = gen_smem_max();
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(gen_kernel<kModeClassCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
+        return e;
+    if ((e = cudaFuncSetAttribute(gen_kernel<kModeTileCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
+        return e;
+    if ((e = cudaFuncSetAttribute(gen_kernel<kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    if ((e = cudaFuncSetAttribute(gen_kernel_one<kModeDetTerms>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
+        return e;
+    if ((e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes())))
+        return e;
+    return cudaFuncSetAttribute(big_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem_bytes());
 }
 
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s)
@@ -1917,7 +2032,7 @@ cudaError_t launch_det_terms_noalloc(int device, GenParams p, uint64_t cap, uint
     p.n_tiles = 1;
     gen_layout(p, kModeDetTerms);
     if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-    if ((e = launch_gen(kModeDetTerms, p, 1, s)) != cudaSuccess) return e;
+    if ((e = launch_gen_single(kModeDetTerms, p, nullptr, nullptr, s)) != cudaSuccess) return e;
     split_terms_kernel<<<64, 256, 0, s>>>(recs, count, cap, keys, val, haa);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(n_host, count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

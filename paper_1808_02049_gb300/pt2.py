@@ -25,10 +25,13 @@ PT2_ERR_BUSY = -5
 PT2_ERR_NOT_FOUND = -6
 PT2_ERR_UNSUPPORTED = -7
 PT2_FLAG_PROFILE = 1
+PT2_FLAG_AUTOTUNE = 2
 
 EXPORTS = ["pt2_create", "pt2_destroy", "pt2_last_error", "pt2_load_system", "pt2_load_reference",
-           "pt2_unload", "pt2_diagonal", "pt2_run", "pt2_dump_external", "pt2_det_terms",
-           "pt2_det_terms_noalloc", "pt2_phase_times", "pt2_memory_info", "pt2_stream"]
+           "pt2_unload", "pt2_diagonal", "pt2_run", "pt2_dump_external", "pt2_batch_create", "pt2_batch_run",
+           "pt2_batch_info", "pt2_batch_destroy", "pt2_autotune", "pt2_submit", "pt2_poll", "pt2_wait",
+           "pt2_server_stats", "pt2_det_terms", "pt2_det_terms_noalloc", "pt2_phase_times", "pt2_memory_info",
+           "pt2_stream"]
 
 PHASES = ["class_count", "tile_count", "scan", "emit", "ref_partition", "tile_sort_reduce",
           "oversize_tiles", "pass_reduce"]
@@ -83,6 +86,15 @@ def load_library(path: str = LIB_PATH):
         "pt2_run": (i32, [P, u32, ctypes.POINTER(pt2_opts), ctypes.POINTER(pt2_result)]),
         "pt2_dump_external": (i32, [P, u32, ctypes.POINTER(pt2_opts), P, P, P, u64, pu64]),
         "pt2_det_terms": (i32, [P, u32, u64, P, P, P, u64, pu64]),
+        "pt2_batch_create": (i32, [P, u32, P, ctypes.POINTER(pt2_opts), pu32]),
+        "pt2_batch_run": (i32, [P, u32, ctypes.POINTER(pt2_result)]),
+        "pt2_batch_info": (i32, [P, u32, pu32, pu64, pu64]),
+        "pt2_batch_destroy": (i32, [P, u32]),
+        "pt2_autotune": (i32, [P, u32, ctypes.POINTER(pt2_opts), pu32]),
+        "pt2_submit": (i32, [P, u32, ctypes.POINTER(pt2_opts), pu64]),
+        "pt2_poll": (i32, [P, u64, ctypes.POINTER(pt2_result)]),
+        "pt2_wait": (i32, [P, u64, u64, ctypes.POINTER(pt2_result)]),
+        "pt2_server_stats": (i32, [P, pu64, pu64, pu64]),
         "pt2_det_terms_noalloc": (i32, [P, u32, u64, P, P, P, u64, pu64]),
         "pt2_phase_times": (i32, [P, P, i32, pu64]),
         "pt2_memory_info": (i32, [P, pu64, pu64, pu64]),
@@ -107,12 +119,12 @@ def _check(ctx, rc):
     return rc
 
 
-def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False) -> pt2_opts:
+def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
     o.tile_target = int(tile_target)
-    o.flags = PT2_FLAG_PROFILE if profile else 0
+    o.flags = (PT2_FLAG_PROFILE if profile else 0) | (PT2_FLAG_AUTOTUNE if autotune else 0)
     return o
 
 
@@ -181,6 +193,66 @@ def pt2_dump_external(ctx, ref_id: int, cap: int, opts: pt2_opts | None = None):
                                                  _ptr(keys), _ptr(num), _ptr(haa), int(cap), ctypes.byref(n)))
     m = n.value
     return keys[: 2 * m].reshape(m, 2), num[:m], haa[:m]
+
+
+def pt2_batch_create(ctx, ref_ids, opts: pt2_opts | None = None) -> int:
+    ids = np.ascontiguousarray(ref_ids, dtype=np.uint32)
+    bid = ctypes.c_uint32()
+    _check(ctx, load_library().pt2_batch_create(ctx, ids.shape[0], _ptr(ids), ctypes.byref(opts) if opts else None,
+                                                ctypes.byref(bid)))
+    return bid.value
+
+
+def pt2_batch_run(ctx, batch_id: int, n: int) -> list:
+    res = (pt2_result * n)()
+    _check(ctx, load_library().pt2_batch_run(ctx, int(batch_id), res))
+    return [r.as_dict() for r in res]
+
+
+def pt2_batch_info(ctx, batch_id: int) -> dict:
+    st, te, la = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, load_library().pt2_batch_info(ctx, int(batch_id), ctypes.byref(st), ctypes.byref(te),
+                                              ctypes.byref(la)))
+    return {"steps": st.value, "n_terms": te.value, "launches": la.value}
+
+
+def pt2_batch_destroy(ctx, batch_id: int):
+    _check(ctx, load_library().pt2_batch_destroy(ctx, int(batch_id)))
+
+
+def pt2_autotune(ctx, ref_id: int, opts: pt2_opts | None = None) -> int:
+    best = ctypes.c_uint32()
+    _check(ctx, load_library().pt2_autotune(ctx, int(ref_id), ctypes.byref(opts) if opts else None,
+                                            ctypes.byref(best)))
+    return best.value
+
+
+def pt2_submit(ctx, ref_id: int, opts: pt2_opts | None = None) -> int:
+    t = ctypes.c_uint64()
+    _check(ctx, load_library().pt2_submit(ctx, int(ref_id), ctypes.byref(opts) if opts else None, ctypes.byref(t)))
+    return t.value
+
+
+def pt2_poll(ctx, ticket: int):
+    """The result dict once the request finished, None while it runs."""
+    res = pt2_result()
+    rc = load_library().pt2_poll(ctx, int(ticket), ctypes.byref(res))
+    if rc == PT2_ERR_BUSY:
+        return None
+    _check(ctx, rc)
+    return res.as_dict()
+
+
+def pt2_wait(ctx, ticket: int, timeout_s: float = 3600.0) -> dict:
+    res = pt2_result()
+    _check(ctx, load_library().pt2_wait(ctx, int(ticket), int(timeout_s * 1e9), ctypes.byref(res)))
+    return res.as_dict()
+
+
+def pt2_server_stats(ctx) -> dict:
+    p, a, s_ = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, load_library().pt2_server_stats(ctx, ctypes.byref(p), ctypes.byref(a), ctypes.byref(s_)))
+    return {"pending": p.value, "active": a.value, "steps": s_.value}
 
 
 def pt2_det_terms(ctx, ref_id: int, det_index: int, cap: int):
@@ -265,6 +337,33 @@ class Context:
 
     def det_terms(self, ref_id, det_index, cap):
         return pt2_det_terms(self.handle, ref_id, det_index, cap)
+
+    def batch_create(self, ref_ids, **kw):
+        return pt2_batch_create(self.handle, ref_ids, make_opts(**kw) if kw else None)
+
+    def batch_run(self, batch_id, n):
+        return pt2_batch_run(self.handle, batch_id, n)
+
+    def batch_info(self, batch_id):
+        return pt2_batch_info(self.handle, batch_id)
+
+    def batch_destroy(self, batch_id):
+        pt2_batch_destroy(self.handle, batch_id)
+
+    def autotune(self, ref_id, **kw):
+        return pt2_autotune(self.handle, ref_id, make_opts(**kw) if kw else None)
+
+    def submit(self, ref_id, **kw):
+        return pt2_submit(self.handle, ref_id, make_opts(**kw) if kw else None)
+
+    def poll(self, ticket):
+        return pt2_poll(self.handle, ticket)
+
+    def wait(self, ticket, timeout_s=3600.0):
+        return pt2_wait(self.handle, ticket, timeout_s)
+
+    def server_stats(self):
+        return pt2_server_stats(self.handle)
 
     def phase_times(self):
         return pt2_phase_times(self.handle)

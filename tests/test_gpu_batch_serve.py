@@ -1,0 +1,114 @@
+"""Batched and served PT2: many uneven instances in one captured launch, and
+continuous batching of submitted requests.
+
+Energies and set statistics are accumulated exactly, so an instance's result
+must be bit-identical alone (pt2_run), inside a batch and inside a served
+mix; the smallest instances are also checked against the oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_02049_gb300 import inputs, pt2
+
+pytestmark = pytest.mark.gpu
+
+SAME = ("e2", "n_terms", "n_unique", "n_in_ref", "n_external", "digest_sum", "digest_xor", "n_pos_denom",
+        "min_abs_denom")
+
+
+def same(a, b):
+    return all(a[k] == b[k] for k in SAME)
+
+
+@pytest.fixture(scope="module")
+def fleet():
+    from paper_1808_02049_gb300 import build
+
+    build.build_library()
+    c = pt2.Context(0)
+    refs = []
+    for k in range(10):
+        prm = inputs.batch_instance_params(k)
+        prm["n_det"] = min(prm["n_det"], 600 + 150 * k)  # keep the test quick
+        s, r = inputs.make_instance(prm)
+        sid = c.load_system(s.h, s.eri)
+        e0 = float(c.diagonal(sid, r.keys).min() - 0.1)
+        rid = c.load_reference(sid, r.keys, r.coef, e0)
+        refs.append(dict(sid=sid, rid=rid, s=s, r=r, e0=e0, alone=c.run(rid)))
+    yield c, refs
+    c.close()
+
+
+def test_batch_matches_single_runs_and_oracle(fleet):
+    c, refs = fleet
+    ids = [x["rid"] for x in refs]
+    bid = c.batch_create(ids)
+    try:
+        info = c.batch_info(bid)
+        assert info["steps"] >= 1 and info["n_terms"] == sum(x["alone"]["n_terms"] for x in refs)
+        res = c.batch_run(bid, len(ids))
+        again = c.batch_run(bid, len(ids))  # graph replay
+    finally:
+        c.batch_destroy(bid)
+    for x, got, rep in zip(refs, res, again):
+        assert same(got, x["alone"]), (got, x["alone"])
+        assert same(rep, got)
+    small = sorted(refs, key=lambda x: x["alone"]["n_terms"])[:2]
+    for x in small:
+        ref = oracle.pt2(x["s"].h, x["s"].eri, x["r"].keys, x["r"].coef, x["e0"])
+        assert x["alone"]["n_external"] == ref["n_external"]
+        assert (x["alone"]["digest_sum"], x["alone"]["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
+        assert abs(x["alone"]["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
+
+
+def test_batch_with_small_step_budget_and_autotune(fleet):
+    c, refs = fleet
+    ids = [x["rid"] for x in refs]
+    best = c.autotune(refs[3]["rid"])
+    assert best in (320, 448, 576, 704)
+    # a small pass budget splits instances into many passes packed into steps
+    bid = c.batch_create(ids, pass_budget_bytes=64 << 20, autotune=True)
+    try:
+        assert c.batch_info(bid)["steps"] > 1
+        res = c.batch_run(bid, len(ids))
+    finally:
+        c.batch_destroy(bid)
+    for x, got in zip(refs, res):
+        assert same(got, x["alone"])
+
+
+def test_served_mix_matches_single_runs(fleet):
+    c, refs = fleet
+    order = [3, 1, 4, 1, 5, 9, 2, 6, 5, 3, 5, 8, 9, 7, 0]
+    tickets = [(c.submit(refs[i]["rid"]), i) for i in order]
+    for t, i in tickets:
+        got = c.wait(t, timeout_s=600)
+        assert same(got, refs[i]["alone"]), (i, got, refs[i]["alone"])
+        assert got["seconds"] > 0
+    st = c.server_stats()
+    assert st["pending"] == 0 and st["active"] == 0 and st["steps"] >= 1
+    with pytest.raises(pt2.Pt2Error) as e:  # a finished ticket is reported once
+        c.poll(tickets[0][0])
+    assert e.value.code == pt2.PT2_ERR_NOT_FOUND
+
+
+def test_served_request_timeout_and_busy_reference():
+    from paper_1808_02049_gb300 import build
+
+    build.build_library()
+    s, r = inputs.make_config(1, n_det=8000)  # ~1e9 terms: runs for a while
+    with pt2.Context(0) as c:
+        sid = c.load_system(s.h, s.eri)
+        e0 = float(c.diagonal(sid, r.keys).min() - 0.1)
+        rid = c.load_reference(sid, r.keys, r.coef, e0)
+        t = c.submit(rid)
+        with pytest.raises(pt2.Pt2Error) as e:
+            pt2.pt2_wait(c.handle, t, 0.0)
+        assert e.value.code == pt2.PT2_ERR_TIMEOUT
+        with pytest.raises(pt2.Pt2Error) as e:
+            c.unload(rid)  # still in flight
+        assert e.value.code == pt2.PT2_ERR_BUSY
+        got = c.wait(t, timeout_s=600)
+        assert same(got, c.run(rid))
