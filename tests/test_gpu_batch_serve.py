@@ -69,7 +69,7 @@ def test_batch_with_small_step_budget_and_autotune(fleet):
     best = c.autotune(refs[3]["rid"])
     assert best in (320, 448, 576, 704)
     # a small pass budget splits instances into many passes packed into steps
-    bid = c.batch_create(ids, pass_budget_bytes=64 << 20, autotune=True)
+    bid = c.batch_create(ids, pass_budget_bytes=200 << 20, autotune=True)
     try:
         assert c.batch_info(bid)["steps"] > 1
         res = c.batch_run(bid, len(ids))
