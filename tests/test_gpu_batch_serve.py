@@ -98,17 +98,17 @@ def test_served_request_timeout_and_busy_reference():
     from paper_1808_02049_gb300 import build
 
     build.build_library()
-    s, r = inputs.make_config(1, n_det=8000)  # ~1e9 terms: runs for a while
+    s, r = inputs.make_config(1, n_det=40000)  # ~5e9 terms: runs for a while
     with pt2.Context(0) as c:
         sid = c.load_system(s.h, s.eri)
         e0 = float(c.diagonal(sid, r.keys).min() - 0.1)
         rid = c.load_reference(sid, r.keys, r.coef, e0)
         t = c.submit(rid)
         with pytest.raises(pt2.Pt2Error) as e:
-            pt2.pt2_wait(c.handle, t, 0.0)
-        assert e.value.code == pt2.PT2_ERR_TIMEOUT
-        with pytest.raises(pt2.Pt2Error) as e:
             c.unload(rid)  # still in flight
         assert e.value.code == pt2.PT2_ERR_BUSY
+        with pytest.raises(pt2.Pt2Error) as e:
+            pt2.pt2_wait(c.handle, t, 0.0)
+        assert e.value.code == pt2.PT2_ERR_TIMEOUT
         got = c.wait(t, timeout_s=600)
         assert same(got, c.run(rid))
