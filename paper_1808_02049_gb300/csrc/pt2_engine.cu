@@ -376,6 +376,7 @@ void result_of(const RunAcc &h, const Job &j, pt2_result *out)
     uint64_t tiles = 0;
     for (const auto &p : j.passes) tiles += p.n_tiles;
     out->n_tiles = (uint32_t)std::min<uint64_t>(tiles, 0xFFFFFFFFull);
+    out->n_oversize = h.n_big;
 }
 
 // Upload the device tables of a list of steps (one pinned staging copy).

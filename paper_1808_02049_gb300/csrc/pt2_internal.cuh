@@ -124,8 +124,8 @@ struct RunAcc {
     double e2;                   // filled by the finalize kernel
     double min_abs_den;
     unsigned int err;
-    unsigned int n_big;
-    unsigned long long big_max;  // largest oversize tile of the last pass
+    unsigned int n_big;          // oversize tiles over all passes
+    unsigned long long big_max;  // unused
 };
 
 // Tiles of a step cover several instances: tile t belongs to the instance

@@ -1852,6 +1852,7 @@ __global__ void pass_finish_kernel(const unsigned long long *__restrict__ tile_o
     if (i >= n_inst) return;
     const unsigned long long got = tile_off[tile_base[i + 1]] - tile_off[tile_base[i]];
     acc[i]->n_terms += got;
+    acc[i]->n_big += n_big[i];
     if (got != expected[i]) atomicOr(err, kErrCount);
     n_big[i] = 0;
 }
