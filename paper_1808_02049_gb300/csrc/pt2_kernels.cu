@@ -1575,8 +1575,6 @@ struct MainSmem {
     SortSmem S;
     uint64_t rk[2 * kRefSliceSmem];
     unsigned long long meta[4];  // current tile: offset, count, reference offset, reference count
-    unsigned long long tb[kMaxBatch + 1];
-    double e0[kMaxBatch];
     uint64_t bar[2];
 };
 
@@ -1612,8 +1610,8 @@ __device__ __forceinline__ void push_oversize(const TileParams &p, int inst, uin
     atomicMax(p.big_max, cnt);
 }
 
-// Instance of global tile t (tile_base is in shared memory).
-__device__ __forceinline__ int tile_instance(const unsigned long long *tb, int n_inst, uint64_t t)
+// Instance of global tile t.
+__device__ __forceinline__ int tile_instance(const unsigned long long *__restrict__ tb, int n_inst, uint64_t t)
 {
     int lo = 0, hi = n_inst;
     while (hi - lo > 1) {
@@ -1633,8 +1631,6 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
     const uint64_t G = gridDim.x;
-    for (int i = threadIdx.x; i <= p.n_inst; i += blockDim.x) M.tb[i] = p.tile_base[i];
-    for (int i = threadIdx.x; i < p.n_inst; i += blockDim.x) M.e0[i] = p.e0[i];
     KeyStats st;
     st.clear();
     TileMeta nx{0, 0, 0, 0};
@@ -1643,11 +1639,11 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
         nx = tile_meta(p, blockIdx.x);
     }
     __syncthreads();
-    int cur = tile_instance(M.tb, p.n_inst, blockIdx.x);
+    int cur = tile_instance(p.tile_base, p.n_inst, blockIdx.x);
     bool dirty = false;
     uint32_t phase = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G) {
-        const int inst = tile_instance(M.tb, p.n_inst, t);
+        const int inst = tile_instance(p.tile_base, p.n_inst, t);
         if (inst != cur) {  // uniform across the CTA
             if (dirty) flush_stats(p, p.acc[cur], st, M.S.u.red);
             st.clear();
@@ -1669,7 +1665,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
             if (threadIdx.x == 0) push_oversize(p, inst, t, cntl);
         } else if (cntl > 0) {
             const int cnt = (int)cntl;
-            const double e0 = M.e0[inst];
+            const double e0 = p.e0[inst];
             const uint64_t *rk = M.rk;
             if (rcnt <= (unsigned long long)kRefSliceSmem) {
                 for (unsigned long long i = threadIdx.x; i < 2 * rcnt; i += blockDim.x)
