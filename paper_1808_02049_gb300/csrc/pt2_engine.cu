@@ -130,7 +130,7 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
     GenBatch b{reinterpret_cast<const GenParams *>(c->gen_tab.ptr),
                reinterpret_cast<const unsigned long long *>(static_cast<char *>(c->gen_tab.ptr) +
                                                             n * sizeof(GenParams)),
-               (int)n, 0};
+               (int)n, 0, hp[0]};
     CK(gen_launch(c, kModeClassCount, b, cta, smem), "class count kernel");
     std::vector<unsigned long long> cls(n * kNumClasses);
     CK(cudaMemcpyAsync(cls.data(), c->class_counts.ptr, n * kNumClasses * 8, cudaMemcpyDeviceToHost, st), "copy");
@@ -234,6 +234,26 @@ int step_smem(const StepPlan &sp)
     return m;
 }
 
+// Generator parameters of item i of a step whose tiles start at tile_base.
+GenParams step_item_params(pt2_ctx *c, const StepPlan &sp, size_t i, uint64_t tile_base)
+{
+    const Job &j = *sp.items[i].job;
+    const Pass &P = j.passes[sp.items[i].pass];
+    GenParams g = j.gp;
+    g.class_lo = P.c_lo;
+    g.class_hi = P.c_hi;
+    g.n_tiles = P.n_tiles;
+    g.tile_base = tile_base;
+    g.det_begin = 0;
+    g.class_counts = nullptr;
+    g.tile_counts = reinterpret_cast<uint32_t *>(c->tile_counts.ptr);
+    g.cursor = reinterpret_cast<unsigned long long *>(c->cursor.ptr);
+    g.recs = reinterpret_cast<Rec32 *>(c->recs.ptr);
+    g.rec_cap = sp.records;
+    gen_layout(g, kModeEmit);
+    return g;
+}
+
 void fill_step(pt2_ctx *c, const StepPlan &sp, StepDev &h)
 {
     uint64_t cta = 0, tb = 0;
@@ -241,19 +261,7 @@ void fill_step(pt2_ctx *c, const StepPlan &sp, StepDev &h)
     for (size_t i = 0; i < n; ++i) {
         Job &j = *sp.items[i].job;
         const Pass &P = j.passes[sp.items[i].pass];
-        GenParams g = j.gp;
-        g.class_lo = P.c_lo;
-        g.class_hi = P.c_hi;
-        g.n_tiles = P.n_tiles;
-        g.tile_base = tb;
-        g.det_begin = 0;
-        g.class_counts = nullptr;
-        g.tile_counts = reinterpret_cast<uint32_t *>(c->tile_counts.ptr);
-        g.cursor = reinterpret_cast<unsigned long long *>(c->cursor.ptr);
-        g.recs = reinterpret_cast<Rec32 *>(c->recs.ptr);
-        g.rec_cap = sp.records;
-        gen_layout(g, kModeEmit);
-        h.params[i] = g;
+        h.params[i] = step_item_params(c, sp, i, tb);
         h.det_base[i] = cta;
         h.tile_base[i] = tb;
         h.e0[i] = j.r->e0;
@@ -283,7 +291,8 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     cudaEvent_t *E = &c->ev[2];
     if (prof) CK(cudaEventRecord(E[0], st), "event");
     CK(cudaMemsetAsync(c->tile_counts.ptr, 0, sp.n_tiles * 4, st), "memset");
-    GenBatch gb{d->params, d->det_base, n, 0};
+    GenBatch gb{d->params, d->det_base, n, 0, {}};
+    if (n == 1) gb.one = step_item_params(c, sp, 0, 0);
     const int smem = step_smem(sp);
     CK(gen_launch(c, kModeTileCount, gb, sp.n_ctas, smem), "tile count kernel");
     if (prof) CK(cudaEventRecord(E[1], st), "event");

@@ -113,6 +113,9 @@ struct GenBatch {
     const unsigned long long *det_base;  // n_inst + 1
     int n_inst;
     unsigned long long cta_offset;
+    // n_inst == 1: the instance's parameters, read from the launch arguments
+    // (constant bank) instead of the device table
+    GenParams one;
 };
 
 // Run accumulator: every field is an exact integer reduction.

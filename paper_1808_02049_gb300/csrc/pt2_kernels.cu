@@ -714,6 +714,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 template <int MODE>
 __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenBatch b)
 {
+    if (b.n_inst == 1) {
+        gen_body<MODE>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
+        return;
+    }
     __shared__ GenParams sp;
     __shared__ unsigned long long sdet;
     if (threadIdx.x == 0) {
