@@ -44,10 +44,16 @@ def dist_env():
     return rank, world, local
 
 
-def workload():
+def workload(n_det=None):
     from paper_1808_02049_gb300 import inputs
 
-    return inputs.make_config(1)
+    return inputs.make_config(1, n_det=n_det)
+
+
+def workload_name(n_det):
+    if not n_det:
+        return WORKLOAD
+    return WORKLOAD.replace("N_det=100000", f"N_det={n_det} (reduced case)")
 
 
 def cpu_baseline(s, r, e0):
@@ -115,6 +121,116 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def load_fleet(ctx, n=64):
+    """The 64 uneven instances of the batched workload, loaded and resident."""
+    from paper_1808_02049_gb300 import inputs
+
+    fleet = []
+    for k in range(n):
+        prm = inputs.batch_instance_params(k)
+        s, r = inputs.make_instance(prm)
+        sid = ctx.load_system(s.h, s.eri)
+        e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
+        fleet.append(dict(sid=sid, rid=ctx.load_reference(sid, r.keys, r.coef, e0), prm=prm))
+    return fleet
+
+
+SAME = ("e2", "n_terms", "n_unique", "n_in_ref", "n_external", "digest_sum", "digest_xor", "n_pos_denom")
+
+
+def timed_run(ctx, rid):
+    t = time.perf_counter()
+    res = ctx.run(rid)
+    return res, time.perf_counter() - t
+
+
+def bench_batched(ctx, fleet, reps):
+    """64 instances: one captured batch (autotuned tile targets) against
+    pt2_run of each instance one after the other (wall time of the blocking
+    calls in both cases)."""
+    for x in fleet:  # warm-up, and each instance's result alone
+        x["alone"], _ = timed_run(ctx, x["rid"])
+    serial = []
+    for _ in range(reps):
+        t = 0.0
+        for x in fleet:
+            _, dt = timed_run(ctx, x["rid"])
+            x["alone_s"] = dt
+            t += dt
+        serial.append(t)
+    ids = [x["rid"] for x in fleet]
+    t0 = time.perf_counter()
+    bid = ctx.batch_create(ids, autotune=True)
+    create_s = time.perf_counter() - t0
+    try:
+        info = ctx.batch_info(bid)
+        res = ctx.batch_run(bid, len(ids))  # warm-up replay
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            res = ctx.batch_run(bid, len(ids))
+            times.append(time.perf_counter() - t0)
+    finally:
+        ctx.batch_destroy(bid)
+    terms = sum(x["alone"]["n_terms"] for x in fleet)
+    identical = all(all(g[k] == x["alone"][k] for k in SAME) for g, x in zip(res, fleet))
+    d_e2 = max(abs(g["e2"] - x["alone"]["e2"]) for g, x in zip(res, fleet))
+    tb, ts = min(times), min(serial)
+    return {"workload": "64 independent instances, n_orb U{16..40}, 4-10 electrons per spin, "
+                        "N_det log-uniform in [1e3, 5e4], seeded synthetic FP64 integrals",
+            "terms": terms, "steps": info["steps"], "gpu_launches": info["launches"],
+            "batched_terms_per_s": terms / tb, "batched_s": tb,
+            "serial_terms_per_s": terms / ts, "serial_s": ts, "speedup_vs_serial": ts / tb,
+            "capture_and_autotune_s": create_s, "max_abs_dE2_vs_alone": d_e2,
+            "bit_identical_to_alone": identical,
+            "timing": "wall time of the blocking C-ABI calls, best of %d" % reps}
+
+
+def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
+    """Poisson stream of solves: 90% instances of the batched workload, 10% the
+    one-large-solve workload.  Latency = submission to completion; plain =
+    the same arrivals served first-come first-served by pt2_run alone, from
+    each request's measured pt2_run time."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pool = [(x["rid"], x["alone"], x["alone_s"]) for x in fleet]
+    reqs = [big if rng.random() < 0.1 else pool[int(rng.integers(len(pool)))] for _ in range(n_req)]
+    mean_service = float(np.mean([r[2] for r in reqs]))
+    rate = load / mean_service  # offered load relative to the plain path's capacity
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    tickets = []
+    t0 = time.perf_counter()
+    for (rid, _, _), ta in zip(reqs, arrivals):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append((ctx.submit(rid), time.perf_counter() - t0))
+    lat, done, identical, d_e2 = [], [], True, 0.0
+    for (t, ts), (_, alone, _) in zip(tickets, reqs):
+        got = ctx.wait(t, timeout_s=3600)
+        lat.append(got["seconds"])
+        done.append(ts + got["seconds"])
+        identical &= all(got[k] == alone[k] for k in SAME)
+        d_e2 = max(d_e2, abs(got["e2"] - alone["e2"]))
+    terms = sum(r[1]["n_terms"] for r in reqs)
+    span = max(done) - tickets[0][1]
+    # plain: FIFO single server over the same arrivals
+    free, plat, pdone = 0.0, [], []
+    for (_, _, sv), ta in zip(reqs, arrivals):
+        start = max(free, ta)
+        free = start + sv
+        plat.append(free - ta)
+    pspan = free - arrivals[0]
+    return {"workload": f"{n_req} requests, Poisson arrivals at {rate:.2f}/s "
+                        f"({load:.2f}x the plain path's capacity); 90% batched-workload instances, "
+                        "10% the one-large-solve workload",
+            "requests": n_req, "terms": terms,
+            "served_terms_per_s": terms / span, "plain_terms_per_s": terms / pspan,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "plain_p50_s": float(np.percentile(plat, 50)), "plain_p99_s": float(np.percentile(plat, 99)),
+            "max_abs_dE2_vs_alone": d_e2, "bit_identical_to_alone": bool(identical),
+            "plain": "first-come first-served pt2_run of the same arrivals, from measured pt2_run times"}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -129,7 +245,7 @@ def run_reference(args):
     from paper_1808_02049_gb300 import inputs  # noqa: F401
     import oracle
 
-    s, r = workload()
+    s, r = workload(args.n_det)
     oracle.build()
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     m = SAMPLE_DETS
@@ -146,7 +262,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD + f"; bounded sample: first {m} determinants per step",
+            "config": {"workload": workload_name(args.n_det) + f"; bounded sample: first {m} determinants per step",
                        "l2": "CPU run"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"full PT2 of the first {m} reference determinants per step"},
@@ -167,7 +283,7 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     build.build_library()
-    s, r = workload()
+    s, r = workload(args.n_det)
     ctx = pt2.Context(local)
     sid = ctx.load_system(s.h, s.eri)
     e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
@@ -236,6 +352,15 @@ def run_gpu(args):
         ctx.unload(sid2)
     e2e_s = time.perf_counter() - t0
 
+    extra = {}
+    if rank == 0 and not args.no_batch:
+        fleet = load_fleet(ctx)
+        extra["batched"] = bench_batched(ctx, fleet, reps=2)
+        if args.served_requests > 0:
+            big_res, big_s = timed_run(ctx, rid)
+            extra["served"] = bench_served(ctx, fleet, (rid, big_res, big_s), args.served_requests,
+                                           args.served_load)
+
     if rank == 0:
         value = terms / (total_ms * 1e-3)
         peaks = measured_peaks()
@@ -257,7 +382,7 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "terms_per_step": terms_step, "passes": n_pass,
+                "config": {"workload": workload_name(args.n_det), "terms_per_step": terms_step, "passes": n_pass,
                            "tiles": results[0]["n_tiles"], "oversize_tiles": results[0]["n_oversize"],
                            "e2": results[0]["e2"], "e2_bit_identical_across_steps": len(e2s) == 1,
                            "l2": "inputs larger than L2 (32 B x 1.3e10 terms stream through HBM per step) "
@@ -268,6 +393,7 @@ def run_gpu(args):
                 "e2e": {"value": e2e_terms / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches}
+        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(s, r, e0)
         print(json.dumps(line), flush=True)
@@ -286,6 +412,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--n-det", type=int, default=0,
+                    help="reference size of the one-large-solve workload (0: 100000); smaller values "
+                         "give the reduced cases used for profiling")
+    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-load", type=float, default=1.5,
+                    help="offered load of the served stream relative to the plain path's capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

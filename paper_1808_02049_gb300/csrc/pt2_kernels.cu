@@ -1643,17 +1643,23 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
         nx = tile_meta(p, blockIdx.x);
     }
     __syncthreads();
+    // current instance, the first tile past it and its E0, kept in registers
+    // (a CTA's tiles increase, so they only change at instance boundaries)
     int cur = tile_instance(p.tile_base, p.n_inst, blockIdx.x);
+    unsigned long long cur_end = p.tile_base[cur + 1];
+    double e0 = p.e0[cur];
     bool dirty = false;
     uint32_t phase = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G) {
-        const int inst = tile_instance(p.tile_base, p.n_inst, t);
-        if (inst != cur) {  // uniform across the CTA
+        if (t >= cur_end) {  // uniform across the CTA
             if (dirty) flush_stats(p, p.acc[cur], st, M.S.u.red);
             st.clear();
             dirty = false;
-            cur = inst;
+            cur = tile_instance(p.tile_base, p.n_inst, t);
+            cur_end = p.tile_base[cur + 1];
+            e0 = p.e0[cur];
         }
+        const int inst = cur;
         if (threadIdx.x == 0) {
             issue_tile(p, M, nx);
             M.meta[0] = nx.off;
@@ -1669,7 +1675,6 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams 
             if (threadIdx.x == 0) push_oversize(p, inst, t, cntl);
         } else if (cntl > 0) {
             const int cnt = (int)cntl;
-            const double e0 = p.e0[inst];
             const uint64_t *rk = M.rk;
             if (rcnt <= (unsigned long long)kRefSliceSmem) {
                 for (unsigned long long i = threadIdx.x; i < 2 * rcnt; i += blockDim.x)
