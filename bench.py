@@ -47,7 +47,7 @@ def dist_env():
 def workload(n_det=None):
     from paper_1808_02049_gb300 import inputs
 
-    return inputs.make_config(1, n_det=n_det)
+    return inputs.make_config(1, n_det=n_det or None)
 
 
 def workload_name(n_det):
@@ -224,7 +224,7 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
                         f"({load:.2f}x the plain path's capacity); 90% batched-workload instances, "
                         "10% the one-large-solve workload",
             "requests": n_req, "terms": terms,
-            "served_terms_per_s": terms / span, "plain_terms_per_s": terms / pspan,
+            "served_terms_per_s": terms / span, "plain_terms_per_s": float(terms / pspan),
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "plain_p50_s": float(np.percentile(plat, 50)), "plain_p99_s": float(np.percentile(plat, 99)),
             "max_abs_dE2_vs_alone": d_e2, "bit_identical_to_alone": bool(identical),
