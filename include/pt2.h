@@ -69,6 +69,10 @@ const char *pt2_last_error(const pt2_ctx *ctx);
 /* Load the integrals of one system (the Hamiltonian of Eq. 3).
  * h: n_orb*n_orb doubles, symmetric to 1e-12; eri: n_orb^4 doubles with
  * (pq|rs) = (qp|rs) = (pq|sr) = (rs|pq) to 1e-12.  All values finite.
+ * The library keeps one canonical element of each symmetry class (h_pq with
+ * p >= q; (pq|rs) with p >= q, r >= s and pq >= rs as pair indices), so
+ * inputs symmetric only to the tolerance give the same result whichever
+ * equivalent element a kernel reads.
  * Errors: PT2_ERR_UNSUPPORTED for n_orb > 64, PT2_ERR_INVALID otherwise. */
 int pt2_load_system(pt2_ctx *ctx, int n_orb, const double *h, const double *eri,
                     uint32_t *system_id);

@@ -265,6 +265,27 @@ int pt2_load_system(pt2_ctx *c, int n_orb, const double *h, const double *eri, u
                         std::fabs(v - E(r, s, p, q)) > tol)
                         return fail(c, PT2_ERR_INVALID, "eri lacks 8-fold symmetry at (%zu %zu|%zu %zu)", p, q, r, s);
                 }
+    // Canonical copies: every symmetry-equivalent element takes the value at one
+    // canonical index, so the kernels may read whichever permutation gives them
+    // contiguous addresses and still see bit-identical integrals.
+    std::vector<double> hc(n2), ec(n4);
+    for (size_t p = 0; p < n; ++p)
+        for (size_t q = 0; q < n; ++q) hc[p * n + q] = p >= q ? h[p * n + q] : h[q * n + p];
+    for (size_t p = 0; p < n; ++p)
+        for (size_t q = 0; q < n; ++q)
+            for (size_t r = 0; r < n; ++r)
+                for (size_t t = 0; t < n; ++t) {
+                    size_t a = p, b = q, x = r, y = t;
+                    if (a < b) std::swap(a, b);
+                    if (x < y) std::swap(x, y);
+                    if (a * n + b < x * n + y) {
+                        std::swap(a, x);
+                        std::swap(b, y);
+                    }
+                    ec[((p * n + q) * n + r) * n + t] = E(a, b, x, y);
+                }
+    h = hc.data();
+    eri = ec.data();
     cudaSetDevice(c->device);
     // Coulomb and same-spin pair energies, as doubles for the direct diagonal and
     // as exact 2^-48 Ha integers for the incremental diagonal of the generator
@@ -446,17 +467,18 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
     if ((rc = ensure(c, c->cursor, 8, "cursor"))) return rc;
     GenParams p = gen_params(c, s, r);
     p.n_tiles = 1;
-    p.cursor = (unsigned long long *)c->cursor.ptr;
+    p.cursor = (unsigned int *)c->cursor.ptr;
     p.recs = (Rec32 *)c->recs.ptr;
     p.rec_cap = T;
     p.det_begin = det_index;
     gen_layout(p, kModeDetTerms);
     CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, c->stream), "memset");
-    CK(cudaMemsetAsync(c->cursor.ptr, 0, 8, c->stream), "memset");
+    CK(cudaMemsetAsync(c->cursor.ptr, 0, 4, c->stream), "memset");
     CK(launch_gen_single(kModeDetTerms, p, nullptr, nullptr, c->stream), "generator");
-    unsigned long long n = 0;
-    CK(cudaMemcpyAsync(&n, c->cursor.ptr, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+    unsigned int n32 = 0;
+    CK(cudaMemcpyAsync(&n32, c->cursor.ptr, 4, cudaMemcpyDeviceToHost, c->stream), "copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
+    const unsigned long long n = n32;
     *n_out = n;
     if (n > cap) return fail(c, PT2_ERR_OOM, "determinant has %llu terms, above cap %llu", n, (unsigned long long)cap);
     std::vector<Rec32> h(n);

@@ -36,7 +36,10 @@ int size_class(uint64_t total)
     return std::max(0, std::min(7, k - 5));  // <1e6, 1e6, 1e7, ..., >=1e11
 }
 
-uint64_t records_budget(pt2_ctx *c)
+// Records one step may hold: what the HBM budget leaves, and at most
+// `passes` full-size passes (steps of batches and of the server hold two, so a
+// full pass of a large solve and passes of smaller ones run side by side).
+uint64_t records_budget(pt2_ctx *c, int passes = 1)
 {
     // the step workspace a previous run left allocated is reused, so it counts as available
     const DevBuf *ws[] = {&c->tile_counts, &c->tile_off, &c->cursor, &c->scan_tmp, &c->ref_count,
@@ -49,7 +52,7 @@ uint64_t records_budget(pt2_ctx *c)
     const uint64_t avail = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
     // per record: 32 bytes plus tile bookkeeping (about 60 bytes per tile of ~500 records)
     uint64_t rec = (uint64_t)((double)avail / (sizeof(Rec32) + 0.15));
-    return std::min<uint64_t>(rec, kMaxPassBytes / sizeof(Rec32));
+    return std::min<uint64_t>(rec, (uint64_t)passes * (kMaxPassBytes / sizeof(Rec32)));
 }
 
 int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)
@@ -147,6 +150,7 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
         uint64_t cap = j.o.pass_budget_bytes ? (uint64_t)((double)j.o.pass_budget_bytes / (sizeof(Rec32) + 60.0 / tt))
                                              : step_cap;
         if (!j.o.pass_budget_bytes) cap = std::min<uint64_t>(cap, kMaxTilesPerPass * tt);
+        cap = std::min<uint64_t>(cap, kMaxPassBytes / sizeof(Rec32));  // slots are 32-bit
         if (split_large && !j.o.pass_budget_bytes) cap = std::min<uint64_t>(cap, std::max<uint64_t>(step_cap / 2, 1024));
         if (cap < 1024) return fail(c, PT2_ERR_OOM, "pass budget is too small (%llu records)", (unsigned long long)cap);
         j.pass_cap = cap;
@@ -208,7 +212,7 @@ int ensure_step_workspace(pt2_ctx *c, const std::vector<StepPlan> &steps)
     int rc;
     if ((rc = ensure(c, c->tile_counts, tiles * 4, "tile counts"))) return rc;
     if ((rc = ensure(c, c->tile_off, (tiles + 1) * 8, "tile offsets"))) return rc;
-    if ((rc = ensure(c, c->cursor, tiles * 8, "tile cursors"))) return rc;
+    if ((rc = ensure(c, c->cursor, tiles * 4, "tile cursors"))) return rc;
     if ((rc = ensure(c, c->scan_tmp, scan_tmp_elems(tiles) * 8 * 2, "scan scratch"))) return rc;
     if ((rc = ensure(c, c->ref_count, tiles * 4, "reference counts"))) return rc;
     if ((rc = ensure(c, c->ref_off, (tiles + 1) * 8, "reference offsets"))) return rc;
@@ -247,7 +251,7 @@ GenParams step_item_params(pt2_ctx *c, const StepPlan &sp, size_t i, uint64_t ti
     g.det_begin = 0;
     g.class_counts = nullptr;
     g.tile_counts = reinterpret_cast<uint32_t *>(c->tile_counts.ptr);
-    g.cursor = reinterpret_cast<unsigned long long *>(c->cursor.ptr);
+    g.cursor = reinterpret_cast<unsigned int *>(c->cursor.ptr);
     g.recs = reinterpret_cast<Rec32 *>(c->recs.ptr);
     g.rec_cap = sp.records;
     gen_layout(g, kModeEmit);
@@ -298,9 +302,10 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     if (prof) CK(cudaEventRecord(E[1], st), "event");
     unsigned long long *tile_off = reinterpret_cast<unsigned long long *>(c->tile_off.ptr);
     unsigned long long *tmp = reinterpret_cast<unsigned long long *>(c->scan_tmp.ptr);
-    CK(launch_scan_u32_to_u64(reinterpret_cast<uint32_t *>(c->tile_counts.ptr), tile_off, sp.n_tiles, tmp, st),
+    // tile offsets, and the same offsets as the 32-bit slot cursors of the emission
+    CK(launch_scan_u32_to_u64(reinterpret_cast<uint32_t *>(c->tile_counts.ptr), tile_off,
+                              reinterpret_cast<uint32_t *>(c->cursor.ptr), sp.n_tiles, tmp, st),
        "scan");
-    CK(cudaMemcpyAsync(c->cursor.ptr, tile_off, sp.n_tiles * 8, cudaMemcpyDeviceToDevice, st), "copy");
     c->launches += 3;
     if (prof) CK(cudaEventRecord(E[2], st), "event");
     CK(gen_launch(c, kModeEmit, gb, sp.n_ctas, smem), "emit kernel");
@@ -317,7 +322,7 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     rp.ref_keys_out = reinterpret_cast<uint64_t *>(c->ref_keys.ptr);
     CK(cudaMemsetAsync(rp.ref_count, 0, sp.n_tiles * 4, st), "memset");
     CK(launch_ref_partition(rp, 0, st), "reference tiles");
-    CK(launch_scan_u32_to_u64(rp.ref_count, reinterpret_cast<unsigned long long *>(c->ref_off.ptr), sp.n_tiles,
+    CK(launch_scan_u32_to_u64(rp.ref_count, reinterpret_cast<unsigned long long *>(c->ref_off.ptr), nullptr, sp.n_tiles,
                               tmp + scan_tmp_elems(c->tile_counts.bytes / 4), st),
        "scan");
     CK(cudaMemcpyAsync(rp.ref_cursor, c->ref_off.ptr, sp.n_tiles * 8, cudaMemcpyDeviceToDevice, st), "copy");
@@ -580,7 +585,7 @@ void server_iteration(pt2_ctx *c)
     }
     std::lock_guard<std::recursive_mutex> lock(c->exec);
     cudaSetDevice(c->device);
-    const uint64_t cap = records_budget(c);
+    const uint64_t cap = records_budget(c, 2);
     if (!admit.empty()) {
         int rc = plan_jobs(c, admit, true, cap);
         for (Job *j : admit) j->t_admit = now_s();
@@ -750,7 +755,7 @@ int pt2_batch_create(pt2_ctx *c, uint32_t n, const uint32_t *ref_ids, const pt2_
         uint32_t best;
         // tune each size class on its largest instance, before planning the batch
         std::vector<Job *> probe = jobs;
-        if ((rc = plan_jobs(c, probe, true, records_budget(c)))) return rc;
+        if ((rc = plan_jobs(c, probe, true, records_budget(c, 2)))) return rc;
         std::map<int, Job *> largest;
         for (Job *j : jobs) {
             int k = size_class(j->total);
@@ -759,10 +764,10 @@ int pt2_batch_create(pt2_ctx *c, uint32_t n, const uint32_t *ref_ids, const pt2_
         for (auto &kv : largest)
             if ((rc = pt2_autotune(c, kv.second->ref_id, opts, &best))) return rc;
     }
-    if ((rc = plan_jobs(c, jobs, true, records_budget(c)))) return rc;
+    if ((rc = plan_jobs(c, jobs, true, records_budget(c, 2)))) return rc;
     if ((rc = dev_alloc(c, b->acc, n * sizeof(RunAcc), "batch accumulators"))) return rc;
     for (uint32_t i = 0; i < n; ++i) jobs[i]->acc = reinterpret_cast<RunAcc *>(b->acc.ptr) + i;
-    b->steps = pack_steps(jobs, records_budget(c));
+    b->steps = pack_steps(jobs, records_budget(c, 2));
     if ((rc = capture_batch(c, *b))) {
         dev_free(c, b->acc);
         dev_free(c, b->tables);

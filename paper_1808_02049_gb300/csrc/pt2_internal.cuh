@@ -17,8 +17,10 @@ constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per S
 constexpr int kTileCap = 768;                // records a tile CTA sorts in shared memory
 constexpr int kSortCap = 768;                // records one in-shared-memory sort handles
 constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
-constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (8 B each) resident in L2
+constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (4 B each) resident in L2
 constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
+// a step holds at most two full passes (batches, serving); its record slots are 32-bit
+static_assert(2 * (kMaxPassBytes / 32) < (1ull << 32), "record slots of a step must fit 32-bit tile cursors");
 constexpr int kBigThreads = 256;
 constexpr int kBigCap = 768;                 // Rec48 records sorted per chunk (oversize path)
 constexpr uint64_t kBigScratch = 16384;      // partial records per buffer of one oversize CTA
@@ -95,7 +97,7 @@ struct GenParams {
     // outputs
     unsigned long long *class_counts;  // kNumClasses (this instance's slice)
     uint32_t *tile_counts;             // n_tiles
-    unsigned long long *cursor;        // n_tiles
+    unsigned int *cursor;              // n_tiles: next free slot of each tile (a pass holds < 2^32 records)
     Rec32 *recs;
     unsigned long long rec_cap;        // records the launch may write (emit and det-terms modes)
     uint32_t *err;
@@ -179,7 +181,7 @@ cudaError_t launch_gen_single(GenMode mode, const GenParams &p, GenParams *d_par
                               cudaStream_t s);  // one determinant (parity aid); d_* are 1- and 2-entry scratch
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s);
 cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s);
-cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint64_t n,
+cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint32_t *out32, uint64_t n,
                                    unsigned long long *tmp, cudaStream_t s);
 size_t scan_tmp_elems(uint64_t n);
 cudaError_t launch_ref_partition(const RefPartParams &p, int phase, cudaStream_t s);

@@ -335,6 +335,14 @@ __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
     j1 = t - k * (k - 1) / 2;
 }
 
+// One 32-byte record written with a single 256-bit store (one L2 sector).
+__device__ __forceinline__ void store_rec32(Rec32 *dst, uint64_t a, uint64_t b, double num, int64_t den)
+{
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b),
+                 "l"((uint64_t)__double_as_longlong(num)), "l"((uint64_t)den)
+                 : "memory");
+}
+
 // One batch of up to kGenBatch terms of a lane, items i0, i0 + step, ...:
 // first every term's tile is hashed and its slot requested (the atomics of
 // the batch are then in flight together), then the values are computed and
@@ -344,7 +352,7 @@ __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
 template <int MODE, class KeyFn, class ValFn>
 __device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step, int n, KeyFn key, ValFn val)
 {
-    unsigned long long slot[kGenBatch];
+    uint32_t slot[kGenBatch];
     bool ok[kGenBatch];
 #pragma unroll
     for (int u = 0; u < kGenBatch; ++u) {
@@ -356,9 +364,9 @@ __device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step,
             if constexpr (MODE == kModeTileCount) {
                 atomicAdd(&p.tile_counts[p.tile_base + __umul64hi(zt, p.n_tiles)], 1u);
             } else if constexpr (MODE == kModeEmit) {
-                slot[u] = atomicAdd(&p.cursor[p.tile_base + __umul64hi(zt, p.n_tiles)], 1ull);
+                slot[u] = atomicAdd(&p.cursor[p.tile_base + __umul64hi(zt, p.n_tiles)], 1u);
             } else {
-                slot[u] = atomicAdd(&p.cursor[0], 1ull);
+                slot[u] = atomicAdd(&p.cursor[0], 1u);
             }
         }
     }
@@ -376,9 +384,7 @@ __device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step,
             val(i0 + u * step, a, b, num, den);
             if constexpr (MODE == kModeDetTerms)  // this mode reports H_aa itself (as double bits)
                 den = __double_as_longlong(p.e0 - den_to_double(den));
-            double2 *dst = reinterpret_cast<double2 *>(p.recs + slot[u]);
-            dst[0] = make_double2(__longlong_as_double((long long)a), __longlong_as_double((long long)b));
-            dst[1] = make_double2(num, __longlong_as_double((long long)den));
+            store_rec32(p.recs + slot[u], a, b, num, den);
         }
     }
 }
@@ -626,7 +632,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 __syncwarp();
                 baseD = d0 - sa_delta[s];
                 cA = flip_sign(c, info >> 16);
-                slice = eri + ((size_t)aA * N + rA) * N * N;
+                // (aA rA|aB rB) = (rA aA|rB aB): lanes take consecutive beta
+                // singles (same rB, ascending aB), so this layout is contiguous
+                slice = eri + ((size_t)rA * N + aA) * N * N;
             }
             for (int sb0 = lane; sb0 < p.n_sb; sb0 += 32 * kGenBatch)
                 emit_batch<MODE>(
@@ -640,7 +648,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                         const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
                         ka = a2;
                         kb = B ^ (1ull << rB) ^ (1ull << aB);
-                        num = flip_sign(cA * slice[aB * N + rB], bi >> 16);
+                        num = flip_sign(cA * slice[rB * N + aB], bi >> 16);
                         den = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
                     });
             __syncwarp();
@@ -699,8 +707,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                             const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
                             const uint32_t par =
                                 __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                            const double e = eri[(((size_t)a1 * N + r1) * N + a2) * N + r2] -
-                                             eri[(((size_t)a1 * N + r2) * N + a2) * N + r1];
+                            // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
+                            // a1 is the fastest-varying index across lanes
+                            const double e = eri[(((size_t)r2 * N + a2) * N + r1) * N + a1] -
+                                             eri[(((size_t)r1 * N + a2) * N + r2) * N + a1];
                             num = flip_sign(c * e, par);
                             den = base - vec[j1] - vec[j2] - WSx[a1 * N + a2];
                         });
@@ -849,7 +859,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_parts_kernel(unsigned long 
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t *__restrict__ in, uint64_t n,
                                                                   const unsigned long long *__restrict__ part,
                                                                   uint64_t nparts,
-                                                                  unsigned long long *__restrict__ out)
+                                                                  unsigned long long *__restrict__ out,
+                                                                  uint32_t *__restrict__ out32)
 {
     __shared__ unsigned long long wt[33];
     uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
@@ -865,20 +876,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
     unsigned long long run = part[blockIdx.x] + pre;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = run;
+        if (base + k < n) {
+            out[base + k] = run;
+            if (out32) out32[base + k] = (uint32_t)run;
+        }
         run += v[k];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = part[nparts];
 }
 
-cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint64_t n,
+cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint32_t *out32, uint64_t n,
                                    unsigned long long *tmp, cudaStream_t s)
 {
     uint64_t nparts = (n + kScanTile - 1) / kScanTile;
     if (nparts == 0) return cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
     scan_sums_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, tmp);
     scan_parts_kernel<<<1, kScanThreads, 0, s>>>(tmp, nparts);
-    scan_apply_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, tmp, nparts, out);
+    scan_apply_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, tmp, nparts, out, out32);
     return cudaGetLastError();
 }
 
@@ -2010,11 +2024,11 @@ static cudaError_t noalloc_scratch(int device, void **out)
 
 // Split staged records into the caller's key / numerator / diagonal arrays
 // (at most cap of them).
-__global__ void split_terms_kernel(const Rec32 *__restrict__ recs, const unsigned long long *__restrict__ count,
+__global__ void split_terms_kernel(const Rec32 *__restrict__ recs, const unsigned int *__restrict__ count,
                                    uint64_t cap, uint64_t *__restrict__ keys, double *__restrict__ val,
                                    double *__restrict__ haa)
 {
-    const uint64_t n = *count < cap ? *count : cap;
+    const uint64_t n = (uint64_t)*count < cap ? (uint64_t)*count : cap;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const Rec32 r = recs[i];
         keys[2 * i] = r.a;
@@ -2030,20 +2044,22 @@ cudaError_t launch_det_terms_noalloc(int device, GenParams p, uint64_t cap, uint
     void *base = nullptr;
     cudaError_t e = noalloc_scratch(device, &base);
     if (e != cudaSuccess) return e;
-    unsigned long long *count = reinterpret_cast<unsigned long long *>(base);
+    unsigned int *count = reinterpret_cast<unsigned int *>(base);
     Rec32 *recs = reinterpret_cast<Rec32 *>(static_cast<unsigned char *>(base) + 256);
     p.cursor = count;
     p.recs = recs;
     p.rec_cap = kNoAllocMaxTerms;
     p.n_tiles = 1;
     gen_layout(p, kModeDetTerms);
-    if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
     if ((e = launch_gen_single(kModeDetTerms, p, nullptr, nullptr, s)) != cudaSuccess) return e;
     split_terms_kernel<<<64, 256, 0, s>>>(recs, count, cap, keys, val, haa);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(n_host, count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return e;
-    return cudaStreamSynchronize(s);
+    unsigned int n32 = 0;
+    if ((e = cudaMemcpyAsync(&n32, count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    *n_host = n32;
+    return e;
 }
 
 }  // namespace pt2
