@@ -338,9 +338,9 @@ __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
 // One 32-byte record written with a single 256-bit store (one L2 sector).
 __device__ __forceinline__ void store_rec32(Rec32 *dst, uint64_t a, uint64_t b, double num, int64_t den)
 {
+    // no memory clobber: nothing in the generator reads records back
     asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(dst), "l"(a), "l"(b),
-                 "l"((uint64_t)__double_as_longlong(num)), "l"((uint64_t)den)
-                 : "memory");
+                 "l"((uint64_t)__double_as_longlong(num)), "l"((uint64_t)den));
 }
 
 // One batch of up to kGenBatch terms of a lane, items i0, i0 + step, ...:
@@ -728,7 +728,9 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenBatch b)
         gen_body<MODE>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
         return;
     }
-    __shared__ GenParams sp;
+    // instance of this CTA (thread 0 searches, the others read the result);
+    // its parameters are read in place through the read-only data path
+    __shared__ int sinst;
     __shared__ unsigned long long sdet;
     if (threadIdx.x == 0) {
         const unsigned long long g = b.cta_offset + blockIdx.x;
@@ -738,11 +740,12 @@ __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel(const GenBatch b)
             if (b.det_base[mid] <= g) lo = mid;
             else hi = mid;
         }
-        sp = b.params[lo];
-        sdet = sp.det_begin + (g - b.det_base[lo]);
+        sinst = lo;
+        sdet = b.params[lo].det_begin + (g - b.det_base[lo]);
     }
     __syncthreads();
-    gen_body<MODE>(sp, sdet);
+    const GenParams *__restrict__ gp = b.params + sinst;
+    gen_body<MODE>(*gp, sdet);
 }
 
 // Generator for one determinant with its parameters passed by value.
