@@ -111,7 +111,8 @@ typedef struct {
     uint32_t flags;             /* PT2_FLAG_* below */
 } pt2_opts;
 
-#define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times) */
+#define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times); a batch created
+                                 with it runs its steps one by one instead of replaying its graph */
 #define PT2_FLAG_AUTOTUNE 2u  /* pt2_batch_create: tune the tile target per size class first */
 
 typedef struct {

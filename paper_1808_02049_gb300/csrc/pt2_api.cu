@@ -184,11 +184,14 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
     if (prop.major < 10)
         return fail(nullptr, PT2_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a", device,
                     prop.major, prop.minor);
-    e = init_kernel_attributes();
+    int tile_per_sm = 0, big_per_sm = 0;
+    e = init_kernel_attributes(&tile_per_sm, &big_per_sm);
     if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
     auto c = std::make_unique<pt2_ctx>();
     c->device = device;
     c->sm_count = prop.multiProcessorCount;
+    c->tile_per_sm = tile_per_sm;
+    c->big_per_sm = big_per_sm;
     size_t fr = 0, tot = 0;
     e = cudaMemGetInfo(&fr, &tot);
     if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "cudaMemGetInfo: %s", cudaGetErrorString(e));

@@ -47,7 +47,7 @@ uint64_t records_budget(pt2_ctx *c, int passes = 1)
     uint64_t held = 0;
     for (const DevBuf *b : ws) held += b->bytes;
     const uint64_t fixed = c->used - held;
-    const uint64_t scratch = (uint64_t)4 * c->sm_count * 2 * kBigScratch * sizeof(Rec48);
+    const uint64_t scratch = (uint64_t)c->big_per_sm * c->sm_count * 2 * kBigScratch * sizeof(Rec48);
     const uint64_t reserve = scratch + (256ull << 20);
     const uint64_t avail = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
     // per record: 32 bytes plus tile bookkeeping (about 60 bytes per tile of ~500 records)
@@ -221,7 +221,7 @@ int ensure_step_workspace(pt2_ctx *c, const std::vector<StepPlan> &steps)
     if ((rc = ensure(c, c->ref_tile, refs * 4, "reference tiles"))) return rc;
     if ((rc = ensure(c, c->ref_keys, refs * 16, "reference slices"))) return rc;
     if ((rc = ensure(c, c->big_max, 16, "oversize maximum"))) return rc;
-    const uint64_t scratch = (uint64_t)4 * c->sm_count * 2 * kBigScratch * sizeof(Rec48);
+    const uint64_t scratch = (uint64_t)c->big_per_sm * c->sm_count * 2 * kBigScratch * sizeof(Rec48);
     if ((rc = ensure(c, c->scratch, scratch, "oversize scratch"))) return rc;
     if ((rc = ensure(c, c->recs, recs * sizeof(Rec32), "term records"))) return rc;
     return PT2_OK;
@@ -356,9 +356,9 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
         tp.dump_count = reinterpret_cast<unsigned long long *>(c->dump_count.ptr);
         tp.dump_cap = dump->cap;
     }
-    CK(launch_tiles(tp, 4 * c->sm_count, st), "tile kernel");
+    CK(launch_tiles(tp, c->tile_per_sm * c->sm_count, st), "tile kernel");
     if (prof) CK(cudaEventRecord(E[5], st), "event");
-    CK(launch_big_tiles(tp, 4 * c->sm_count, st), "oversize tile kernel");
+    CK(launch_big_tiles(tp, c->big_per_sm * c->sm_count, st), "oversize tile kernel");
     if (prof) CK(cudaEventRecord(E[6], st), "event");
     CK(launch_pass_finish(tile_off, d->tile_base, n, d->expected, d->acc, d->n_big, tp.err, st), "pass finish");
     c->launches += 3;
@@ -487,6 +487,7 @@ struct Batch {
     cudaGraphExec_t exec = nullptr;
     uint64_t ws_gen = 0;  // workspace generation the graph was captured with
     double capture_s = 0;
+    bool profile = false;  // run the steps one by one with per-phase events instead of the graph
 };
 
 namespace {
@@ -768,6 +769,7 @@ int pt2_batch_create(pt2_ctx *c, uint32_t n, const uint32_t *ref_ids, const pt2_
     if ((rc = dev_alloc(c, b->acc, n * sizeof(RunAcc), "batch accumulators"))) return rc;
     for (uint32_t i = 0; i < n; ++i) jobs[i]->acc = reinterpret_cast<RunAcc *>(b->acc.ptr) + i;
     b->steps = pack_steps(jobs, records_budget(c, 2));
+    b->profile = opts && (opts->flags & PT2_FLAG_PROFILE);
     if ((rc = capture_batch(c, *b))) {
         dev_free(c, b->acc);
         dev_free(c, b->tables);
@@ -797,7 +799,18 @@ int pt2_batch_run(pt2_ctx *c, uint32_t batch_id, pt2_result *results)
     std::vector<RunAcc> h(n);
     uint32_t err = 0;
     CK(cudaEventRecord(c->ev[0], st), "event");
-    CK(cudaGraphLaunch(b.exec, st), "graph launch");
+    if (b.profile) {  // the captured work, launched step by step with per-phase events
+        for (double &x : c->phase_ms) x = 0.0;
+        c->launches = 0;
+        CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, st), "memset");
+        CK(launch_acc_init(reinterpret_cast<RunAcc *>(b.acc.ptr), (int)n, st), "acc init");
+        StepDev *d = reinterpret_cast<StepDev *>(b.tables.ptr);
+        for (size_t k = 0; k < b.steps.size(); ++k)
+            if ((rc = enqueue_step(c, b.steps[k], d + k, nullptr, true))) return rc;
+        CK(launch_acc_finalize(reinterpret_cast<RunAcc *>(b.acc.ptr), (int)n, st), "acc finalize");
+    } else {
+        CK(cudaGraphLaunch(b.exec, st), "graph launch");
+    }
     CK(cudaEventRecord(c->ev[1], st), "event");
     CK(cudaMemcpyAsync(h.data(), b.acc.ptr, n * sizeof(RunAcc), cudaMemcpyDeviceToHost, st), "copy");
     CK(cudaMemcpyAsync(&err, c->err_word.ptr, 4, cudaMemcpyDeviceToHost, st), "copy");

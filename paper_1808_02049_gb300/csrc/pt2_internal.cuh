@@ -24,6 +24,8 @@ static_assert(2 * (kMaxPassBytes / 32) < (1ull << 32), "record slots of a step m
 constexpr int kBigThreads = 256;
 constexpr int kBigCap = 768;                 // Rec48 records sorted per chunk (oversize path)
 constexpr uint64_t kBigScratch = 16384;      // partial records per buffer of one oversize CTA
+constexpr int kBigBuckets = 256;             // most hash buckets the partials of one oversize tile split into
+static_assert(kBigBuckets * kBigCap >= 2 * kBigScratch, "the hash split can always make buckets fit a chunk");
 constexpr int kMaxBatch = 256;               // instances in one step
 
 // Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is
@@ -39,7 +41,7 @@ constexpr int kFxShift = 90;
 constexpr uint32_t kErrFixedRange = 1u;      // |numerator| or |term| beyond the fixed-point range
 constexpr uint32_t kErrWaitTimeout = 2u;     // a bounded mbarrier wait ran out
 constexpr uint32_t kErrScratch = 4u;         // oversize tile larger than its scratch
-constexpr uint32_t kErrNoProgress = 8u;      // chunked grouping could not shrink a tile
+constexpr uint32_t kErrNoProgress = 8u;      // the partials of an oversize tile could not be split to fit a chunk
 constexpr uint32_t kErrCount = 16u;          // emitted terms differ from the plan
 
 // One generated term: the excited determinant, its numerator H_ai c_i and
@@ -194,7 +196,7 @@ cudaError_t launch_pass_finish(const unsigned long long *tile_off, const unsigne
                                uint32_t *err, cudaStream_t s);
 cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s);
 cudaError_t launch_acc_finalize(RunAcc *acc, int n, cudaStream_t s);
-cudaError_t init_kernel_attributes();  // once per process and device, before any capture
+cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm);  // once per process and device, before any capture
 size_t tile_smem_bytes();
 size_t big_smem_bytes();
 

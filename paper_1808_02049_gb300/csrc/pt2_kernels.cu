@@ -1738,6 +1738,8 @@ struct BigSmem {
     uint64_t rk[2 * kRefSliceSmem];
     uint64_t bar;
     unsigned int out_count;
+    unsigned int big_pre[kMaxBatch + 1];  // oversize tiles before instance i
+    unsigned int bk_cnt[kBigBuckets], bk_off[kBigBuckets], bk_cur[kBigBuckets];  // hash split of partials
 };
 
 size_t big_smem_bytes() { return sizeof(BigSmem); }
@@ -1766,10 +1768,13 @@ __device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst
     if (!sort_reduce_chunk(recs, m, M.S, err, put)) exact_reduce_chunk(recs, m, M.S, err, put);
 }
 
-// Persistent over the oversize tiles of every instance, instance by
-// instance, so each CTA flushes its statistics once per instance.  The
-// partial lists live in a fixed per-CTA scratch of two buffers of
-// scratch_cap records; a tile whose partials outgrow it sets kErrScratch.
+// Persistent over the oversize tiles of all instances, numbered in one index
+// space (instance i owns [big_pre[i], big_pre[i+1])) and dealt round-robin to
+// the CTAs, so a step's oversize work spreads over the whole grid whatever
+// its instance mix; a CTA flushes its statistics when its tiles move on to
+// the next instance.  The partial lists live in a fixed per-CTA scratch of
+// two buffers of scratch_cap records; a tile whose partials outgrow it sets
+// kErrScratch.
 __global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1780,14 +1785,38 @@ __global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TilePara
     if (threadIdx.x == 0) mbar_init(&M.bar, 1);
     __syncthreads();
     const int nt = blockDim.x;
-    for (int inst = 0; inst < p.n_inst; ++inst) {
-        const unsigned int nbig = p.n_big[inst];
-        if ((unsigned)blockIdx.x >= nbig) continue;  // uniform: nothing of this instance for this CTA
-        const double e0 = p.e0[inst];
-        KeyStats st;
-        st.clear();
-        for (unsigned int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
-            const uint64_t t = p.big_list[p.tile_base[inst] + idx];
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int i = 0; i < p.n_inst; ++i) {
+            M.big_pre[i] = run;
+            run += p.n_big[i];
+        }
+        M.big_pre[p.n_inst] = run;
+    }
+    __syncthreads();
+    const unsigned int total = M.big_pre[p.n_inst];
+    int inst = -1;
+    double e0 = 0.0;
+    KeyStats st;
+    st.clear();
+    {
+        for (unsigned int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+            if (inst < 0 || idx >= M.big_pre[inst + 1]) {  // uniform across the CTA
+                if (inst >= 0) {
+                    flush_stats(p, p.acc[inst], st, M.S.u.red);
+                    __syncthreads();
+                }
+                st.clear();
+                int lo = 0, hi = p.n_inst;  // last instance whose range starts at or before idx
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (M.big_pre[mid] <= idx) lo = mid;
+                    else hi = mid;
+                }
+                inst = lo;
+                e0 = p.e0[inst];
+            }
+            const uint64_t t = p.big_list[p.tile_base[inst] + (idx - M.big_pre[inst])];
             const unsigned long long off = p.tile_off[t];
             const unsigned long long cnt = p.tile_off[t + 1] - off;
             bool bad = false;
@@ -1812,43 +1841,65 @@ __global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TilePara
                 u += M.out_count;
                 __syncthreads();
             }
-            // further rounds until the reduced list fits one chunk
-            Rec48 *src = bufA, *dst = bufB;
-            while (!bad && u > (unsigned long long)kBigCap) {
-                unsigned long long u2 = 0;
-                for (unsigned long long cs = 0; cs < u; cs += kBigCap) {
-                    const int m = (int)min((unsigned long long)kBigCap, u - cs);
-                    if (threadIdx.x == 0) M.out_count = 0;
-                    for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[cs + i];
-                    __syncthreads();
-                    chunk_to_partials(M.u.r48, m, M, dst + u2, st.err);
-                    u2 += M.out_count;
-                    __syncthreads();
-                }
-                if (u2 >= u) {
-                    if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
-                    bad = true;
-                    break;
-                }
-                Rec48 *tmp = src;
-                src = dst;
-                dst = tmp;
-                u = u2;
-            }
-            // final sort-reduce and the energy
+            // Partials of different chunks may share a key.  If they fit one
+            // chunk they are sorted and reduced together; otherwise they are
+            // first split by a hash of the key into buckets that each fit a
+            // chunk (equal keys share a bucket) and every bucket is finished
+            // on its own.  Exact sums make the result independent of the split.
             unsigned long long nrk;
             const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
-            if (!bad) {
-                const int m = (int)u;
+            auto fin = [&](const KeyVal &v) { finish_keyval(p, e0, rk, nrk, v, st); };
+            auto finish_list = [&](const Rec48 *src, int m) {
                 for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
                 __syncthreads();
-                auto fin = [&](const KeyVal &v) { finish_keyval(p, e0, rk, nrk, v, st); };
-                if (!sort_reduce_chunk(M.u.r48, m, M.S, st.err, fin))
-                    exact_reduce_chunk(M.u.r48, m, M.S, st.err, fin);
+                if (!sort_reduce_chunk(M.u.r48, m, M.S, st.err, fin)) exact_reduce_chunk(M.u.r48, m, M.S, st.err, fin);
+                __syncthreads();
+            };
+            if (!bad && u <= (unsigned long long)kBigCap) {
+                finish_list(bufA, (int)u);
+            } else if (!bad) {
+                int nbk = 2;
+                while ((unsigned long long)nbk * (kBigCap / 2) < u && nbk < kBigBuckets) nbk *= 2;
+                for (;;) {  // uniform: every thread sees the same counts
+                    for (int i = threadIdx.x; i < nbk; i += nt) M.bk_cnt[i] = 0;
+                    __syncthreads();
+                    for (unsigned long long i = threadIdx.x; i < u; i += nt)
+                        atomicAdd(&M.bk_cnt[bucket_hash(bufA[i].a, bufA[i].b) & (nbk - 1)], 1u);
+                    __syncthreads();
+                    unsigned int mx = 0;
+                    for (int i = 0; i < nbk; ++i) mx = max(mx, M.bk_cnt[i]);
+                    if (mx <= (unsigned)kBigCap || nbk >= kBigBuckets) {
+                        if (mx > (unsigned)kBigCap) {
+                            if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
+                            bad = true;
+                        }
+                        break;
+                    }
+                    nbk *= 2;
+                    __syncthreads();
+                }
+                if (!bad) {
+                    if (threadIdx.x == 0) {
+                        unsigned int run = 0;
+                        for (int i = 0; i < nbk; ++i) {
+                            M.bk_off[i] = run;
+                            M.bk_cur[i] = run;
+                            run += M.bk_cnt[i];
+                        }
+                    }
+                    __syncthreads();
+                    for (unsigned long long i = threadIdx.x; i < u; i += nt) {
+                        const Rec48 r = bufA[i];
+                        bufB[atomicAdd(&M.bk_cur[bucket_hash(r.a, r.b) & (nbk - 1)], 1u)] = r;
+                    }
+                    __syncthreads();
+                    for (int k = 0; k < nbk; ++k)
+                        if (M.bk_cnt[k]) finish_list(bufB + M.bk_off[k], (int)M.bk_cnt[k]);
+                }
             }
             __syncthreads();
         }
-        flush_stats(p, p.acc[inst], st, M.S.u.red);
+        if (inst >= 0) flush_stats(p, p.acc[inst], st, M.S.u.red);
         __syncthreads();
     }
     if (threadIdx.x == 0) mbar_inval(&M.bar);
@@ -1973,7 +2024,7 @@ static int gen_smem_max()
     return p.smem_bytes;
 }
 
-cudaError_t init_kernel_attributes()
+cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm)
 {
     const int g = gen_smem_max();
     cudaError_t e;
@@ -1986,7 +2037,15 @@ cudaError_t init_kernel_attributes()
         return e;
     if ((e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes())))
         return e;
-    return cudaFuncSetAttribute(big_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem_bytes());
+    if ((e = cudaFuncSetAttribute(big_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem_bytes())))
+        return e;
+    // the persistent kernels launch exactly the CTAs that fit at once
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(tile_per_sm, tile_kernel, kTileThreads, tile_smem_bytes())))
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(big_per_sm, big_tile_kernel, kBigThreads, big_smem_bytes())))
+        return e;
+    if (*tile_per_sm < 1 || *big_per_sm < 1) return cudaErrorInvalidConfiguration;
+    return cudaSuccess;
 }
 
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s)

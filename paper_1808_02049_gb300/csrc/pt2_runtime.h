@@ -96,6 +96,7 @@ struct Server;
 struct pt2_ctx {
     int device = 0;
     int sm_count = 0;
+    int tile_per_sm = 4, big_per_sm = 3;  // resident CTAs of the persistent kernels
     cudaStream_t stream = nullptr;
     uint64_t budget = 0, used = 0;
     std::string err;

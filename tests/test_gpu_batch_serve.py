@@ -63,6 +63,20 @@ def test_batch_matches_single_runs_and_oracle(fleet):
         assert abs(x["alone"]["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
 
 
+def test_profiled_batch_matches_graph_replay(fleet):
+    c, refs = fleet
+    ids = [x["rid"] for x in refs]
+    bid = c.batch_create(ids, profile=True)  # steps launched one by one, with phase events
+    try:
+        res = c.batch_run(bid, len(ids))
+        ph, launches = c.phase_times()
+    finally:
+        c.batch_destroy(bid)
+    for x, got in zip(refs, res):
+        assert same(got, x["alone"])
+    assert ph["emit"] > 0 and ph["tile_sort_reduce"] > 0 and launches > 0
+
+
 def test_batch_with_small_step_budget_and_autotune(fleet):
     c, refs = fleet
     ids = [x["rid"] for x in refs]

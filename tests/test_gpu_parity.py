@@ -112,6 +112,27 @@ def test_tile_sizes_and_oversize_path(ctx, cfg0, tile_target):
         assert got["n_oversize"] > 0  # tiles above shared-memory capacity took the chunked path
 
 
+def test_oversize_tiles_with_mostly_distinct_keys(ctx):
+    # Three determinants of the large system: almost every one of the ~3.9e5
+    # terms is a distinct key, so at the largest tile target about half of the
+    # tiles exceed shared memory with more distinct keys than one chunk holds;
+    # their partials are split by hash before the final reduction.
+    s, r = inputs.make_config(1, n_det=3)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    sid = ctx.load_system(s.h, s.eri)
+    rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    try:
+        ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
+        assert ref["n_unique"] > 0.95 * ref["n_terms"]
+        got = ctx.run(rid, tile_target=768)
+        assert got["n_oversize"] > 0.2 * got["n_tiles"]
+        assert_same_result(got, ref)
+        assert ctx.run(rid)["e2"] == got["e2"]
+    finally:
+        ctx.unload(rid)
+        ctx.unload(sid)
+
+
 def test_e2_is_bit_identical_for_any_tiling_and_pass_plan(ctx, cfg0):
     # numerators and the energy are summed exactly in fixed point, so the
     # result cannot depend on how terms are split into passes and tiles
