@@ -180,12 +180,10 @@ __device__ __forceinline__ double fx_to_double(uint64_t lo, int64_t hi)
     return u128_to_double(ulo, uhi, kFxShift, neg);
 }
 
-__device__ __forceinline__ double den_to_double(int64_t d)
-{
-    bool neg = d < 0;
-    uint64_t m = neg ? (uint64_t)(-d) : (uint64_t)d;
-    return u128_to_double(m, 0, kDenShift, neg);
-}
+// E0 - H_aa as a double: the int64 is rounded to nearest (ties to even) by the
+// conversion instruction and the power-of-two scale is exact.
+__device__ __forceinline__ double den_to_double(int64_t d) { return __ll2double_rn((long long)d) * 0x1p-48; }
+static_assert(kDenShift == 48, "den_to_double scales by 2^-48");
 
 // Reciprocal of d: a single-precision hardware estimate refined by one
 // Newton-Raphson step, x1 = x0 (2 - d x0) (relative error about 2^-46).
@@ -349,8 +347,22 @@ __device__ __forceinline__ void store_rec32(Rec32 *dst, uint64_t a, uint64_t b, 
 // stored, so the arithmetic overlaps the atomic round trips.
 //   key(i, zt) -> false if item i is outside the pass, else sets the tile hash
 //   val(i, a, b, num, den) -> the record of item i
+// Where one determinant's terms go, copied out of the instance parameters once
+// (the counters and cursors already offset to the instance's first tile), so
+// the hot loops hold them in registers whether the parameters live in the
+// constant bank or in global memory.
+struct EmitOut {
+    uint32_t *counts;      // TileCount: terms per tile
+    unsigned int *cursor;  // Emit / DetTerms: next slot per tile
+    Rec32 *recs;
+    uint64_t n_tiles;
+    unsigned long long rec_cap;
+    uint32_t *err;
+    double e0;
+};
+
 template <int MODE, class KeyFn, class ValFn>
-__device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step, int n, KeyFn key, ValFn val)
+__device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, int n, KeyFn key, ValFn val)
 {
     uint32_t slot[kGenBatch];
     bool ok[kGenBatch];
@@ -362,9 +374,9 @@ __device__ __forceinline__ void emit_batch(const GenParams &p, int i0, int step,
         slot[u] = 0;
         if (ok[u]) {
             if constexpr (MODE == kModeTileCount) {
-                atomicAdd(&p.tile_counts[p.tile_base + __umul64hi(zt, p.n_tiles)], 1u);
+                atomicAdd(&p.counts[__umul64hi(zt, p.n_tiles)], 1u);
             } else if constexpr (MODE == kModeEmit) {
-                slot[u] = atomicAdd(&p.cursor[p.tile_base + __umul64hi(zt, p.n_tiles)], 1u);
+                slot[u] = atomicAdd(&p.cursor[__umul64hi(zt, p.n_tiles)], 1u);
             } else {
                 slot[u] = atomicAdd(&p.cursor[0], 1u);
             }
@@ -562,11 +574,22 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         return;
     } else {
         const uint64_t ZtaA = F.ZtaA, ZtbB = F.ZtbB;
+        EmitOut out;
+        out.counts = MODE == kModeTileCount ? p.tile_counts + p.tile_base : nullptr;
+        out.cursor = MODE == kModeEmit ? p.cursor + p.tile_base : p.cursor;
+        out.recs = p.recs;
+        out.n_tiles = p.n_tiles;
+        out.rec_cap = p.rec_cap;
+        out.err = p.err;
+        out.e0 = p.e0;
+        const uint32_t class_lo = p.class_lo, class_hi = p.class_hi;
+        const uint64_t cons_mod = p.cons_mod, cons_rem = p.cons_rem;
+        const int n_sb = p.n_sb;
 
         // ---- alpha singles (few per determinant: O(n) element each)
         for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch)
             emit_batch<MODE>(
-                p, k0, kGenThreads, n_sa_pass,
+                out, k0, kGenThreads, n_sa_pass,
                 [&](int k, uint64_t &zt) {
                     zt = sa_zt[sa_pass[k]] ^ ZtbB;
                     return true;
@@ -591,9 +614,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 });
         // ---- beta singles
         if (a_in)
-            for (int s0 = tid; s0 < p.n_sb; s0 += kGenThreads * kGenBatch)
+            for (int s0 = tid; s0 < n_sb; s0 += kGenThreads * kGenBatch)
                 emit_batch<MODE>(
-                    p, s0, kGenThreads, p.n_sb,
+                    out, s0, kGenThreads, n_sb,
                     [&](int s, uint64_t &zt) {
                         zt = ZtaA ^ sb_zt[s];
                         return true;
@@ -636,9 +659,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 // singles (same rB, ascending aB), so this layout is contiguous
                 slice = eri + ((size_t)rA * N + aA) * N * N;
             }
-            for (int sb0 = lane; sb0 < p.n_sb; sb0 += 32 * kGenBatch)
+            for (int sb0 = lane; sb0 < n_sb; sb0 += 32 * kGenBatch)
                 emit_batch<MODE>(
-                    p, sb0, 32, p.n_sb,
+                    out, sb0, 32, n_sb,
                     [&](int sb, uint64_t &zt) {
                         zt = ztA ^ sb_zt[sb];
                         return true;
@@ -683,14 +706,14 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 }
                 for (int t0 = lane; t0 < npv; t0 += 32 * kGenBatch)
                     emit_batch<MODE>(
-                        p, t0, 32, npv,
+                        out, t0, 32, npv,
                         [&](int t, uint64_t &zt) {
                             const int pv = pairs[t];
                             const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
                             if (spin == 0) {
                                 uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
-                                if (cl < p.class_lo || cl >= p.class_hi) return false;
-                                if (!cons_ok(p.cons_mod, p.cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
+                                if (cl < class_lo || cl >= class_hi) return false;
+                                if (!cons_ok(cons_mod, cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
                                 zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
                             } else {
                                 zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
@@ -1223,14 +1246,16 @@ __device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint6
 // ------------------------------------------- in-tile LSD radix sort + reduce
 //
 // A tile (or a chunk of an oversize tile) of at most kSortCap records sits in
-// shared memory.  Its keys are compressed to 32-bit hashes (the paper's
-// generalised compression with hash functions) and sorted with a stable LSD
-// radix sort, four 8-bit digit passes staged through shared memory: each warp
-// ranks its items with eight ballots per digit, a block-wide scan turns the
-// per-warp digit counts into offsets, and items scatter to their rank.  Equal
-// keys then form contiguous runs; every run is verified against the full
-// 128-bit key (a hash collision makes the chunk fall back to an exact path)
-// and reduced by key.
+// shared memory.  Each key is compressed to a 32-bit hash (the paper's
+// compression of keys by hash functions) carried in a 64-bit word with the
+// record's index, and the words are sorted with a stable LSD radix sort staged
+// through shared memory: three 8-bit digit passes over the low 24 hash bits
+// (a fourth over the top 8 bits only when two different keys share those 24),
+// each ranking items within a warp with __match_any_sync, scanning the
+// per-(digit, warp, item) counts into offsets and scattering.  Equal keys then
+// form contiguous runs; every run is verified against the full 128-bit key (a
+// remaining hash collision sends the chunk to an exact path) and reduced by
+// key.
 
 constexpr int kSortThreads = kTileThreads;
 constexpr int kSortItems = kSortCap / kSortThreads;   // items per thread, striped
