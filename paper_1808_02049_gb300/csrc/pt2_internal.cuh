@@ -16,7 +16,7 @@ constexpr int kGenBatch = 8;                 // terms whose slots a lane request
 constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per SM)
 constexpr int kTileCap = 768;                // records a tile CTA sorts in shared memory
 constexpr int kSortCap = 768;                // records one in-shared-memory sort handles
-constexpr int kRefSliceSmem = 64;            // reference keys per tile kept in shared memory
+constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)
 constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (4 B each) resident in L2
 constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
 // a step holds at most two full passes (batches, serving); its record slots are 32-bit
@@ -26,6 +26,7 @@ constexpr int kBigCap = 768;                 // Rec48 records sorted per chunk (
 constexpr uint64_t kBigScratch = 16384;      // partial records per buffer of one oversize CTA
 constexpr int kBigBuckets = 256;             // most hash buckets the partials of one oversize tile split into
 static_assert(kBigBuckets * kBigCap >= 2 * kBigScratch, "the hash split can always make buckets fit a chunk");
+static_assert(kBigScratch <= 65535, "bucket starts of the hash split are 16-bit");
 constexpr int kMaxBatch = 256;               // instances in one step
 
 // Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is

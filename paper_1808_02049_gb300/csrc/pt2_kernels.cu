@@ -1258,21 +1258,24 @@ __device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint6
 // key.
 
 constexpr int kSortThreads = kTileThreads;
-constexpr int kSortItems = kSortCap / kSortThreads;   // items per thread, striped
-constexpr int kSortRows = kSortItems * (kSortThreads / 32);
-constexpr int kCountersPerThread = 256 * kSortRows / kSortThreads;  // scanned by each thread
-constexpr int kLongRun = 8;                            // longer runs are summed by a warp
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = kSortCap / kSortThreads;  // items per thread
+constexpr int kWarpSpan = kSortCap / kSortWarps;     // positions a warp ranks in a digit pass
+constexpr int kLongRun = 8;                          // longer runs are summed by a warp
 static_assert(kSortItems * kSortThreads == kSortCap, "the sort holds whole items per thread");
-static_assert(kCountersPerThread % 8 == 0, "counters are scanned in 16-byte groups");
+static_assert(kWarpSpan == 32 * kSortItems, "a warp ranks whole rows of 32 positions");
+static_assert(kSortThreads == 256, "one thread per digit in the offset scan");
 static_assert(kBigThreads == kSortThreads, "every sorting CTA has the sort's width");
 
 struct SortSmem {
     uint64_t words[2][kSortCap];  // (hash << 16) | record index
     union {
-        uint16_t cnt16[256 * kSortRows];  // [digit][row] counts, then offsets
-        unsigned long long red[10][32];   // final statistics reduction
+        uint16_t cnt[kSortWarps][256];  // digit pass: per-warp digit counts, then offsets
+        struct {
+            uint16_t heads[kSortCap], longq[kSortCap];  // after the passes: run heads, long runs
+        } h;
+        unsigned long long red[10][32];  // final statistics reduction
     } u;
-    uint16_t heads[kSortCap], longq[kSortCap];
     uint16_t dbase[256];
     uint32_t warp_tot[33];
     unsigned int nheads, nlong, collision;
@@ -1288,87 +1291,51 @@ __device__ __forceinline__ uint32_t key_hash32(uint64_t a, uint64_t b)
     return (uint32_t)(h >> 32);
 }
 
-// Exclusive scan of one value per thread over the block.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t &total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t incl = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += t;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t w = lane < nw ? warp_tot[lane] : 0u;
-        uint32_t wi = w;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += t;
-        }
-        if (lane < nw) warp_tot[lane] = wi - w;
-        if (lane == 31) warp_tot[32] = wi;
-    }
-    __syncthreads();
-    total = warp_tot[32];
-    return warp_tot[warp] + incl - v;
-}
-
 // One stable counting-sort pass on the 8-bit digit at `shift` of the hash.
-// Positions are striped: item it of thread t is position it * T + t (T
-// threads), and row it * T/32 + warp counts the items of one warp at one item
-// index, so rows in order cover positions in order.  Ranks within a warp come
-// from __match_any_sync; 256 threads then scan the rows of one digit each and
-// a 256-entry scan gives the digit bases.
+// Warp w ranks positions [w * kWarpSpan, (w + 1) * kWarpSpan) row by row (32
+// positions per row, in order): __match_any_sync gives each item its rank
+// among equal digits of the row, added to the warp's running count of that
+// digit, which the row's lowest such lane then advances.  The counts live in
+// a per-warp table, so it is cleared with a warp barrier only.  Thread d then
+// turns digit d's per-warp counts into offsets and a block scan gives the
+// digit bases; every item lands at base + warp offset + rank.
 __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int cnt, int shift, SortSmem &S)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kSortThreads / 32;
-    uint4 *c4 = reinterpret_cast<uint4 *>(S.u.cnt16);
-    constexpr int n4 = 256 * kSortRows * 2 / 16;
-    for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
+    uint16_t *wc = S.u.cnt[warp];
+    reinterpret_cast<uint4 *>(wc)[lane] = make_uint4(0, 0, 0, 0);  // 32 lanes x 16 B = 256 counts
+    __syncwarp();
     uint64_t w[kSortItems];
     uint32_t dig[kSortItems], rank[kSortItems];
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-        const int pos = it * kSortThreads + tid;
+        const int pos = warp * kWarpSpan + it * 32 + lane;
         const bool valid = pos < cnt;
         w[it] = valid ? src[pos] : 0ull;
         const uint32_t d = (uint32_t)(w[it] >> (16 + shift)) & 0xFFu;
         // past-the-end lanes get a value no real digit has, so they match nobody
         const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
         dig[it] = d;
-        rank[it] = __popc(peers & lt);
-        if (valid && rank[it] == 0) S.u.cnt16[d * kSortRows + it * kWarps + warp] = (uint16_t)__popc(peers);
+        const uint32_t before = valid ? wc[d] : 0u;
+        rank[it] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wc[d] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive scan over its rows (vector loads), then the digit totals
+    // thread d: offsets of digit d within each warp's share, and its total
     uint32_t total_d = 0;
-    constexpr int nq = kSortRows * 2 / 16;  // uint4 per digit column
-    static_assert(kSortRows % 8 == 0, "a digit's rows fill whole 16-byte groups");
-    if (tid < 256) {
-        uint4 *col = c4 + tid * nq;
-        uint32_t run = 0;
+    {
+        const int d = tid;
 #pragma unroll
-        for (int q = 0; q < nq; ++q) {
-            uint4 x = col[q];
-            uint32_t v[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t lo = v[k] & 0xFFFFu, hi = v[k] >> 16;
-                const uint32_t olo = run;
-                run += lo;
-                v[k] = olo | (run << 16);
-                run += hi;
-            }
-            col[q] = make_uint4(v[0], v[1], v[2], v[3]);
+        for (int k = 0; k < kSortWarps; ++k) {
+            const uint32_t c = S.u.cnt[k][d];
+            S.u.cnt[k][d] = (uint16_t)total_d;
+            total_d += c;
         }
-        total_d = run;
     }
+    // exclusive scan of the digit totals: the digit bases
     {
         uint32_t incl = total_d;
 #pragma unroll
@@ -1376,20 +1343,18 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += t;
         }
-        if (lane == 31 && warp < 8) S.warp_tot[warp] = incl;
+        if (lane == 31) S.warp_tot[warp] = incl;
         __syncthreads();
-        if (tid < 256) {
-            uint32_t base = 0;
-            for (int k = 0; k < warp; ++k) base += S.warp_tot[k];
-            S.dbase[tid] = (uint16_t)(base + incl - total_d);
-        }
+        uint32_t base = 0;
+#pragma unroll
+        for (int k = 0; k < kSortWarps; ++k) base += k < warp ? S.warp_tot[k] : 0u;
+        S.dbase[tid] = (uint16_t)(base + incl - total_d);
     }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-        const int pos = it * kSortThreads + tid;
-        if (pos < cnt)
-            dst[S.dbase[dig[it]] + S.u.cnt16[dig[it] * kSortRows + it * kWarps + warp] + rank[it]] = w[it];
+        const int pos = warp * kWarpSpan + it * 32 + lane;
+        if (pos < cnt) dst[S.dbase[dig[it]] + S.u.cnt[warp][dig[it]] + rank[it]] = w[it];
     }
     __syncthreads();
 }
@@ -1476,7 +1441,7 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
             uint32_t base = 0;
             if (lane == 0 && m) base = atomicAdd(&S.nheads, (unsigned)__popc(m));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (head) S.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
+            if (head) S.u.h.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
         }
         __syncthreads();
         if (!S.collision) break;
@@ -1492,7 +1457,7 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
     }
     const int nh = (int)S.nheads;
     for (int h = tid; h < nh; h += kSortThreads) {
-        const int j = S.heads[h];
+        const int j = S.u.h.heads[h];
         const uint64_t hj = A[j] & hmask;
         const Rec &r0 = recs[A[j] & 0xFFFF];
         KeyVal v;
@@ -1502,7 +1467,7 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
         rec_value(r0, v.fixed, v.num, v.fl, v.fh);
         if (j + 1 < cnt && (A[j + 1] & hmask) == hj) {
             if (j + kLongRun < cnt && (A[j + kLongRun] & hmask) == hj) {
-                S.longq[atomicAdd(&S.nlong, 1u)] = (uint16_t)j;
+                S.u.h.longq[atomicAdd(&S.nlong, 1u)] = (uint16_t)j;
                 continue;
             }
             uint64_t fl = 0;
@@ -1522,7 +1487,7 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
     __syncthreads();
     const int nl = (int)S.nlong;
     for (int q = warp; q < nl; q += kSortThreads / 32) {
-        const int j = S.longq[q];
+        const int j = S.u.h.longq[q];
         const uint64_t hj = A[j] & hmask;
         uint64_t fl = 0;
         int64_t fh = 0;
@@ -1764,7 +1729,8 @@ struct BigSmem {
     uint64_t bar;
     unsigned int out_count;
     unsigned int big_pre[kMaxBatch + 1];  // oversize tiles before instance i
-    unsigned int bk_cnt[kBigBuckets], bk_off[kBigBuckets], bk_cur[kBigBuckets];  // hash split of partials
+    unsigned int bk_cnt[kBigBuckets];     // hash split of partials: bucket sizes (fill cursors while scattering)
+    unsigned short bk_off[kBigBuckets];   // bucket starts (< kBigScratch)
 };
 
 size_t big_smem_bytes() { return sizeof(BigSmem); }
@@ -1907,15 +1873,16 @@ __global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TilePara
                     if (threadIdx.x == 0) {
                         unsigned int run = 0;
                         for (int i = 0; i < nbk; ++i) {
-                            M.bk_off[i] = run;
-                            M.bk_cur[i] = run;
+                            M.bk_off[i] = (unsigned short)run;
                             run += M.bk_cnt[i];
+                            M.bk_cnt[i] = 0;  // refilled by the scatter below
                         }
                     }
                     __syncthreads();
                     for (unsigned long long i = threadIdx.x; i < u; i += nt) {
                         const Rec48 r = bufA[i];
-                        bufB[atomicAdd(&M.bk_cur[bucket_hash(r.a, r.b) & (nbk - 1)], 1u)] = r;
+                        const int k = bucket_hash(r.a, r.b) & (nbk - 1);
+                        bufB[M.bk_off[k] + atomicAdd(&M.bk_cnt[k], 1u)] = r;
                     }
                     __syncthreads();
                     for (int k = 0; k < nbk; ++k)
