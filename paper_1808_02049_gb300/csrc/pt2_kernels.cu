@@ -333,6 +333,20 @@ __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
     j1 = t - k * (k - 1) / 2;
 }
 
+// Counter updates on global memory.  The counters may be reached through
+// pointers read from a device table, so the global state space is named
+// explicitly: the compiler would otherwise emit generic (returning) atomics.
+__device__ __forceinline__ void red_add_global(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v));
+}
+__device__ __forceinline__ uint32_t atom_add_global(unsigned int *p, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(__cvta_generic_to_global(p)), "r"(v));
+    return old;
+}
+
 // One 32-byte record written with a single 256-bit store (one L2 sector).
 __device__ __forceinline__ void store_rec32(Rec32 *dst, uint64_t a, uint64_t b, double num, int64_t den)
 {
@@ -374,11 +388,11 @@ __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, i
         slot[u] = 0;
         if (ok[u]) {
             if constexpr (MODE == kModeTileCount) {
-                atomicAdd(&p.counts[__umul64hi(zt, p.n_tiles)], 1u);
+                red_add_global(&p.counts[__umul64hi(zt, p.n_tiles)], 1u);
             } else if constexpr (MODE == kModeEmit) {
-                slot[u] = atomicAdd(&p.cursor[__umul64hi(zt, p.n_tiles)], 1u);
+                slot[u] = atom_add_global(&p.cursor[__umul64hi(zt, p.n_tiles)], 1u);
             } else {
-                slot[u] = atomicAdd(&p.cursor[0], 1u);
+                slot[u] = atom_add_global(&p.cursor[0], 1u);
             }
         }
     }
@@ -475,8 +489,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             F.ZtaA = za;
             F.ZtbB = zb;
         }
-    } else if (warp == 1 || warp == 2) {
+    } else if (kVal && (warp == 1 || warp == 2)) {
         // g(x) = h_xx + p(x), p(x) = sum over occupied j of <xj||xj>, exact in 2^-48 units
+        // (only the modes that produce values need diagonals)
         const int spin = warp - 1;  // 0: alpha x, 1: beta x
         const int *os = spin ? F.occB : F.occA;
         const int *oo = spin ? F.occA : F.occB;
@@ -507,7 +522,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             uint32_t cl = class_of(zc);
             inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, a2);
         }
-        sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
+        if constexpr (kVal) sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
         sa_zt[s] = (MODE == kModeClassCount) ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
         sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17);
     }
@@ -515,7 +530,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         int i = s / nvb, j = s - (s / nvb) * nvb;
         int r = F.occB[i], a = F.virB[j];
         uint32_t sg = __popcll(B & between_mask(r, a)) & 1;
-        sb_delta[s] = F.gB[a] - F.gB[r] - WSx[r * N + a];
+        if constexpr (kVal) sb_delta[s] = F.gB[a] - F.gB[r] - WSx[r * N + a];
         sb_zt[s] = F.ZtbB ^ F.ztb[r] ^ F.ztb[a];
         sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16);
     }
@@ -671,7 +686,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                         const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
                         ka = a2;
                         kb = B ^ (1ull << rB) ^ (1ull << aB);
-                        num = flip_sign(cA * slice[rB * N + aB], bi >> 16);
+                        num = flip_sign(cA * __ldg(slice + rB * N + aB), bi >> 16);
                         den = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
                     });
             __syncwarp();
@@ -732,10 +747,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
                             // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
                             // a1 is the fastest-varying index across lanes
-                            const double e = eri[(((size_t)r2 * N + a2) * N + r1) * N + a1] -
-                                             eri[(((size_t)r1 * N + a2) * N + r2) * N + a1];
+                            const double e = __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) -
+                                             __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
                             num = flip_sign(c * e, par);
-                            den = base - vec[j1] - vec[j2] - WSx[a1 * N + a2];
+                            den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
                         });
                 __syncwarp();
             }
