@@ -106,8 +106,8 @@ typedef struct {
     uint64_t pass_budget_bytes; /* device bytes for one pass of generated
                                    terms (0 = derived from the context budget);
                                    smaller values mean more passes */
-    uint32_t tile_target;       /* mean terms per hash tile, at most 768
-                                   (0 = default 576) */
+    uint32_t tile_target;       /* mean terms per hash tile, at most 1024
+                                   (0 = default 832, or the tuned value) */
     uint32_t flags;             /* PT2_FLAG_* below */
 } pt2_opts;
 

@@ -26,8 +26,8 @@ double now_s()
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-constexpr uint64_t kDefaultTileTarget = 576;
-constexpr uint32_t kTuneCandidates[] = {320, 448, 576, 704};
+constexpr uint64_t kDefaultTileTarget = 832;
+constexpr uint32_t kTuneCandidates[] = {704, 768, 832, 896};
 
 int size_class(uint64_t total)
 {

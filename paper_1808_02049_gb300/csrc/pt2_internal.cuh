@@ -14,15 +14,16 @@ constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
 constexpr int kGenBatch = 8;                 // terms whose slots a lane requests before storing any
 constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per SM)
-constexpr int kTileCap = 768;                // records a tile CTA sorts in shared memory
-constexpr int kSortCap = 768;                // records one in-shared-memory sort handles
+constexpr int kTileCap = 1024;                // records a tile CTA sorts in shared memory
+constexpr int kSortCap = 1024;               // records one in-shared-memory sort handles
 constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)
 constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (4 B each) resident in L2
 constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
 // a step holds at most two full passes (batches, serving); its record slots are 32-bit
 static_assert(2 * (kMaxPassBytes / 32) < (1ull << 32), "record slots of a step must fit 32-bit tile cursors");
 constexpr int kBigThreads = 256;
-constexpr int kBigCap = 768;                 // Rec48 records sorted per chunk (oversize path)
+constexpr int kBigChunk = 768;              // records of an oversize tile sorted per chunk
+constexpr int kBigCap = 640;                // partial records finished per sort (oversize path)
 constexpr uint64_t kBigScratch = 16384;      // partial records per buffer of one oversize CTA
 constexpr int kBigBuckets = 256;             // most hash buckets the partials of one oversize tile split into
 static_assert(kBigBuckets * kBigCap >= 2 * kBigScratch, "the hash split can always make buckets fit a chunk");

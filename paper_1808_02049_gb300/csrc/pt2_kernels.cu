@@ -1281,6 +1281,7 @@ static_assert(kSortItems * kSortThreads == kSortCap, "the sort holds whole items
 static_assert(kWarpSpan == 32 * kSortItems, "a warp ranks whole rows of 32 positions");
 static_assert(kSortThreads == 256, "one thread per digit in the offset scan");
 static_assert(kBigThreads == kSortThreads, "every sorting CTA has the sort's width");
+static_assert(kBigChunk <= kSortCap && kBigCap <= kSortCap && kTileCap <= kSortCap, "chunks fit one sort");
 
 struct SortSmem {
     uint64_t words[2][kSortCap];  // (hash << 16) | record index
@@ -1736,7 +1737,7 @@ cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 // normal tile.  Exact sums make the result independent of the chunking.
 struct BigSmem {
     union {
-        Rec32 r32[kTileCap];
+        Rec32 r32[kBigChunk];
         Rec48 r48[kBigCap];
     } u;
     SortSmem S;
@@ -1828,8 +1829,8 @@ __global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TilePara
             bool bad = false;
             // round 1: Rec32 chunks -> reduced Rec48 in bufA
             unsigned long long u = 0;
-            for (unsigned long long cs = 0; !bad && cs < cnt; cs += kTileCap) {
-                const int m = (int)min((unsigned long long)kTileCap, cnt - cs);
+            for (unsigned long long cs = 0; !bad && cs < cnt; cs += kBigChunk) {
+                const int m = (int)min((unsigned long long)kBigChunk, cnt - cs);
                 if (u + (unsigned long long)m > p.scratch_cap) {  // uniform
                     if (threadIdx.x == 0) atomicOr(p.err, kErrScratch);
                     bad = true;

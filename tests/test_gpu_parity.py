@@ -104,11 +104,11 @@ def test_run_is_bit_identical_across_runs(ctx, cfg0):
     assert a == {**b, "seconds": a["seconds"]}
 
 
-@pytest.mark.parametrize("tile_target", [16, 256, 768])
+@pytest.mark.parametrize("tile_target", [16, 256, 1024])
 def test_tile_sizes_and_oversize_path(ctx, cfg0, tile_target):
     got = ctx.run(cfg0["rid"], tile_target=tile_target)
     assert_same_result(got, cfg0["ref"])
-    if tile_target == 768:
+    if tile_target == 1024:
         assert got["n_oversize"] > 0  # tiles above shared-memory capacity took the chunked path
 
 
@@ -124,7 +124,7 @@ def test_oversize_tiles_with_mostly_distinct_keys(ctx):
     try:
         ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
         assert ref["n_unique"] > 0.95 * ref["n_terms"]
-        got = ctx.run(rid, tile_target=768)
+        got = ctx.run(rid, tile_target=1024)
         assert got["n_oversize"] > 0.2 * got["n_tiles"]
         assert_same_result(got, ref)
         assert ctx.run(rid)["e2"] == got["e2"]
@@ -137,7 +137,7 @@ def test_e2_is_bit_identical_for_any_tiling_and_pass_plan(ctx, cfg0):
     # numerators and the energy are summed exactly in fixed point, so the
     # result cannot depend on how terms are split into passes and tiles
     base = ctx.run(cfg0["rid"])
-    for kw in [dict(tile_target=16), dict(tile_target=768), dict(pass_budget_bytes=12 << 20),
+    for kw in [dict(tile_target=16), dict(tile_target=1024), dict(pass_budget_bytes=12 << 20),
                dict(pass_budget_bytes=40 << 20, tile_target=100)]:
         got = ctx.run(cfg0["rid"], **kw)
         assert got["e2"] == base["e2"], kw
