@@ -39,7 +39,11 @@
  * Optional constraint (Algorithm 2, one constraint class): when mod > 1 only
  * excited determinants whose alpha word satisfies alpha % mod == rem are kept.
  * The classes r = 0..mod-1 are non-overlapping and complete, so their E2 sum
- * to the unconstrained E2.
+ * to the unconstrained E2.  When mod exceeds every alpha word (mod > 2^n_orb
+ * - 1) the class is the single alpha string rem; a single or double
+ * excitation changes at most two alpha orbitals, so a reference determinant
+ * whose alpha word differs from rem in more than four bits contributes
+ * nothing to it and is not enumerated.
  */
 #include <math.h>
 #include <stdint.h>
@@ -400,7 +404,9 @@ int64_t oracle_pt2(int n_orb, const double *h, const double *eri, int64_t n_det,
     map_t m;
     if (map_init(&m, 1 << 16)) return -2;
     uint64_t nterms = 0;
+    const int exact_alpha = cons_mod > 1 && (n_orb >= 64 || cons_mod > (1ull << n_orb) - 1ull);
     for (int64_t i = 0; i < n_det; ++i) {
+        if (exact_alpha && __builtin_popcountll(keys[2 * i] ^ cons_rem) > 4) continue;
         nterms += enumerate_det(&s, keys[2 * i], keys[2 * i + 1], coef[i], &cons, visit_map, &m);
         if (m.size == (size_t)-1) { map_free(&m); return -2; }
     }

@@ -143,6 +143,9 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.n_sb = r.nb * (s.n - r.nb);
     p.class_lo = 0;
     p.class_hi = kNumClasses;
+    p.bclass_lo = 0;
+    p.bclass_hi = kNumClasses;
+    p.heavy_class = 0;
     p.cons_mod = 1;
     p.err = (uint32_t *)c->err_word.ptr;
     return p;
@@ -217,6 +220,7 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
     for (int i = 0; i < kMaxOrb; ++i) ht.zc[i] = splitmix64(seed);
     for (int i = 0; i < kMaxOrb; ++i) ht.zta[i] = splitmix64(seed);
     for (int i = 0; i < kMaxOrb; ++i) ht.ztb[i] = splitmix64(seed);
+    for (int i = 0; i < kMaxOrb; ++i) ht.zcb[i] = splitmix64(seed);
     e = cudaMemcpy(c->hash.ptr, &ht, sizeof ht, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
     *out = c.release();

@@ -98,8 +98,31 @@ cudaError_t gen_launch(pt2_ctx *c, GenMode mode, GenBatch b, uint64_t n_ctas, in
     return cudaSuccess;
 }
 
+// Terms per beta class among the terms of alpha class k of a job (one
+// beta-count launch over the job's determinants).
+int beta_counts(pt2_ctx *c, const Job &j, uint32_t k, std::vector<unsigned long long> &out)
+{
+    GenParams g = j.gp;
+    g.det_begin = 0;
+    g.heavy_class = k;
+    g.class_counts = reinterpret_cast<unsigned long long *>(c->class_counts.ptr);
+    gen_layout(g, kModeBetaCount);
+    cudaStream_t st = c->stream;
+    CK(cudaMemsetAsync(c->class_counts.ptr, 0, kNumClasses * 8, st), "memset");
+    GenBatch b{nullptr, nullptr, 1, 0, g};
+    CK(gen_launch(c, kModeBetaCount, b, j.r->n_det, g.smem_bytes), "beta count kernel");
+    out.assign(kNumClasses, 0);
+    CK(cudaMemcpyAsync(out.data(), c->class_counts.ptr, kNumClasses * 8, cudaMemcpyDeviceToHost, st), "copy");
+    CK(cudaStreamSynchronize(st), "sync");
+    return PT2_OK;
+}
+
 // Work list: one class-count launch over all jobs (alpha-hash classes play
-// the role of the paper's constraints), then each job's passes.
+// the role of the paper's constraints), then each job's passes.  An alpha
+// class with more terms than a pass holds (an alpha string shared by many
+// reference determinants) is split further by the beta-hash classes of its
+// terms, counted by a beta-count launch, as the paper splits a heavy
+// constraint into finer ones.
 int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint64_t step_cap)
 {
     const size_t n = jobs.size();
@@ -155,16 +178,50 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
         if (cap < 1024) return fail(c, PT2_ERR_OOM, "pass budget is too small (%llu records)", (unsigned long long)cap);
         j.pass_cap = cap;
         j.passes.clear();
-        Pass cur{0, 0, 0, 0};
+        Pass cur;
+        cur.c_lo = 0;
         for (int k = 0; k < kNumClasses; ++k) {
-            if (cl[k] > cap)
-                return fail(c, PT2_ERR_OOM,
-                            "alpha class %d holds %llu terms, above the %llu a pass can hold; raise the budget", k,
-                            (unsigned long long)cl[k], (unsigned long long)cap);
+            if (cl[k] > cap) {  // heavy alpha class: passes over its beta classes
+                if (cur.records > 0) {
+                    cur.c_hi = k;
+                    j.passes.push_back(cur);
+                }
+                std::vector<unsigned long long> bh;
+                if ((rc = beta_counts(c, j, (uint32_t)k, bh))) return rc;
+                unsigned long long sum = 0;
+                Pass bp;
+                bp.c_lo = k;
+                bp.c_hi = k + 1;
+                bp.b_lo = 0;
+                for (int b = 0; b < kNumClasses; ++b) {
+                    sum += bh[b];
+                    if (bh[b] > cap)
+                        return fail(c, PT2_ERR_OOM,
+                                    "alpha class %d, beta class %d holds %llu terms, above the %llu a pass can "
+                                    "hold; raise the budget",
+                                    k, b, (unsigned long long)bh[b], (unsigned long long)cap);
+                    if (bp.records + bh[b] > cap) {
+                        bp.b_hi = b;
+                        j.passes.push_back(bp);
+                        bp.b_lo = b;
+                        bp.records = 0;
+                    }
+                    bp.records += bh[b];
+                }
+                bp.b_hi = kNumClasses;
+                if (bp.records > 0) j.passes.push_back(bp);
+                if (sum != cl[k])
+                    return fail(c, PT2_ERR_CUDA, "beta counts of alpha class %d sum to %llu, not %llu", k, sum,
+                                (unsigned long long)cl[k]);
+                cur = Pass();
+                cur.c_lo = k + 1;
+                continue;
+            }
             if (cur.records + cl[k] > cap) {
                 cur.c_hi = k;
                 j.passes.push_back(cur);
-                cur = Pass{(uint32_t)k, 0, 0, 0};
+                cur = Pass();
+                cur.c_lo = k;
             }
             cur.records += cl[k];
         }
@@ -246,6 +303,8 @@ GenParams step_item_params(pt2_ctx *c, const StepPlan &sp, size_t i, uint64_t ti
     GenParams g = j.gp;
     g.class_lo = P.c_lo;
     g.class_hi = P.c_hi;
+    g.bclass_lo = P.b_lo;
+    g.bclass_hi = P.b_hi;
     g.n_tiles = P.n_tiles;
     g.tile_base = tile_base;
     g.det_begin = 0;

@@ -77,11 +77,12 @@ struct SysDev {
 
 struct HashTables {
     uint64_t zc[kMaxOrb];   // alpha class hash (Zobrist)
+    uint64_t zcb[kMaxOrb];  // beta class hash: splits the passes of a heavy alpha class
     uint64_t zta[kMaxOrb];  // tile hash, alpha part
     uint64_t ztb[kMaxOrb];  // tile hash, beta part
 };
 
-enum GenMode { kModeClassCount = 0, kModeTileCount = 1, kModeEmit = 2, kModeDetTerms = 3 };
+enum GenMode { kModeClassCount = 0, kModeTileCount = 1, kModeEmit = 2, kModeDetTerms = 3, kModeBetaCount = 4 };
 
 struct GenParams {
     SysDev sys;
@@ -94,7 +95,9 @@ struct GenParams {
     uint64_t det_begin;    // first determinant of this launch
     int na, nb;            // electrons per spin (same for all determinants)
     // pass selection
-    uint32_t class_lo, class_hi;  // classes [lo, hi) belong to the pass
+    uint32_t class_lo, class_hi;  // alpha classes [lo, hi) belong to the pass
+    uint32_t bclass_lo, bclass_hi;  // and, within them, beta classes [lo, hi) (all: 0, kNumClasses)
+    uint32_t heavy_class;         // beta-count mode: the alpha class whose beta classes are counted
     uint64_t cons_mod, cons_rem;  // alpha % mod == rem (mod <= 1: none)
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance

@@ -314,14 +314,17 @@ __device__ void block_scan_excl_u32(uint32_t *a, int n, uint32_t *warp_tot)
 // ======================================================= generation kernel
 
 struct GenFixed {
-    uint64_t zc[kMaxOrb], zta[kMaxOrb], ztb[kMaxOrb];
+    uint64_t zc[kMaxOrb], zcb[kMaxOrb], zta[kMaxOrb], ztb[kMaxOrb];
     int64_t gA[kMaxOrb], gB[kMaxOrb];  // (h_xx + p(x)) * 2^48 for alpha / beta spin-orbital x
     int occA[kMaxOrb], virA[kMaxOrb], occB[kMaxOrb], virB[kMaxOrb];
-    uint64_t A, B, ZcA, ZtaA, ZtbB;
+    uint64_t A, B, ZcA, ZcbB, ZtaA, ZtbB;
     double c;
     int64_t d0;
-    int n_sa_pass, a_in_pass;
+    int n_sa_pass, a_in_pass, n_sb_pass, b_in_pass;
 };
+
+// beta class of a beta-string hash (splits the heavy alpha classes)
+__device__ __forceinline__ uint32_t bclass_of(uint64_t zcb) { return (uint32_t)(zcb >> (64 - kClassBits)); }
 
 // colex order of pairs: t = j2 (j2 - 1) / 2 + j1, j1 < j2
 __device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
@@ -429,6 +432,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     int64_t *sb_delta = reinterpret_cast<int64_t *>(smem + p.smem_sb);
     uint64_t *sb_zt = reinterpret_cast<uint64_t *>(sb_delta + p.n_sb);
     uint32_t *sb_info = reinterpret_cast<uint32_t *>(sb_zt + p.n_sb);
+    uint16_t *sb_pass = reinterpret_cast<uint16_t *>(sb_info + p.n_sb);
     uint16_t *pairs = reinterpret_cast<uint16_t *>(smem + p.smem_pairs);
     int64_t *vec_all = reinterpret_cast<int64_t *>(smem + p.smem_vec);
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + p.smem_hist);
@@ -436,6 +440,11 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nw = kGenThreads / 32;
     constexpr bool kVal = MODE == kModeEmit || MODE == kModeDetTerms;
+    constexpr bool kCount = MODE == kModeClassCount || MODE == kModeBetaCount;
+    // pass membership of a term: alpha class in [class_lo, class_hi) and beta
+    // class in [bclass_lo, bclass_hi); most passes take every beta class
+    const bool bfull = p.bclass_lo == 0 && p.bclass_hi >= (uint32_t)kNumClasses;
+    const uint32_t blo = p.bclass_lo, bhi = p.bclass_hi;
     const int N = p.sys.n;
     const int na = p.na, nb = p.nb, nva = N - na, nvb = N - nb;
     const double *__restrict__ eri = p.sys.eri;
@@ -446,6 +455,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
     for (int i = tid; i < kMaxOrb; i += kGenThreads) {
         F.zc[i] = p.hash->zc[i];
+        F.zcb[i] = p.hash->zcb[i];
         F.zta[i] = p.hash->zta[i];
         F.ztb[i] = p.hash->ztb[i];
     }
@@ -454,7 +464,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         pair_of(t, j1, j2);
         pairs[t] = (uint16_t)(j1 | (j2 << 8));
     }
-    if constexpr (MODE == kModeClassCount)
+    if constexpr (kCount)
         for (int i = tid; i < kNumClasses; i += kGenThreads) hist[i] = 0;
     if (tid == 0) {
         uint64_t A = p.keys[2 * det], B = p.keys[2 * det + 1];
@@ -472,20 +482,25 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     }
     __syncthreads();
     if (warp == 0) {
-        uint64_t zc = 0, za = 0, zb = 0;
+        uint64_t zc = 0, za = 0, zb = 0, zcb = 0;
         for (int i = lane; i < na; i += 32) {
             zc ^= F.zc[F.occA[i]];
             za ^= F.zta[F.occA[i]];
         }
-        for (int i = lane; i < nb; i += 32) zb ^= F.ztb[F.occB[i]];
+        for (int i = lane; i < nb; i += 32) {
+            zb ^= F.ztb[F.occB[i]];
+            zcb ^= F.zcb[F.occB[i]];
+        }
 #pragma unroll
         for (int off = 16; off; off >>= 1) {
             zc ^= __shfl_xor_sync(0xffffffffu, zc, off);
             za ^= __shfl_xor_sync(0xffffffffu, za, off);
             zb ^= __shfl_xor_sync(0xffffffffu, zb, off);
+            zcb ^= __shfl_xor_sync(0xffffffffu, zcb, off);
         }
         if (lane == 0) {
             F.ZcA = zc;
+            F.ZcbB = zcb;
             F.ZtaA = za;
             F.ZtbB = zb;
         }
@@ -518,12 +533,14 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         uint32_t inp;
         if constexpr (MODE == kModeClassCount) {
             inp = cons_ok(p.cons_mod, p.cons_rem, a2);
+        } else if constexpr (MODE == kModeBetaCount) {
+            inp = class_of(zc) == p.heavy_class && cons_ok(p.cons_mod, p.cons_rem, a2);
         } else {
             uint32_t cl = class_of(zc);
             inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, a2);
         }
         if constexpr (kVal) sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
-        sa_zt[s] = (MODE == kModeClassCount) ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
+        sa_zt[s] = kCount ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
         sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17);
     }
     for (int s = tid; s < p.n_sb; s += kGenThreads) {
@@ -531,16 +548,24 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         int r = F.occB[i], a = F.virB[j];
         uint32_t sg = __popcll(B & between_mask(r, a)) & 1;
         if constexpr (kVal) sb_delta[s] = F.gB[a] - F.gB[r] - WSx[r * N + a];
-        sb_zt[s] = F.ZtbB ^ F.ztb[r] ^ F.ztb[a];
-        sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16);
+        const uint64_t zcb = F.ZcbB ^ F.zcb[r] ^ F.zcb[a];  // beta class hash of the excited beta string
+        // the beta-count mode histograms beta classes, so it keeps that hash here
+        sb_zt[s] = MODE == kModeBetaCount ? zcb : (F.ZtbB ^ F.ztb[r] ^ F.ztb[a]);
+        const uint32_t bc = bclass_of(zcb);
+        const uint32_t binp = bfull || (bc >= blo && bc < bhi);
+        sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (binp << 17);
     }
     if (tid == 0) {
         bool ok = cons_ok(p.cons_mod, p.cons_rem, A);
-        if constexpr (MODE != kModeClassCount) {
+        if constexpr (MODE == kModeBetaCount) {
+            ok = ok && class_of(F.ZcA) == p.heavy_class;
+        } else if constexpr (MODE != kModeClassCount) {
             uint32_t cl = class_of(F.ZcA);
             ok = ok && cl >= p.class_lo && cl < p.class_hi;
         }
         F.a_in_pass = ok;
+        const uint32_t bc = bclass_of(F.ZcbB);
+        F.b_in_pass = bfull || (bc >= blo && bc < bhi);
     }
     __syncthreads();
     // compact the alpha singles of the pass (warp 0, ballot + popc)
@@ -554,10 +579,22 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             base += __popc(m);
         }
         if (lane == 0) F.n_sa_pass = base;
+    } else if (warp == 1 && !bfull) {
+        // and the beta singles whose beta class belongs to the pass
+        int base = 0;
+        for (int s0 = 0; s0 < p.n_sb; s0 += 32) {
+            int s = s0 + lane;
+            bool f = s < p.n_sb && ((sb_info[s] >> 17) & 1u);
+            uint32_t m = __ballot_sync(0xffffffffu, f);
+            if (f) sb_pass[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)s;
+            base += __popc(m);
+        }
+        if (lane == 0) F.n_sb_pass = base;
     }
     __syncthreads();
     const int n_sa_pass = F.n_sa_pass;
     const bool a_in = F.a_in_pass != 0;
+    const bool b_in = F.b_in_pass != 0;
 
     const int n_occ_pairs_a = na * (na - 1) / 2, n_vir_pairs_a = nva * (nva - 1) / 2;
     const int n_occ_pairs_b = nb * (nb - 1) / 2, n_vir_pairs_b = nvb * (nvb - 1) / 2;
@@ -587,6 +624,45 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         for (int i = tid; i < kNumClasses; i += kGenThreads)
             if (hist[i]) atomicAdd(&p.class_counts[i], (unsigned long long)hist[i]);
         return;
+    } else if constexpr (MODE == kModeBetaCount) {
+        // beta classes of the terms whose alpha class is the heavy class K:
+        // alpha singles and alpha-alpha doubles keep beta = B; beta singles
+        // (alpha = A) and alpha-beta doubles (alpha single in K) take the
+        // beta string of a beta single; beta-beta doubles one of their own
+        const uint32_t K = p.heavy_class;
+        const uint32_t per_sb = (uint32_t)n_sa_pass + (a_in ? 1u : 0u);
+        if (per_sb)
+            for (int sb = tid; sb < p.n_sb; sb += kGenThreads) atomicAdd(&hist[bclass_of(sb_zt[sb])], per_sb);
+        uint32_t keepB = 0;  // terms of class K whose beta string is B
+        if (tid == 0) keepB = (uint32_t)n_sa_pass;
+        for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
+            int pr = pairs[pi];
+            int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+            uint64_t z12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
+            uint64_t a12 = A ^ (1ull << r1) ^ (1ull << r2);
+            for (int t = lane; t < n_vir_pairs_a; t += 32) {
+                int pv = pairs[t];
+                int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
+                if (class_of(z12 ^ F.zc[a1] ^ F.zc[a2]) != K) continue;
+                if (!cons_ok(p.cons_mod, p.cons_rem, a12 ^ (1ull << a1) ^ (1ull << a2))) continue;
+                ++keepB;
+            }
+        }
+        if (keepB) atomicAdd(&hist[bclass_of(F.ZcbB)], keepB);
+        if (a_in)
+            for (int pi = warp; pi < n_occ_pairs_b; pi += nw) {
+                int pr = pairs[pi];
+                int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
+                uint64_t z12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
+                for (int t = lane; t < n_vir_pairs_b; t += 32) {
+                    int pv = pairs[t];
+                    atomicAdd(&hist[bclass_of(z12 ^ F.zcb[F.virB[pv & 0xFF]] ^ F.zcb[F.virB[pv >> 8]])], 1u);
+                }
+            }
+        __syncthreads();
+        for (int i = tid; i < kNumClasses; i += kGenThreads)
+            if (hist[i]) atomicAdd(&p.class_counts[i], (unsigned long long)hist[i]);
+        return;
     } else {
         const uint64_t ZtaA = F.ZtaA, ZtbB = F.ZtbB;
         EmitOut out;
@@ -599,9 +675,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         out.e0 = p.e0;
         const uint32_t class_lo = p.class_lo, class_hi = p.class_hi;
         const uint64_t cons_mod = p.cons_mod, cons_rem = p.cons_rem;
-        const int n_sb = p.n_sb;
+        // beta singles of the pass: all of them, or the compacted list
+        const int n_sb = bfull ? p.n_sb : F.n_sb_pass;
+        auto sb_at = [&](int k) { return bfull ? k : (int)sb_pass[k]; };
 
-        // ---- alpha singles (few per determinant: O(n) element each)
+        // ---- alpha singles (few per determinant: O(n) element each); beta string B
+        if (b_in)
         for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch)
             emit_batch<MODE>(
                 out, k0, kGenThreads, n_sa_pass,
@@ -632,11 +711,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             for (int s0 = tid; s0 < n_sb; s0 += kGenThreads * kGenBatch)
                 emit_batch<MODE>(
                     out, s0, kGenThreads, n_sb,
-                    [&](int s, uint64_t &zt) {
-                        zt = ZtaA ^ sb_zt[s];
+                    [&](int k, uint64_t &zt) {
+                        zt = ZtaA ^ sb_zt[sb_at(k)];
                         return true;
                     },
-                    [&](int s, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                    [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                        const int s = sb_at(k);
                         const uint32_t info = sb_info[s];
                         const int r = info & 0xFF, a = (info >> 8) & 0xFF;
                         double v = ht[a * N + r];
@@ -677,11 +757,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             for (int sb0 = lane; sb0 < n_sb; sb0 += 32 * kGenBatch)
                 emit_batch<MODE>(
                     out, sb0, 32, n_sb,
-                    [&](int sb, uint64_t &zt) {
-                        zt = ztA ^ sb_zt[sb];
+                    [&](int k, uint64_t &zt) {
+                        zt = ztA ^ sb_zt[sb_at(k)];
                         return true;
                     },
-                    [&](int sb, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                    [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                        const int sb = sb_at(k);
                         const uint32_t bi = sb_info[sb];
                         const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
                         ka = a2;
@@ -693,6 +774,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         }
         // ---- same-spin doubles: one occupied pair per warp, virtual pairs over lanes
         for (int spin = 0; spin < 2; ++spin) {
+            if (spin == 0 && !b_in) continue;  // alpha-alpha doubles keep beta string B
             if (spin == 1 && !a_in) break;
             const int npo = spin ? n_occ_pairs_b : n_occ_pairs_a;
             const int npv = spin ? n_vir_pairs_b : n_vir_pairs_a;
@@ -706,6 +788,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 const int r1 = occ[pr & 0xFF], r2 = occ[pr >> 8];
                 const uint64_t w12 = W ^ (1ull << r1) ^ (1ull << r2);
                 const uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
+                const uint64_t zcb12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
                 const uint64_t zt12 =
                     spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
                 int64_t base = 0;
@@ -731,6 +814,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 if (!cons_ok(cons_mod, cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
                                 zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
                             } else {
+                                if (!bfull) {
+                                    const uint32_t bc = bclass_of(zcb12 ^ F.zcb[a1] ^ F.zcb[a2]);
+                                    if (bc < blo || bc >= bhi) return false;
+                                }
                                 zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
                             }
                             return true;
@@ -964,10 +1051,16 @@ __global__ void ref_tile_kernel(const RefPartParams p)
         zc ^= p.hash->zc[k];
         zt ^= p.hash->zta[k];
     }
-    for (uint64_t x = B; x; x &= x - 1) zt ^= p.hash->ztb[__ffsll((long long)x) - 1];
-    const uint32_t cl = class_of(zc);
+    uint64_t zcb = 0;
+    for (uint64_t x = B; x; x &= x - 1) {
+        int k = __ffsll((long long)x) - 1;
+        zt ^= p.hash->ztb[k];
+        zcb ^= p.hash->zcb[k];
+    }
+    const uint32_t cl = class_of(zc), bc = bclass_of(zcb);
     uint32_t t = 0xFFFFFFFFu;
-    if (cl >= q.class_lo && cl < q.class_hi && cons_ok(q.cons_mod, q.cons_rem, A)) {
+    if (cl >= q.class_lo && cl < q.class_hi && bc >= q.bclass_lo && bc < q.bclass_hi &&
+        cons_ok(q.cons_mod, q.cons_rem, A)) {
         t = (uint32_t)(q.tile_base + __umul64hi(zt, q.n_tiles));
         atomicAdd(&p.ref_count[t], 1u);
     }
@@ -1993,13 +2086,13 @@ void gen_layout(GenParams &p, GenMode mode)
     p.smem_sa = (int)off;
     off = al(off + (size_t)p.n_sa * (8 + 8 + 4 + 2));
     p.smem_sb = (int)off;
-    off = al(off + (size_t)p.n_sb * (8 + 8 + 4));
+    off = al(off + (size_t)p.n_sb * (8 + 8 + 4 + 2));
     p.smem_pairs = (int)off;
     off = al(off + (size_t)(kMaxOrb * (kMaxOrb - 1) / 2) * 2);
     p.smem_vec = (int)off;
     off = al(off + (size_t)(kGenThreads / 32) * kMaxOrb * 8);
     p.smem_hist = (int)off;
-    if (mode == kModeClassCount) off = al(off + (size_t)kNumClasses * 4);
+    if (mode == kModeClassCount || mode == kModeBetaCount) off = al(off + (size_t)kNumClasses * 4);
     p.smem_bytes = (int)off;
 }
 
@@ -2010,6 +2103,7 @@ cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int sme
     case kModeClassCount: gen_kernel<kModeClassCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
     case kModeTileCount: gen_kernel<kModeTileCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
     case kModeEmit: gen_kernel<kModeEmit><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeBetaCount: gen_kernel<kModeBetaCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -2041,6 +2135,8 @@ cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm)
     if ((e = cudaFuncSetAttribute(gen_kernel<kModeTileCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
         return e;
     if ((e = cudaFuncSetAttribute(gen_kernel<kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    if ((e = cudaFuncSetAttribute(gen_kernel<kModeBetaCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
+        return e;
     if ((e = cudaFuncSetAttribute(gen_kernel_one<kModeDetTerms>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
         return e;
     if ((e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes())))

@@ -40,11 +40,14 @@ struct RefRes {
 constexpr int kPhases = 8;
 
 // One memory-bounded pass of an instance: the alpha-hash classes
-// [c_lo, c_hi) (a set of Algorithm 2 constraints), its terms and tiles.
+// [c_lo, c_hi) (a set of Algorithm 2 constraints) and, for an alpha class too
+// heavy for one pass, the beta-hash classes [b_lo, b_hi) within it; its terms
+// and tiles.
 struct Pass {
-    uint32_t c_lo, c_hi;
-    uint64_t records;
-    uint64_t n_tiles;
+    uint32_t c_lo = 0, c_hi = 0;
+    uint32_t b_lo = 0, b_hi = kNumClasses;
+    uint64_t records = 0;
+    uint64_t n_tiles = 0;
 };
 
 // One PT2 solve scheduled by the engine.

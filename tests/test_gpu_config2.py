@@ -1,0 +1,84 @@
+"""The 24-electron / 60-orbital / 1,000,000-determinant workload (4.8e11
+generated terms) at full size, in the launch configuration of a plain run.
+
+Here the Hartree-Fock alpha string is shared by about 234,000 reference
+determinants, so its alpha class holds about 1.8e10 terms, more than any pass;
+the engine splits it by beta class.  The oracle cannot enumerate the full sum
+in test time, so the full run is checked through properties that hold at any
+size (closed-form term count, set bookkeeping, identical energy and set for a
+different pass plan), and parity with the oracle on one alpha string: the
+constraint with a modulus above every alpha word keeps exactly that string
+(Algorithm 2 with a one-string constraint), which the oracle computes from
+the few reference determinants within a double excitation of it.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_02049_gb300 import inputs, pt2
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N_DET = 1_000_000
+N_ORB, N_EL = 60, 12
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    from paper_1808_02049_gb300 import build
+
+    build.build_library()
+    s, r = inputs.make_config(2)
+    assert r.n_det == N_DET
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    c = pt2.Context(0)
+    sid = c.load_system(s.h, s.eri)
+    rid = c.load_reference(sid, r.keys, r.coef, e0)
+    yield dict(c=c, s=s, r=r, e0=e0, rid=rid)
+    c.close()
+
+
+def test_full_size_with_heavy_alpha_class(cfg2):
+    c, rid = cfg2["c"], cfg2["rid"]
+    alpha = cfg2["r"].keys[0::2]
+    assert np.unique(alpha, return_counts=True)[1].max() > 200_000
+    a = c.run(rid)
+    n, v = N_EL, N_ORB - N_EL
+    T = 2 * n * v + 2 * math.comb(n, 2) * math.comb(v, 2) + (n * v) ** 2
+    assert a["n_terms"] == T * N_DET == 481_824_000_000
+    assert a["n_unique"] == a["n_in_ref"] + a["n_external"]
+    assert a["n_in_ref"] <= N_DET
+    assert a["n_passes"] > a["n_terms"] // (48 << 30) * 32
+    assert math.isfinite(a["e2"]) and a["e2"] < 0
+    # a smaller pass budget splits the classes differently: same energy and set
+    b = c.run(rid, pass_budget_bytes=16 << 30)
+    assert b["n_passes"] > a["n_passes"]
+    assert b["e2"] == a["e2"]
+    assert (b["digest_sum"], b["digest_xor"], b["n_external"]) == (a["digest_sum"], a["digest_xor"], a["n_external"])
+
+
+@pytest.mark.parametrize("level", [3, 4])
+def test_one_alpha_string_matches_oracle(cfg2, level):
+    # the smallest alpha string of the reference that is a triple (quadruple)
+    # excitation of the Hartree-Fock one: a few thousand (hundred) reference
+    # determinants lie within a double excitation of it
+    c, s, r, e0, rid = cfg2["c"], cfg2["s"], cfg2["r"], cfg2["e0"], cfg2["rid"]
+    alpha = r.keys[0::2]
+    hf = (1 << N_EL) - 1
+    dist = np.array([bin(int(x) ^ hf).count("1") for x in alpha])
+    a0 = int(alpha[dist == 2 * level].min())
+    cls = (1 << 63, a0)
+    got = c.run(rid, constraint=cls)
+    ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=cls)
+    assert ref["n_terms"] > 0
+    assert got["n_terms"] == ref["n_terms"]
+    assert got["n_external"] == ref["n_external"]
+    assert got["n_in_ref"] == ref["n_in_ref"]
+    assert (got["digest_sum"], got["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
+    assert got["n_pos_denom"] == ref["n_pos_denom"]
+    assert abs(got["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
+    # the class energy is small, so check it relatively as well
+    assert abs(got["e2"] - ref["e2"]) <= 1e-10 * abs(ref["e2"])

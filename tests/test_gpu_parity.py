@@ -145,6 +145,21 @@ def test_e2_is_bit_identical_for_any_tiling_and_pass_plan(ctx, cfg0):
             (base["digest_sum"], base["digest_xor"], base["n_external"])
 
 
+def test_heavy_alpha_class_is_split_by_beta_class(ctx, cfg0):
+    # 288 of the 1000 determinants share the Hartree-Fock alpha string, so its
+    # alpha class holds at least 288 * (4*12 + 6*66) = 127,872 terms; a 1 MB
+    # pass budget holds about 32,000, so that class must be split into passes
+    # by beta class (the run fails otherwise) and give the same result
+    alpha = cfg0["r"].keys[0::2]
+    assert np.unique(alpha, return_counts=True)[1].max() == 288
+    base = ctx.run(cfg0["rid"])
+    got = ctx.run(cfg0["rid"], pass_budget_bytes=1 << 20)
+    assert got["n_passes"] > 90
+    assert_same_result(got, cfg0["ref"])
+    assert got["e2"] == base["e2"]
+    assert (got["digest_sum"], got["digest_xor"]) == (base["digest_sum"], base["digest_xor"])
+
+
 def test_many_passes(ctx, cfg0):
     # a 12 MB pass budget forces several memory-bounded passes
     got = ctx.run(cfg0["rid"], pass_budget_bytes=12 << 20)

@@ -217,6 +217,34 @@ def test_constraint_classes_partition_the_sum():
     assert abs(sum(p["e2"] for p in parts) - base["e2"]) <= 1e-13 * abs(base["e2"])
 
 
+def test_single_alpha_string_classes_partition_the_sum():
+    # With a modulus above every alpha word the constraint keeps one alpha
+    # string, and the oracle skips reference determinants more than a double
+    # excitation away from it.  Over all C(16, 4) = 1820 alpha strings the
+    # classes are complete, so they must rebuild the unconstrained result;
+    # a wrongly skipped determinant would lose its terms.
+    import itertools
+
+    s, r = inputs.make_config(0, n_det=60)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    base = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
+    mod = 1 << 40
+    tot_terms = tot_ext = dsum = dxor = 0
+    e2 = 0.0
+    for occ in itertools.combinations(range(16), 4):
+        a = sum(1 << q for q in occ)
+        p = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=(mod, a))
+        tot_terms += p["n_terms"]
+        tot_ext += p["n_external"]
+        dsum = (dsum + p["digest_sum"]) % 2 ** 64
+        dxor ^= p["digest_xor"]
+        e2 += p["e2"]
+    assert tot_terms == base["n_terms"]
+    assert tot_ext == base["n_external"]
+    assert (dsum, dxor) == (base["digest_sum"], base["digest_xor"])
+    assert abs(e2 - base["e2"]) <= 1e-13 * abs(base["e2"])
+
+
 def test_oracle_rejects_invalid_reference():
     s, r = inputs.make_config(0, n_det=10)
     bad = r.keys.copy()
