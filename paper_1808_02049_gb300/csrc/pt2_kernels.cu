@@ -321,7 +321,25 @@ struct GenFixed {
     double c;
     int64_t d0;
     int n_sa_pass, a_in_pass, n_sb_pass, b_in_pass;
+    uint32_t wsum[kGenThreads / 32];
 };
+
+// Narrow passes (at most kNarrowClasses alpha classes) find their alpha-alpha
+// doubles through a table of the determinant's virtual alpha pairs bucketed by
+// the top kVbkBits bits of the pair's class hash: the class of the double is
+// (hash of the occupied part) xor (hash of the virtual pair), so for each
+// occupied pair only the buckets that can land in the pass are visited.
+constexpr int kVbkBits = 10;
+constexpr int kVbkBuckets = 1 << kVbkBits;
+constexpr int kNarrowClasses = 120;  // at most 32 buckets per occupied pair
+constexpr int kMaxVirPairs = kMaxOrb * (kMaxOrb - 1) / 2;
+static_assert(kVbkBuckets == 4 * kGenThreads, "the bucket scan takes four buckets per thread");
+static_assert((kNarrowClasses + 3) / 4 + 1 <= 32, "a narrow pass needs at most one bucket per lane");
+__device__ __forceinline__ uint32_t vb_bucket(uint64_t z) { return (uint32_t)(z >> (64 - kVbkBits)); }
+
+// Shared memory of the bucket table (in the histogram area, unused by the
+// emitting modes): counts then cursors, starts, pair list, per-warp lookups.
+constexpr size_t kVbkBytes = kVbkBuckets * 4 + (kVbkBuckets + 1) * 2 + kMaxVirPairs * 2 + (kGenThreads / 32) * 64 * 2 + 16;
 
 // beta class of a beta-string hash (splits the heavy alpha classes)
 __device__ __forceinline__ uint32_t bclass_of(uint64_t zcb) { return (uint32_t)(zcb >> (64 - kClassBits)); }
@@ -679,6 +697,52 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         const int n_sb = bfull ? p.n_sb : F.n_sb_pass;
         auto sb_at = [&](int k) { return bfull ? k : (int)sb_pass[k]; };
 
+        // bucket table of the virtual alpha pairs (narrow passes only)
+        const bool narrow = class_hi - class_lo <= (uint32_t)kNarrowClasses;
+        uint32_t *vb_cnt = reinterpret_cast<uint32_t *>(smem + p.smem_hist);
+        uint16_t *vb_off = reinterpret_cast<uint16_t *>(vb_cnt + kVbkBuckets);
+        uint16_t *vb_list = vb_off + kVbkBuckets + 1;
+        uint16_t *vb_warp = vb_list + kMaxVirPairs;
+        if (narrow && b_in) {  // uniform across the CTA
+            for (int b = tid; b < kVbkBuckets; b += kGenThreads) vb_cnt[b] = 0;
+            __syncthreads();
+            for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
+                const int pv = pairs[t];
+                atomicAdd(&vb_cnt[vb_bucket(F.zc[F.virA[pv & 0xFF]] ^ F.zc[F.virA[pv >> 8]])], 1u);
+            }
+            __syncthreads();
+            {
+                const uint4 c4 = reinterpret_cast<const uint4 *>(vb_cnt)[tid];
+                const uint32_t sum = c4.x + c4.y + c4.z + c4.w;
+                uint32_t incl = sum;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                if (lane == 31) F.wsum[warp] = incl;
+                __syncthreads();
+                uint32_t run = incl - sum;
+#pragma unroll
+                for (int k = 0; k < nw; ++k) run += k < warp ? F.wsum[k] : 0u;
+                const uint32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    vb_off[4 * tid + k] = (uint16_t)run;
+                    vb_cnt[4 * tid + k] = run;  // scatter cursor
+                    run += c[k];
+                }
+                if (tid == kGenThreads - 1) vb_off[kVbkBuckets] = (uint16_t)run;
+            }
+            __syncthreads();
+            for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
+                const int pv = pairs[t];
+                const uint32_t b = vb_bucket(F.zc[F.virA[pv & 0xFF]] ^ F.zc[F.virA[pv >> 8]]);
+                vb_list[atomicAdd(&vb_cnt[b], 1u)] = (uint16_t)t;
+            }
+            __syncthreads();
+        }
+
         // ---- alpha singles (few per determinant: O(n) element each); beta string B
         if (b_in)
         for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch)
@@ -802,10 +866,46 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     __syncwarp();
                     base = d0 + g[r1] + g[r2] - WSx[r1 * N + r2];
                 }
-                for (int t0 = lane; t0 < npv; t0 += 32 * kGenBatch)
+                // items: every virtual pair, or (narrow alpha-alpha) the pairs of the
+                // buckets (q ^ top bits of zc12), q over the pass's classes
+                const bool nar = spin == 0 && narrow;
+                int nitems = npv, nq = 0;
+                uint16_t *ws = vb_warp + warp * 64;  // [0, 32): bucket starts, [32, 64): item offsets
+                if (nar) {
+                    const uint32_t u = vb_bucket(zc12);
+                    const uint32_t q0 = class_lo >> (kClassBits - kVbkBits);
+                    const uint32_t q1 = (class_hi - 1) >> (kClassBits - kVbkBits);
+                    nq = (int)(q1 - q0 + 1);
+                    uint32_t start = 0, sz = 0;
+                    if (lane < nq) {
+                        const uint32_t b = (q0 + (uint32_t)lane) ^ u;
+                        start = vb_off[b];
+                        sz = (uint32_t)vb_off[b + 1] - start;
+                    }
+                    uint32_t incl = sz;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += v;
+                    }
+                    if (lane < nq) {
+                        ws[lane] = (uint16_t)start;
+                        ws[32 + lane] = (uint16_t)(incl - sz);
+                    }
+                    nitems = (int)__shfl_sync(0xffffffffu, incl, 31);
+                    __syncwarp();
+                }
+                auto pair_at = [&](int i) -> int {
+                    if (!nar) return i;
+                    int k = 0;
+                    while (k + 1 < nq && (int)ws[32 + k + 1] <= i) ++k;
+                    return vb_list[ws[k] + (i - (int)ws[32 + k])];
+                };
+                for (int t0 = lane; t0 < nitems; t0 += 32 * kGenBatch)
                     emit_batch<MODE>(
-                        out, t0, 32, npv,
-                        [&](int t, uint64_t &zt) {
+                        out, t0, 32, nitems,
+                        [&](int i, uint64_t &zt) {
+                            const int t = pair_at(i);
                             const int pv = pairs[t];
                             const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
                             if (spin == 0) {
@@ -822,7 +922,8 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                             }
                             return true;
                         },
-                        [&](int t, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                        [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                            const int t = pair_at(i);
                             const int pv = pairs[t];
                             const int j1 = pv & 0xFF, j2 = pv >> 8;
                             const int a1 = vir[j1], a2 = vir[j2];
@@ -2094,6 +2195,7 @@ void gen_layout(GenParams &p, GenMode mode)
     off = al(off + (size_t)(kGenThreads / 32) * kMaxOrb * 8);
     p.smem_hist = (int)off;
     if (mode == kModeClassCount || mode == kModeBetaCount) off = al(off + (size_t)kNumClasses * 4);
+    else off = al(off + kVbkBytes);
     p.smem_bytes = (int)off;
 }
 
