@@ -895,51 +895,57 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     nitems = (int)__shfl_sync(0xffffffffu, incl, 31);
                     __syncwarp();
                 }
-                auto pair_at = [&](int i) -> int {
-                    if (!nar) return i;
-                    int k = 0;
-                    while (k + 1 < nq && (int)ws[32 + k + 1] <= i) ++k;
-                    return vb_list[ws[k] + (i - (int)ws[32 + k])];
-                };
-                for (int t0 = lane; t0 < nitems; t0 += 32 * kGenBatch)
-                    emit_batch<MODE>(
-                        out, t0, 32, nitems,
-                        [&](int i, uint64_t &zt) {
-                            const int t = pair_at(i);
-                            const int pv = pairs[t];
-                            const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
-                            if (spin == 0) {
-                                uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
-                                if (cl < class_lo || cl >= class_hi) return false;
-                                if (!cons_ok(cons_mod, cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
-                                zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
-                            } else {
-                                if (!bfull) {
-                                    const uint32_t bc = bclass_of(zcb12 ^ F.zcb[a1] ^ F.zcb[a2]);
-                                    if (bc < blo || bc >= bhi) return false;
+                // the same emission over items mapped to virtual pairs by `pair_at`
+                // (instantiated separately for the direct and the bucketed case)
+                auto emit_pairs = [&](int n_items, auto pair_at) {
+                    for (int t0 = lane; t0 < n_items; t0 += 32 * kGenBatch)
+                        emit_batch<MODE>(
+                            out, t0, 32, n_items,
+                            [&](int i, uint64_t &zt) {
+                                const int t = pair_at(i);
+                                const int pv = pairs[t];
+                                const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
+                                if (spin == 0) {
+                                    uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
+                                    if (cl < class_lo || cl >= class_hi) return false;
+                                    if (!cons_ok(cons_mod, cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
+                                    zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
+                                } else {
+                                    if (!bfull) {
+                                        const uint32_t bc = bclass_of(zcb12 ^ F.zcb[a1] ^ F.zcb[a2]);
+                                        if (bc < blo || bc >= bhi) return false;
+                                    }
+                                    zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
                                 }
-                                zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
-                            }
-                            return true;
-                        },
-                        [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
-                            const int t = pair_at(i);
-                            const int pv = pairs[t];
-                            const int j1 = pv & 0xFF, j2 = pv >> 8;
-                            const int a1 = vir[j1], a2 = vir[j2];
-                            const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
-                            ka = spin ? A : w2;
-                            kb = spin ? w2 : B;
-                            const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
-                            const uint32_t par =
-                                __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                            // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
-                            // a1 is the fastest-varying index across lanes
-                            const double e = __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) -
-                                             __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
-                            num = flip_sign(c * e, par);
-                            den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
-                        });
+                                return true;
+                            },
+                            [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                                const int t = pair_at(i);
+                                const int pv = pairs[t];
+                                const int j1 = pv & 0xFF, j2 = pv >> 8;
+                                const int a1 = vir[j1], a2 = vir[j2];
+                                const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
+                                ka = spin ? A : w2;
+                                kb = spin ? w2 : B;
+                                const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
+                                const uint32_t par =
+                                    __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                                // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
+                                // a1 is the fastest-varying index across lanes
+                                const double e = __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) -
+                                                 __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
+                                num = flip_sign(c * e, par);
+                                den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
+                            });
+                };
+                if (nar)
+                    emit_pairs(nitems, [&](int i) -> int {
+                        int k = 0;
+                        while (k + 1 < nq && (int)ws[32 + k + 1] <= i) ++k;
+                        return vb_list[ws[k] + (i - (int)ws[32 + k])];
+                    });
+                else
+                    emit_pairs(npv, [](int i) -> int { return i; });
                 __syncwarp();
             }
         }
