@@ -13,7 +13,7 @@ constexpr int kClassBits = 12;               // alpha-hash classes used to form 
 constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
 constexpr int kGenBatch = 8;                 // terms whose slots a lane requests before storing any
-constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per SM)
+constexpr int kTileThreads = 256;            // tile sort-reduce CTA (1024 / kTileThreads per SM)
 constexpr int kTileCap = 1024;                // records a tile CTA sorts in shared memory
 constexpr int kSortCap = 1024;               // records one in-shared-memory sort handles
 constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)

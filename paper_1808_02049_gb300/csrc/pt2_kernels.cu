@@ -1477,10 +1477,11 @@ constexpr int kSortThreads = kTileThreads;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = kSortCap / kSortThreads;  // items per thread
 constexpr int kWarpSpan = kSortCap / kSortWarps;     // positions a warp ranks in a digit pass
+constexpr int kSortCtasPerSm = 1024 / kSortThreads;  // sorting CTAs per SM the registers are sized for
 constexpr int kLongRun = 8;                          // longer runs are summed by a warp
 static_assert(kSortItems * kSortThreads == kSortCap, "the sort holds whole items per thread");
 static_assert(kWarpSpan == 32 * kSortItems, "a warp ranks whole rows of 32 positions");
-static_assert(kSortThreads == 256, "one thread per digit in the offset scan");
+static_assert(kSortThreads % 256 == 0, "the first 256 threads take one digit each in the offset scan");
 static_assert(kBigThreads == kSortThreads, "every sorting CTA has the sort's width");
 static_assert(kBigChunk <= kSortCap && kBigCap <= kSortCap && kTileCap <= kSortCap, "chunks fit one sort");
 
@@ -1541,9 +1542,9 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
         __syncwarp();
     }
     __syncthreads();
-    // thread d: offsets of digit d within each warp's share, and its total
+    // thread d < 256: offsets of digit d within each warp's share, and its total
     uint32_t total_d = 0;
-    {
+    if (tid < 256) {
         const int d = tid;
 #pragma unroll
         for (int k = 0; k < kSortWarps; ++k) {
@@ -1552,7 +1553,7 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
             total_d += c;
         }
     }
-    // exclusive scan of the digit totals: the digit bases
+    // exclusive scan of the digit totals over warps 0..7: the digit bases
     {
         uint32_t incl = total_d;
 #pragma unroll
@@ -1560,12 +1561,14 @@ __device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += t;
         }
-        if (lane == 31) S.warp_tot[warp] = incl;
+        if (lane == 31 && warp < 8) S.warp_tot[warp] = incl;
         __syncthreads();
-        uint32_t base = 0;
+        if (tid < 256) {
+            uint32_t base = 0;
 #pragma unroll
-        for (int k = 0; k < kSortWarps; ++k) base += k < warp ? S.warp_tot[k] : 0u;
-        S.dbase[tid] = (uint16_t)(base + incl - total_d);
+            for (int k = 0; k < 8; ++k) base += k < warp ? S.warp_tot[k] : 0u;
+            S.dbase[tid] = (uint16_t)(base + incl - total_d);
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -1796,8 +1799,8 @@ __device__ __forceinline__ void finish_keyval(const TileParams &p, double e0, co
     finish_key(p, e0, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
 }
 
-// Shared memory of the main tile kernel (two CTAs share an SM, so one CTA's
-// tile load and barriers overlap the other's work).
+// Shared memory of the main tile kernel (several CTAs share an SM, so one CTA's
+// tile load and barriers overlap the others' work).
 struct MainSmem {
     Rec32 recs[kTileCap];
     SortSmem S;
@@ -1854,7 +1857,7 @@ __device__ __forceinline__ int tile_instance(const unsigned long long *__restric
 // tile metadata one tile ahead, so each tile's TMA load starts at once.
 // Tiles of one instance are consecutive, so a CTA's statistics are flushed
 // to an instance's accumulator when its tiles move on to the next instance.
-__global__ void __launch_bounds__(kTileThreads, 4) tile_kernel(const TileParams p)
+__global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
@@ -1983,7 +1986,7 @@ __device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst
 // the next instance.  The partial lists live in a fixed per-CTA scratch of
 // two buffers of scratch_cap records; a tile whose partials outgrow it sets
 // kErrScratch.
-__global__ void __launch_bounds__(kBigThreads, 4) big_tile_kernel(const TileParams p)
+__global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BigSmem &M = *reinterpret_cast<BigSmem *>(smem_raw);
