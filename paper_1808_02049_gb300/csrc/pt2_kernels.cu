@@ -953,9 +953,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 }
 
 // Generator over the determinants of several instances (one CTA each).
-// The counting modes fit four CTAs per SM (64 registers); emission needs more.
+// Four CTAs per SM (64 registers): more warps hide the L2 round trips of the slot atomics.
 template <int MODE>
-__global__ void __launch_bounds__(kGenThreads, MODE == kModeEmit ? 3 : 4) gen_kernel(const GenBatch b)
+__global__ void __launch_bounds__(kGenThreads, 4) gen_kernel(const GenBatch b)
 {
     if (b.n_inst == 1) {
         gen_body<MODE>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
