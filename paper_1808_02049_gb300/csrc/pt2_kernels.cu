@@ -1465,13 +1465,13 @@ __device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint6
 // shared memory.  Each key is compressed to a 32-bit hash (the paper's
 // compression of keys by hash functions) carried in a 64-bit word with the
 // record's index, and the words are sorted with a stable LSD radix sort staged
-// through shared memory: two 8-bit digit passes over the low 16 hash bits,
-// each ranking items within a warp with __match_any_sync against the warp's
-// running digit counts, scanning the counts into offsets and scattering.
-// Equal keys then form contiguous runs.  Every run is checked against the
-// full 128-bit key: a short run holding several keys (a 16-bit collision) is
-// grouped by key when reduced; a longer one sends the chunk through two more
-// passes, to the full 32-bit hash, and a collision there to an exact path.
+// through shared memory: three 8-bit digit passes over the low 24 hash bits
+// (a fourth over the top 8 bits only when two different keys share those 24),
+// each ranking items within a warp with __match_any_sync, scanning the
+// per-(digit, warp, item) counts into offsets and scattering.  Equal keys then
+// form contiguous runs; every run is verified against the full 128-bit key (a
+// remaining hash collision sends the chunk to an exact path) and reduced by
+// key.
 
 constexpr int kSortThreads = kTileThreads;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -1479,7 +1479,6 @@ constexpr int kSortItems = kSortCap / kSortThreads;  // items per thread
 constexpr int kWarpSpan = kSortCap / kSortWarps;     // positions a warp ranks in a digit pass
 constexpr int kSortCtasPerSm = 1024 / kSortThreads;  // sorting CTAs per SM the registers are sized for
 constexpr int kLongRun = 8;                          // longer runs are summed by a warp
-constexpr int kMaxConflicts = 64;                    // 16-bit hash collisions grouped within their runs
 static_assert(kSortItems * kSortThreads == kSortCap, "the sort holds whole items per thread");
 static_assert(kWarpSpan == 32 * kSortItems, "a warp ranks whole rows of 32 positions");
 static_assert(kSortThreads % 256 == 0, "the first 256 threads take one digit each in the offset scan");
@@ -1497,8 +1496,7 @@ struct SortSmem {
     } u;
     uint16_t dbase[256];
     uint32_t warp_tot[33];
-    uint16_t conf[kMaxConflicts];  // positions whose key differs from the previous one of their run
-    unsigned int nheads, nlong, collision, nconf;
+    unsigned int nheads, nlong, collision;
 };
 
 __device__ __forceinline__ uint32_t key_hash32(uint64_t a, uint64_t b)
@@ -1621,8 +1619,7 @@ __device__ __forceinline__ void rec_add(const Rec48 &r, uint64_t &fl, int64_t &f
 
 // Sort the chunk and hand every unique key to `emit` (any order; every thread
 // may call it).  Returns false, for all threads, if two different keys share
-// the full 32-bit hash; then nothing was emitted and the caller must use the
-// exact path.
+// a hash; then nothing was emitted and the caller must use the exact path.
 template <class Rec, class Emit>
 __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_t &err, Emit &&emit)
 {
@@ -1632,7 +1629,6 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
         S.nheads = 0;
         S.nlong = 0;
         S.collision = 0;
-        S.nconf = 0;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
@@ -1640,16 +1636,15 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
         if (pos < cnt) A[pos] = ((uint64_t)key_hash32(recs[pos].a, recs[pos].b) << 16) | (uint64_t)pos;
     }
     __syncthreads();
-    // Two digit passes order the words by the low 16 hash bits.  Different
-    // keys that share those bits (about n^2 / 2^17 pairs for n keys) leave runs
-    // holding several keys; short runs are grouped by key when they are
-    // reduced.  Only a mixed run too long for that (or too many collisions)
-    // sends the chunk through two more passes, to the full 32-bit hash.
+    // three digit passes order the words by the low 24 hash bits; a fourth
+    // (the top 8 bits) runs only if two different keys share those 24 bits
     lsd_pass(A, B, cnt, 0, S);
     lsd_pass(B, A, cnt, 8, S);
-    uint64_t hmask = 0xFFFFull << 16;
+    lsd_pass(A, B, cnt, 16, S);
+    uint64_t hmask = 0xFFFFFFull << 16;
+    A = S.words[1];
     for (int round = 0; round < 2; ++round) {
-        // heads of equal-hash runs; a key change inside a run is a conflict
+        // heads of equal-hash runs; a run must also hold a single 128-bit key
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
             const int pos = it * kSortThreads + tid;
@@ -1659,11 +1654,7 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
                 head = pos == 0 || (A[pos - 1] & hmask) != (wv & hmask);
                 if (!head) {
                     const Rec &r0 = recs[wv & 0xFFFF], &rp = recs[A[pos - 1] & 0xFFFF];
-                    if (r0.a != rp.a || r0.b != rp.b) {
-                        const unsigned c = round == 0 ? atomicAdd(&S.nconf, 1u) : (unsigned)kMaxConflicts;
-                        if (c < (unsigned)kMaxConflicts) S.conf[c] = (uint16_t)pos;
-                        else S.collision = 1;
-                    }
+                    if (r0.a != rp.a || r0.b != rp.b) S.collision = 1;
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, head);
@@ -1673,29 +1664,15 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
             if (head) S.u.h.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
         }
         __syncthreads();
-        if (round == 0 && !S.collision) {
-            // a run holding a conflict must be short enough to group
-            const int nc = (int)S.nconf;
-            for (int c = tid; c < nc; c += kSortThreads) {
-                const int pos = S.conf[c];
-                const uint64_t h = A[pos] & hmask;
-                int st = pos, en = pos + 1;
-                while (st > 0 && (A[st - 1] & hmask) == h) --st;
-                while (en < cnt && (A[en] & hmask) == h && en - st <= kLongRun) ++en;
-                if (en - st > kLongRun) S.collision = 1;
-            }
-            __syncthreads();
-        }
         if (!S.collision) break;
         if (round == 1) return false;
         __syncthreads();
         if (tid == 0) {
             S.nheads = 0;
-            S.nconf = 0;
             S.collision = 0;
         }
-        lsd_pass(A, B, cnt, 16, S);
-        lsd_pass(B, A, cnt, 24, S);
+        lsd_pass(S.words[1], S.words[0], cnt, 24, S);
+        A = S.words[0];
         hmask = 0xFFFFFFFFull << 16;
     }
     const int nh = (int)S.nheads;
@@ -1716,46 +1693,10 @@ __device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_
             uint64_t fl = 0;
             int64_t fh = 0;
             rec_add(r0, fl, fh, err);
-            int e = j + 1;
-            bool mixed = false;
-            for (; e < cnt && (A[e] & hmask) == hj; ++e) {
-                const Rec &r2 = recs[A[e] & 0xFFFF];
-                if (r2.a != v.a || r2.b != v.b) mixed = true;
+            for (int k = j + 1; k < cnt && (A[k] & hmask) == hj; ++k) {
+                const Rec &r2 = recs[A[k] & 0xFFFF];
                 rec_add(r2, fl, fh, err);
                 v.den = r2.den < v.den ? r2.den : v.den;
-            }
-            if (mixed) {
-                // several keys share the run's hash bits: group them by key
-                // (at most kLongRun records; a bit per record marks it done)
-                uint32_t done = 0;
-                for (int i = j; i < e; ++i) {
-                    if ((done >> (i - j)) & 1u) continue;
-                    const Rec &ri = recs[A[i] & 0xFFFF];
-                    KeyVal g;
-                    g.a = ri.a;
-                    g.b = ri.b;
-                    g.den = ri.den;
-                    rec_value(ri, g.fixed, g.num, g.fl, g.fh);
-                    uint64_t gl = 0;
-                    int64_t gh = 0;
-                    int n = 0;
-                    for (int k = i; k < e; ++k) {
-                        const Rec &rk = recs[A[k] & 0xFFFF];
-                        if (rk.a != ri.a || rk.b != ri.b) continue;
-                        done |= 1u << (k - j);
-                        rec_add(rk, gl, gh, err);
-                        g.den = rk.den < g.den ? rk.den : g.den;
-                        ++n;
-                    }
-                    if (n > 1) {
-                        g.fixed = true;
-                        g.num = 0.0;
-                        g.fl = gl;
-                        g.fh = gh;
-                    }
-                    emit(g);
-                }
-                continue;
             }
             v.fixed = true;
             v.fl = fl;
