@@ -287,7 +287,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_name(args.n_det) + f"; bounded sample: first {m} determinants per step",
+            "config": {"workload": workload_name(args.n_det),
+                       "sample": f"bounded sample: PT2 of the first {m} reference determinants per step",
                        "l2": "CPU run"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"full PT2 of the first {m} reference determinants per step"},
