@@ -256,6 +256,21 @@ def profiled_traffic_per_term(kernel):
     return PROFILED_TRAFFIC.get(kernel)
 
 
+def replica_totals(elapsed, units, device):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    and the units all ranks processed (one all-reduce each; no-op alone)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed), float(units)
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -351,14 +366,7 @@ def run_gpu(args):
     clocks = sampler.stop()
     total_ms = float(sum(step_ms))
     terms = sum(x["n_terms"] for x in results)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms, float(terms)], dtype=torch.float64, device=f"cuda:{local}")
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, terms = float(mx[0]), float(t[1])
+    total_ms, terms = replica_totals(total_ms, terms, f"cuda:{local}")
     e2s = {x["e2"] for x in results}
 
     # end to end through the C ABI with host buffers: load system and reference
@@ -377,6 +385,8 @@ def run_gpu(args):
         ctx.unload(rid2)
         ctx.unload(sid2)
     e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_s, e2e_terms = replica_totals(e2e_s, e2e_terms, f"cuda:{local}")
 
     extra = {}
     if rank == 0 and not args.no_batch:
