@@ -436,54 +436,6 @@ __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, i
     }
 }
 
-// As emit_batch, for terms whose value needs one integral load: pre(i) issues
-// it together with the slot atomics of the batch, so both round trips overlap;
-// val(i, x, ...) then uses the loaded value x.
-template <int MODE, class KeyFn, class PreFn, class ValFn>
-__device__ __forceinline__ void emit_batch_pre(const EmitOut &p, int i0, int step, int n, KeyFn key, PreFn pre,
-                                               ValFn val)
-{
-    constexpr bool kVal = MODE == kModeEmit || MODE == kModeDetTerms;
-    uint32_t slot[kGenBatch];
-    bool ok[kGenBatch];
-    double x[kGenBatch];
-#pragma unroll
-    for (int u = 0; u < kGenBatch; ++u) {
-        const int i = i0 + u * step;
-        uint64_t zt = 0;
-        ok[u] = i < n && key(i, zt);
-        slot[u] = 0;
-        x[u] = 0.0;
-        if (ok[u]) {
-            if constexpr (MODE == kModeTileCount) {
-                red_add_global(&p.counts[__umul64hi(zt, p.n_tiles)], 1u);
-            } else if constexpr (MODE == kModeEmit) {
-                slot[u] = atom_add_global(&p.cursor[__umul64hi(zt, p.n_tiles)], 1u);
-            } else {
-                slot[u] = atom_add_global(&p.cursor[0], 1u);
-            }
-            if constexpr (kVal) x[u] = pre(i);
-        }
-    }
-    if constexpr (kVal) {
-#pragma unroll
-        for (int u = 0; u < kGenBatch; ++u) {
-            if (!ok[u]) continue;
-            if (slot[u] >= p.rec_cap) {  // emission disagrees with the counts
-                if constexpr (MODE == kModeEmit) atomicOr(p.err, kErrCount);
-                continue;
-            }
-            uint64_t a, b;
-            double num;
-            int64_t den;
-            val(i0 + u * step, x[u], a, b, num, den);
-            if constexpr (MODE == kModeDetTerms)  // this mode reports H_aa itself (as double bits)
-                den = __double_as_longlong(p.e0 - den_to_double(den));
-            store_rec32(p.recs + slot[u], a, b, num, den);
-        }
-    }
-}
-
 // All singles and doubles of determinant `det` of one instance (the body of
 // both generator kernels).
 template <int MODE>
@@ -867,23 +819,19 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 slice = eri + ((size_t)rA * N + aA) * N * N;
             }
             for (int sb0 = lane; sb0 < n_sb; sb0 += 32 * kGenBatch)
-                emit_batch_pre<MODE>(
+                emit_batch<MODE>(
                     out, sb0, 32, n_sb,
                     [&](int k, uint64_t &zt) {
                         zt = ztA ^ sb_zt[sb_at(k)];
                         return true;
                     },
-                    [&](int k) {
-                        const uint32_t bi = sb_info[sb_at(k)];
-                        return __ldg(slice + (bi & 0xFF) * N + ((bi >> 8) & 0xFF));
-                    },
-                    [&](int k, double x, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                    [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
                         const int sb = sb_at(k);
                         const uint32_t bi = sb_info[sb];
                         const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
                         ka = a2;
                         kb = B ^ (1ull << rB) ^ (1ull << aB);
-                        num = flip_sign(cA * x, bi >> 16);
+                        num = flip_sign(cA * __ldg(slice + rB * N + aB), bi >> 16);
                         den = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
                     });
             __syncwarp();
@@ -951,7 +899,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 // (instantiated separately for the direct and the bucketed case)
                 auto emit_pairs = [&](int n_items, auto pair_at) {
                     for (int t0 = lane; t0 < n_items; t0 += 32 * kGenBatch)
-                        emit_batch_pre<MODE>(
+                        emit_batch<MODE>(
                             out, t0, 32, n_items,
                             [&](int i, uint64_t &zt) {
                                 const int t = pair_at(i);
@@ -971,15 +919,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 }
                                 return true;
                             },
-                            [&](int i) {
-                                // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
-                                // a1 is the fastest-varying index across lanes
-                                const int pv = pairs[pair_at(i)];
-                                const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
-                                return __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) -
-                                       __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
-                            },
-                            [&](int i, double e, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
+                            [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
                                 const int t = pair_at(i);
                                 const int pv = pairs[t];
                                 const int j1 = pv & 0xFF, j2 = pv >> 8;
@@ -990,6 +930,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
                                 const uint32_t par =
                                     __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                                // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
+                                // a1 is the fastest-varying index across lanes
+                                const double e = __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) -
+                                                 __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
                                 num = flip_sign(c * e, par);
                                 den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
                             });
