@@ -84,7 +84,7 @@ void free_system(pt2_ctx *c, SystemRes &s)
 
 void free_ref(pt2_ctx *c, RefRes &r)
 {
-    DevBuf *b[] = {&r.keys, &r.coef, &r.hii, &r.d0};
+    DevBuf *b[] = {&r.keys, &r.coef, &r.hii, &r.d0, &r.g};
     for (DevBuf *x : b) dev_free(c, *x);
 }
 
@@ -135,6 +135,7 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.keys = (const uint64_t *)r.keys.ptr;
     p.coef = (const double *)r.coef.ptr;
     p.d0 = (const int64_t *)r.d0.ptr;
+    p.g = (const int64_t *)r.g.ptr;
     p.e0 = r.e0;
     p.n_det = r.n_det;
     p.na = r.na;
@@ -221,6 +222,8 @@ int pt2_create(pt2_ctx **out, int device, uint64_t hbm_budget_bytes)
     for (int i = 0; i < kMaxOrb; ++i) ht.zta[i] = splitmix64(seed);
     for (int i = 0; i < kMaxOrb; ++i) ht.ztb[i] = splitmix64(seed);
     for (int i = 0; i < kMaxOrb; ++i) ht.zcb[i] = splitmix64(seed);
+    for (int j2 = 1, t = 0; j2 < kMaxOrb; ++j2)
+        for (int j1 = 0; j1 < j2; ++j1, ++t) ht.pairs[t] = (uint16_t)(j1 | (j2 << 8));
     e = cudaMemcpy(c->hash.ptr, &ht, sizeof ht, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(nullptr, PT2_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
     *out = c.release();
@@ -373,7 +376,8 @@ int pt2_load_reference(pt2_ctx *c, uint32_t system_id, uint64_t n_det, const uin
     int rc;
     if ((rc = dev_alloc(c, r->keys, n_det * 16, "reference keys")) ||
         (rc = dev_alloc(c, r->coef, n_det * 8, "coefficients")) ||
-        (rc = dev_alloc(c, r->hii, n_det * 8, "diagonals")) || (rc = dev_alloc(c, r->d0, n_det * 8, "denominators"))) {
+        (rc = dev_alloc(c, r->hii, n_det * 8, "diagonals")) || (rc = dev_alloc(c, r->d0, n_det * 8, "denominators")) ||
+        (rc = dev_alloc(c, r->g, n_det * 2 * (size_t)s.n * 8, "orbital energies"))) {
         free_ref(c, *r);
         return rc;
     }
@@ -382,6 +386,8 @@ int pt2_load_reference(pt2_ctx *c, uint32_t system_id, uint64_t n_det, const uin
     CK(launch_diag(sys_dev(s), (const uint64_t *)r->keys.ptr, n_det, (double *)r->hii.ptr, c->stream),
        "diagonal kernel");
     CK(launch_ref_d0((const double *)r->hii.ptr, n_det, e0, (int64_t *)r->d0.ptr, c->stream), "denominator kernel");
+    CK(launch_ref_g(sys_dev(s), (const uint64_t *)r->keys.ptr, n_det, (int64_t *)r->g.ptr, c->stream),
+       "orbital energy kernel");
     {
         // E0 - H_ii must lie inside the fixed-point range of the diagonal
         std::vector<double> hii(n_det);

@@ -80,6 +80,7 @@ struct HashTables {
     uint64_t zcb[kMaxOrb];  // beta class hash: splits the passes of a heavy alpha class
     uint64_t zta[kMaxOrb];  // tile hash, alpha part
     uint64_t ztb[kMaxOrb];  // tile hash, beta part
+    uint16_t pairs[kMaxOrb * (kMaxOrb - 1) / 2];  // colex pair t -> (j1 | j2 << 8), j1 < j2
 };
 
 enum GenMode { kModeClassCount = 0, kModeTileCount = 1, kModeEmit = 2, kModeDetTerms = 3, kModeBetaCount = 4 };
@@ -90,6 +91,7 @@ struct GenParams {
     const uint64_t *keys;  // 2 * n_det
     const double *coef;
     const int64_t *d0;     // (E0 - H_ii) * 2^48 per determinant
+    const int64_t *g;      // per determinant, 2 n values: (h_xx + p(x)) * 2^48, alpha x then beta x
     double e0;
     uint64_t n_det;
     uint64_t det_begin;    // first determinant of this launch
@@ -188,6 +190,7 @@ cudaError_t launch_gen_single(GenMode mode, const GenParams &p, GenParams *d_par
                               cudaStream_t s);  // one determinant (parity aid); d_* are 1- and 2-entry scratch
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s);
 cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s);
+cudaError_t launch_ref_g(const SysDev &sys, const uint64_t *keys, uint64_t n, int64_t *g, cudaStream_t s);
 cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint32_t *out32, uint64_t n,
                                    unsigned long long *tmp, cudaStream_t s);
 size_t scan_tmp_elems(uint64_t n);

@@ -344,15 +344,6 @@ constexpr size_t kVbkBytes = kVbkBuckets * 4 + (kVbkBuckets + 1) * 2 + kMaxVirPa
 // beta class of a beta-string hash (splits the heavy alpha classes)
 __device__ __forceinline__ uint32_t bclass_of(uint64_t zcb) { return (uint32_t)(zcb >> (64 - kClassBits)); }
 
-// colex order of pairs: t = j2 (j2 - 1) / 2 + j1, j1 < j2
-__device__ __forceinline__ void pair_of(int t, int &j1, int &j2)
-{
-    int k = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-    while (k * (k - 1) / 2 > t) --k;
-    while ((k + 1) * k / 2 <= t) ++k;
-    j2 = k;
-    j1 = t - k * (k - 1) / 2;
-}
 
 // Counter updates on global memory.  The counters may be reached through
 // pointers read from a device table, so the global state space is named
@@ -477,25 +468,29 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         F.zta[i] = p.hash->zta[i];
         F.ztb[i] = p.hash->ztb[i];
     }
-    for (int t = tid; t < N * (N - 1) / 2; t += kGenThreads) {
-        int j1, j2;
-        pair_of(t, j1, j2);
-        pairs[t] = (uint16_t)(j1 | (j2 << 8));
-    }
+    for (int t = tid; t < N * (N - 1) / 2; t += kGenThreads) pairs[t] = p.hash->pairs[t];
     if constexpr (kCount)
         for (int i = tid; i < kNumClasses; i += kGenThreads) hist[i] = 0;
-    if (tid == 0) {
-        uint64_t A = p.keys[2 * det], B = p.keys[2 * det + 1];
-        F.A = A;
-        F.B = B;
-        F.c = p.coef[det];
-        F.d0 = p.d0[det];
-        int ia = 0, iva = 0, ib = 0, ivb = 0;
-        for (int q = 0; q < N; ++q) {
-            if ((A >> q) & 1ull) F.occA[ia++] = q;
-            else F.virA[iva++] = q;
-            if ((B >> q) & 1ull) F.occB[ib++] = q;
-            else F.virB[ivb++] = q;
+    {
+        // occupied and virtual lists, one orbital per thread: its rank among
+        // the occupied (virtual) orbitals below it is a population count
+        const uint64_t A = p.keys[2 * det], B = p.keys[2 * det + 1];
+        if (tid < N) {
+            const int q = tid;
+            const uint64_t below = (1ull << q) - 1ull;
+            const int ra = __popcll(A & below), rb = __popcll(B & below);
+            if ((A >> q) & 1ull) F.occA[ra] = q;
+            else F.virA[q - ra] = q;
+            if ((B >> q) & 1ull) F.occB[rb] = q;
+            else F.virB[q - rb] = q;
+        }
+        if constexpr (kVal)  // g(x) = h_xx + p(x), exact in 2^-48 units, from the reference tables
+            for (int i = tid; i < 2 * N; i += kGenThreads) (i < N ? F.gA : F.gB)[i < N ? i : i - N] = p.g[det * 2 * N + i];
+        if (tid == 0) {
+            F.A = A;
+            F.B = B;
+            F.c = p.coef[det];
+            F.d0 = p.d0[det];
         }
     }
     __syncthreads();
@@ -521,19 +516,6 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             F.ZcbB = zcb;
             F.ZtaA = za;
             F.ZtbB = zb;
-        }
-    } else if (kVal && (warp == 1 || warp == 2)) {
-        // g(x) = h_xx + p(x), p(x) = sum over occupied j of <xj||xj>, exact in 2^-48 units
-        // (only the modes that produce values need diagonals)
-        const int spin = warp - 1;  // 0: alpha x, 1: beta x
-        const int *os = spin ? F.occB : F.occA;
-        const int *oo = spin ? F.occA : F.occB;
-        const int ns = spin ? nb : na, no = spin ? na : nb;
-        for (int x = lane; x < N; x += 32) {
-            int64_t g = p.sys.hdx[x];
-            for (int k = 0; k < ns; ++k) g += WSx[x * N + os[k]];
-            for (int k = 0; k < no; ++k) g += Jx[x * N + oo[k]];
-            (spin ? F.gB : F.gA)[x] = g;
         }
     }
     __syncthreads();
@@ -1017,6 +999,42 @@ __global__ void ref_d0_kernel(const double *__restrict__ hii, uint64_t n, double
     uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     d0[i] = __double2ll_rn((e0 - hii[i]) * kDenScale);
+}
+
+// g(x) = h_xx + p(x) of every reference determinant, p(x) = sum over its
+// occupied spin-orbitals j of <xj||xj> (the appendix on fast diagonals), exact
+// in 2^-48 Ha: alpha x takes same-spin pair energies with the alpha electrons
+// and Coulomb energies with the beta ones, and conversely.  One CTA of kMaxOrb
+// threads per determinant; computed once per reference, read by every pass.
+__global__ void ref_g_kernel(const SysDev sys, const uint64_t *__restrict__ keys, uint64_t n,
+                             int64_t *__restrict__ g)
+{
+    const uint64_t det = blockIdx.x;
+    const int N = sys.n, x = threadIdx.x;
+    if (det >= n || x >= N) return;
+    const uint64_t A = keys[2 * det], B = keys[2 * det + 1];
+    int64_t ga = sys.hdx[x], gb = sys.hdx[x];
+    for (uint64_t m = A; m; m &= m - 1) {
+        const int k = __ffsll((long long)m) - 1;
+        ga += sys.WSx[x * N + k];
+        gb += sys.Jx[x * N + k];
+    }
+    for (uint64_t m = B; m; m &= m - 1) {
+        const int k = __ffsll((long long)m) - 1;
+        ga += sys.Jx[x * N + k];
+        gb += sys.WSx[x * N + k];
+    }
+    g[det * 2 * N + x] = ga;
+    g[det * 2 * N + N + x] = gb;
+}
+
+cudaError_t launch_ref_g(const SysDev &sys, const uint64_t *keys, uint64_t n, int64_t *g, cudaStream_t s)
+{
+    for (uint64_t o = 0; o < n; o += (1ull << 30)) {
+        const uint64_t m = n - o < (1ull << 30) ? n - o : (1ull << 30);
+        ref_g_kernel<<<(unsigned)m, kMaxOrb, 0, s>>>(sys, keys + 2 * o, m, g + o * 2 * sys.n);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s)

@@ -34,6 +34,7 @@ struct RefRes {
     int na = 0, nb = 0;
     double e0 = 0.0;
     DevBuf keys, coef, hii, d0;
+    DevBuf g;      // per determinant: (h_xx + p(x)) * 2^48 for the n alpha then the n beta spin-orbitals
     int busy = 0;  // requests of the serving engine that use it
 };
 
