@@ -837,17 +837,6 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 const uint64_t zcb12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
                 const uint64_t zt12 =
                     spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
-                int64_t base = 0;
-                if constexpr (kVal) {
-                    // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
-                    // v(x) = g(x) - W(r1,x) - W(r2,x)
-                    for (int j = lane; j < nv; j += 32) {
-                        int x = vir[j];
-                        vec[j] = g[x] - WSx[r1 * N + x] - WSx[r2 * N + x];
-                    }
-                    __syncwarp();
-                    base = d0 + g[r1] + g[r2] - WSx[r1 * N + r2];
-                }
                 // items: every virtual pair, or (narrow alpha-alpha) the pairs of the
                 // buckets (q ^ top bits of zc12), q over the pass's classes
                 const bool nar = spin == 0 && narrow;
@@ -876,6 +865,18 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     }
                     nitems = (int)__shfl_sync(0xffffffffu, incl, 31);
                     __syncwarp();
+                }
+                if (nitems == 0) continue;  // uniform across the warp
+                int64_t base = 0;
+                if constexpr (kVal) {
+                    // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
+                    // v(x) = g(x) - W(r1,x) - W(r2,x)
+                    for (int j = lane; j < nv; j += 32) {
+                        int x = vir[j];
+                        vec[j] = g[x] - WSx[r1 * N + x] - WSx[r2 * N + x];
+                    }
+                    __syncwarp();
+                    base = d0 + g[r1] + g[r2] - WSx[r1 * N + r2];
                 }
                 // the same emission over items mapped to virtual pairs by `pair_at`
                 // (instantiated separately for the direct and the bucketed case)
