@@ -52,7 +52,8 @@ uint64_t records_budget(pt2_ctx *c, int passes = 1)
     const uint64_t avail = c->budget > fixed + reserve ? c->budget - fixed - reserve : 0;
     // per record: 32 bytes plus tile bookkeeping (about 60 bytes per tile of ~500 records)
     uint64_t rec = (uint64_t)((double)avail / (sizeof(Rec32) + 0.15));
-    return std::min<uint64_t>(rec, (uint64_t)passes * (kMaxPassBytes / sizeof(Rec32)));
+    return std::min<uint64_t>(std::min<uint64_t>(rec, (uint64_t)passes * (kMaxPassBytes / sizeof(Rec32))),
+                              kMaxStepRecords);
 }
 
 int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)

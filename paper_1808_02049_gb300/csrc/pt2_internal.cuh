@@ -19,8 +19,8 @@ constexpr int kSortCap = 1024;               // records one in-shared-memory sor
 constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)
 constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (4 B each) resident in L2
 constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
-// a step holds at most two full passes (batches, serving); its record slots are 32-bit
-static_assert(2 * (kMaxPassBytes / 32) < (1ull << 32), "record slots of a step must fit 32-bit tile cursors");
+constexpr uint64_t kMaxStepRecords = (1ull << 32) - 1;  // record slots of a step are 32-bit
+static_assert(kMaxPassBytes / 32 <= kMaxStepRecords, "record slots of a pass must fit 32-bit tile cursors");
 constexpr int kBigThreads = 256;
 constexpr int kBigChunk = 768;              // records of an oversize tile sorted per chunk
 constexpr int kBigCap = 640;                // partial records finished per sort (oversize path)
