@@ -313,6 +313,25 @@ __device__ void block_scan_excl_u32(uint32_t *a, int n, uint32_t *warp_tot)
 
 // ======================================================= generation kernel
 
+// Alpha-alpha doubles are found through a table of the determinant's virtual
+// alpha pairs bucketed by the top kVbkBits bits of the pair's class hash.  The
+// class of a double is (hash of the occupied part) xor (hash of the virtual
+// pair), so the classes of a pass, as groups of 2^(kClassBits - kVbkBits)
+// classes, split into at most 2 kVbkBits aligned blocks; xor with the
+// occupied part's top bits maps each block onto one contiguous range of
+// buckets, and only those pairs are visited (then checked class by class).
+constexpr int kVbkBits = 10;
+constexpr int kVbkBitsMax = kVbkBits;
+constexpr int kVbkBuckets = 1 << kVbkBits;
+constexpr int kMaxVirPairs = kMaxOrb * (kMaxOrb - 1) / 2;
+static_assert(kVbkBuckets == 4 * kGenThreads, "the bucket scan takes four buckets per thread");
+static_assert(2 * kVbkBits <= 32, "one lane per block of buckets");
+__device__ __forceinline__ uint32_t vb_bucket(uint64_t z) { return (uint32_t)(z >> (64 - kVbkBits)); }
+
+// Shared memory of the bucket table (in the histogram area, unused by the
+// emitting modes): counts then cursors, starts, pair list, per-warp lookups.
+constexpr size_t kVbkBytes = kVbkBuckets * 4 + (kVbkBuckets + 1) * 2 + kMaxVirPairs * 2 + (kGenThreads / 32) * 64 * 2 + 16;
+
 struct GenFixed {
     uint64_t zc[kMaxOrb], zcb[kMaxOrb], zta[kMaxOrb], ztb[kMaxOrb];
     int64_t gA[kMaxOrb], gB[kMaxOrb];  // (h_xx + p(x)) * 2^48 for alpha / beta spin-orbital x
@@ -322,24 +341,11 @@ struct GenFixed {
     int64_t d0;
     int n_sa_pass, a_in_pass, n_sb_pass, b_in_pass;
     uint32_t wsum[kGenThreads / 32];
+    // the pass's alpha classes as aligned blocks of bucket groups (see above)
+    uint16_t blk_g[2 * kVbkBitsMax];
+    uint8_t blk_k[2 * kVbkBitsMax];
+    int n_blk;
 };
-
-// Narrow passes (at most kNarrowClasses alpha classes) find their alpha-alpha
-// doubles through a table of the determinant's virtual alpha pairs bucketed by
-// the top kVbkBits bits of the pair's class hash: the class of the double is
-// (hash of the occupied part) xor (hash of the virtual pair), so for each
-// occupied pair only the buckets that can land in the pass are visited.
-constexpr int kVbkBits = 10;
-constexpr int kVbkBuckets = 1 << kVbkBits;
-constexpr int kNarrowClasses = 120;  // at most 32 buckets per occupied pair
-constexpr int kMaxVirPairs = kMaxOrb * (kMaxOrb - 1) / 2;
-static_assert(kVbkBuckets == 4 * kGenThreads, "the bucket scan takes four buckets per thread");
-static_assert((kNarrowClasses + 3) / 4 + 1 <= 32, "a narrow pass needs at most one bucket per lane");
-__device__ __forceinline__ uint32_t vb_bucket(uint64_t z) { return (uint32_t)(z >> (64 - kVbkBits)); }
-
-// Shared memory of the bucket table (in the histogram area, unused by the
-// emitting modes): counts then cursors, starts, pair list, per-warp lookups.
-constexpr size_t kVbkBytes = kVbkBuckets * 4 + (kVbkBuckets + 1) * 2 + kMaxVirPairs * 2 + (kGenThreads / 32) * 64 * 2 + 16;
 
 // beta class of a beta-string hash (splits the heavy alpha classes)
 __device__ __forceinline__ uint32_t bclass_of(uint64_t zcb) { return (uint32_t)(zcb >> (64 - kClassBits)); }
@@ -679,13 +685,28 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         const int n_sb = bfull ? p.n_sb : F.n_sb_pass;
         auto sb_at = [&](int k) { return bfull ? k : (int)sb_pass[k]; };
 
-        // bucket table of the virtual alpha pairs (narrow passes only)
-        const bool narrow = class_hi - class_lo <= (uint32_t)kNarrowClasses;
+        // bucket table of the virtual alpha pairs, and the pass's classes as
+        // aligned blocks of bucket groups
         uint32_t *vb_cnt = reinterpret_cast<uint32_t *>(smem + p.smem_hist);
         uint16_t *vb_off = reinterpret_cast<uint16_t *>(vb_cnt + kVbkBuckets);
         uint16_t *vb_list = vb_off + kVbkBuckets + 1;
         uint16_t *vb_warp = vb_list + kMaxVirPairs;
-        if (narrow && b_in) {  // uniform across the CTA
+        if (b_in) {  // uniform across the CTA
+            if (tid == 0) {
+                constexpr int gs = kClassBits - kVbkBits;
+                uint32_t g = class_lo >> gs;
+                const uint32_t g1 = ((class_hi - 1) >> gs) + 1;
+                int nb = 0;
+                while (g < g1) {
+                    int k = kVbkBits;
+                    while (k > 0 && ((g & ((1u << k) - 1u)) != 0 || g + (1u << k) > g1)) --k;
+                    F.blk_g[nb] = (uint16_t)g;
+                    F.blk_k[nb] = (uint8_t)k;
+                    ++nb;
+                    g += 1u << k;
+                }
+                F.n_blk = nb;
+            }
             for (int b = tid; b < kVbkBuckets; b += kGenThreads) vb_cnt[b] = 0;
             __syncthreads();
             for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
@@ -837,21 +858,20 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 const uint64_t zcb12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
                 const uint64_t zt12 =
                     spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
-                // items: every virtual pair, or (narrow alpha-alpha) the pairs of the
-                // buckets (q ^ top bits of zc12), q over the pass's classes
-                const bool nar = spin == 0 && narrow;
+                // items: every virtual beta pair, or the alpha pairs of the bucket
+                // ranges the pass's blocks map to (block xor top bits of zc12)
+                const bool nar = spin == 0;
                 int nitems = npv, nq = 0;
-                uint16_t *ws = vb_warp + warp * 64;  // [0, 32): bucket starts, [32, 64): item offsets
+                uint16_t *ws = vb_warp + warp * 64;  // [0, 32): slice starts, [32, 64): item offsets
                 if (nar) {
                     const uint32_t u = vb_bucket(zc12);
-                    const uint32_t q0 = class_lo >> (kClassBits - kVbkBits);
-                    const uint32_t q1 = (class_hi - 1) >> (kClassBits - kVbkBits);
-                    nq = (int)(q1 - q0 + 1);
+                    nq = F.n_blk;
                     uint32_t start = 0, sz = 0;
                     if (lane < nq) {
-                        const uint32_t b = (q0 + (uint32_t)lane) ^ u;
+                        const uint32_t k = F.blk_k[lane];
+                        const uint32_t b = (F.blk_g[lane] ^ u) & ~((1u << k) - 1u);
                         start = vb_off[b];
-                        sz = (uint32_t)vb_off[b + 1] - start;
+                        sz = (uint32_t)vb_off[b + (1u << k)] - start;
                     }
                     uint32_t incl = sz;
 #pragma unroll
@@ -923,9 +943,13 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 };
                 if (nar)
                     emit_pairs(nitems, [&](int i) -> int {
-                        int k = 0;
-                        while (k + 1 < nq && (int)ws[32 + k + 1] <= i) ++k;
-                        return vb_list[ws[k] + (i - (int)ws[32 + k])];
+                        int lo = 0, hi = nq;  // last slice whose offset is at most i
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if ((int)ws[32 + mid] <= i) lo = mid;
+                            else hi = mid;
+                        }
+                        return vb_list[ws[lo] + (i - (int)ws[32 + lo])];
                     });
                 else
                     emit_pairs(npv, [](int i) -> int { return i; });
