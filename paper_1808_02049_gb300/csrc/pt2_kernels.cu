@@ -442,13 +442,11 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     GenFixed &F = *reinterpret_cast<GenFixed *>(smem);
     int64_t *sa_delta = reinterpret_cast<int64_t *>(smem + p.smem_sa);
     uint64_t *sa_zt = reinterpret_cast<uint64_t *>(sa_delta + p.n_sa);
-    double *sa_val = reinterpret_cast<double *>(sa_zt + p.n_sa);
-    uint32_t *sa_info = reinterpret_cast<uint32_t *>(sa_val + p.n_sa);
+    uint32_t *sa_info = reinterpret_cast<uint32_t *>(sa_zt + p.n_sa);
     uint16_t *sa_pass = reinterpret_cast<uint16_t *>(sa_info + p.n_sa);
     int64_t *sb_delta = reinterpret_cast<int64_t *>(smem + p.smem_sb);
     uint64_t *sb_zt = reinterpret_cast<uint64_t *>(sb_delta + p.n_sb);
-    double *sb_val = reinterpret_cast<double *>(sb_zt + p.n_sb);
-    uint32_t *sb_info = reinterpret_cast<uint32_t *>(sb_val + p.n_sb);
+    uint32_t *sb_info = reinterpret_cast<uint32_t *>(sb_zt + p.n_sb);
     uint16_t *sb_pass = reinterpret_cast<uint16_t *>(sb_info + p.n_sb);
     uint16_t *pairs = reinterpret_cast<uint16_t *>(smem + p.smem_pairs);
     int64_t *vec_all = reinterpret_cast<int64_t *>(smem + p.smem_vec);
@@ -748,33 +746,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             __syncthreads();
         }
 
-        // single-excitation elements h_ar + sum_j <aj||rj> of the singles this
-        // pass emits: a warp per single, lanes over the occupied spin-orbitals
-        // j (same spin: Coulomb minus exchange; other spin: Coulomb)
-        if constexpr (kVal) {
-            const int nsa = b_in ? n_sa_pass : 0;
-            const int nsb = a_in ? n_sb : 0;
-            for (int k = warp; k < nsa + nsb; k += nw) {
-                const bool alpha = k < nsa;
-                const int si = alpha ? (int)sa_pass[k] : sb_at(k - nsa);
-                const uint32_t info = alpha ? sa_info[si] : sb_info[si];
-                const int r = info & 0xFF, a = (info >> 8) & 0xFF;
-                const int *same = alpha ? F.occA : F.occB;
-                const int *other = alpha ? F.occB : F.occA;
-                const int ns = alpha ? na : nb, no = alpha ? nb : na;
-                double v = 0.0;
-                for (int q = lane; q < ns + no; q += 32) {
-                    const int j = q < ns ? same[q] : other[q - ns];
-                    const double coul = __ldg(eri + (((size_t)a * N + r) * N + j) * N + j);
-                    v += q < ns ? coul - __ldg(eri + (((size_t)a * N + j) * N + j) * N + r) : coul;
-                }
-#pragma unroll
-                for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if (lane == 0) (alpha ? sa_val : sb_val)[si] = ht[a * N + r] + v;
-            }
-            __syncthreads();
-        }
-        // ---- alpha singles (few per determinant); beta string B
+        // ---- alpha singles (few per determinant: O(n) element each); beta string B
         if (b_in)
         for (int k0 = tid; k0 < n_sa_pass; k0 += kGenThreads * kGenBatch)
             emit_batch<MODE>(
@@ -787,9 +759,18 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     const int s = sa_pass[k];
                     const uint32_t info = sa_info[s];
                     const int r = info & 0xFF, a = (info >> 8) & 0xFF;
+                    double v = ht[a * N + r];
+                    for (int q = 0; q < na; ++q) {
+                        int j = F.occA[q];
+                        v += eri[(((size_t)a * N + r) * N + j) * N + j] - eri[(((size_t)a * N + j) * N + j) * N + r];
+                    }
+                    for (int q = 0; q < nb; ++q) {
+                        int j = F.occB[q];
+                        v += eri[(((size_t)a * N + r) * N + j) * N + j];
+                    }
                     ka = A ^ (1ull << r) ^ (1ull << a);
                     kb = B;
-                    num = flip_sign(c * sa_val[s], info >> 16);
+                    num = flip_sign(c * v, info >> 16);
                     den = d0 - sa_delta[s];
                 });
         // ---- beta singles
@@ -805,9 +786,19 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                         const int s = sb_at(k);
                         const uint32_t info = sb_info[s];
                         const int r = info & 0xFF, a = (info >> 8) & 0xFF;
+                        double v = ht[a * N + r];
+                        for (int q = 0; q < nb; ++q) {
+                            int j = F.occB[q];
+                            v += eri[(((size_t)a * N + r) * N + j) * N + j] -
+                                 eri[(((size_t)a * N + j) * N + j) * N + r];
+                        }
+                        for (int q = 0; q < na; ++q) {
+                            int j = F.occA[q];
+                            v += eri[(((size_t)a * N + r) * N + j) * N + j];
+                        }
                         ka = A;
                         kb = B ^ (1ull << r) ^ (1ull << a);
-                        num = flip_sign(c * sb_val[s], info >> 16);
+                        num = flip_sign(c * v, info >> 16);
                         den = d0 - sb_delta[s];
                     });
         // ---- alpha-beta doubles: one alpha single per warp, beta singles over lanes
@@ -2247,9 +2238,9 @@ void gen_layout(GenParams &p, GenMode mode)
     auto al = [](size_t x) { return (x + 127) & ~(size_t)127; };
     size_t off = al(sizeof(GenFixed));
     p.smem_sa = (int)off;
-    off = al(off + (size_t)p.n_sa * (8 + 8 + 8 + 4 + 2));
+    off = al(off + (size_t)p.n_sa * (8 + 8 + 4 + 2));
     p.smem_sb = (int)off;
-    off = al(off + (size_t)p.n_sb * (8 + 8 + 8 + 4 + 2));
+    off = al(off + (size_t)p.n_sb * (8 + 8 + 4 + 2));
     p.smem_pairs = (int)off;
     off = al(off + (size_t)(kMaxOrb * (kMaxOrb - 1) / 2) * 2);
     p.smem_vec = (int)off;
