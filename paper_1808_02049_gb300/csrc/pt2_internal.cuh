@@ -17,8 +17,15 @@ constexpr int kTileThreads = 256;            // tile sort-reduce CTA (1024 / kTi
 constexpr int kTileCap = 1024;                // records a tile CTA sorts in shared memory
 constexpr int kSortCap = 1024;               // records one in-shared-memory sort handles
 constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)
-constexpr uint64_t kMaxTilesPerPass = 3200000;  // keeps the tile cursors (4 B each) resident in L2
-constexpr uint64_t kMaxPassBytes = 48ull << 30;  // default bound on one pass's term records
+constexpr uint64_t kMaxTilesPerPass = 6400000;  // keeps the tile cursors (4 B each) resident in L2
+constexpr uint64_t kMaxPassBytes = 96ull << 30;  // bound on one pass's term records
+// Emission scatters records over the tiles of a pass; up to about 1.5e9
+// records (1.8M tiles) per pass the partly written tile lines stay in L2.  A
+// pass grows beyond that only when its determinants would otherwise emit
+// fewer than kTermsPerDetPass terms each, where the per-determinant set-up
+// of every pass costs more than the scatter.
+constexpr uint64_t kLocalPassRecords = (48ull << 30) / 32;
+constexpr uint64_t kTermsPerDetPass = 10000;
 constexpr uint64_t kMaxStepRecords = (1ull << 32) - 1;  // record slots of a step are 32-bit
 static_assert(kMaxPassBytes / 32 <= kMaxStepRecords, "record slots of a pass must fit 32-bit tile cursors");
 constexpr int kBigThreads = 256;
