@@ -104,7 +104,8 @@ typedef struct {
                                  (Algorithm 2). */
     uint64_t constraint_rem;
     uint64_t pass_budget_bytes; /* device bytes for one pass of generated
-                                   terms (0 = derived from the context budget);
+                                   terms (0 = chosen from the context budget
+                                   and the reference size, at most 96 GB);
                                    smaller values mean more passes */
     uint32_t tile_target;       /* mean terms per hash tile, at most 1024
                                    (0 = default 832, or the tuned value) */
