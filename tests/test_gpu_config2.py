@@ -51,7 +51,7 @@ def test_full_size_with_heavy_alpha_class(cfg2):
     assert a["n_terms"] == T * N_DET == 481_824_000_000
     assert a["n_unique"] == a["n_in_ref"] + a["n_external"]
     assert a["n_in_ref"] <= N_DET
-    assert a["n_passes"] > a["n_terms"] // (48 << 30) * 32
+    assert a["n_passes"] >= a["n_terms"] * 32 // (96 << 30)  # passes of at most 96 GB
     assert math.isfinite(a["e2"]) and a["e2"] < 0
     # a smaller pass budget splits the classes differently: same energy and set
     b = c.run(rid, pass_budget_bytes=32 << 30)
