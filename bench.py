@@ -236,9 +236,9 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    "kernels_sha256": "d0ad7b1dbb34cfe0b2b35f621f6f5e9ed0515fe7b01d37b2043146fd39f77fff",
-    "tile_kernel": (4.133496e9 + 5.236224e6) / 129_750_000,      # 31.90 B per term
-    "gen_kernel<Emit>": (0.164822272e9 + 4.105734e9) / 129_750_000,  # 32.91 B per term
+    "kernels_sha256": "51f01d5c8ae9c47089a4e0f73a961972a81d2ee14c5e6554a733c47fd6e006c2",
+    "tile_kernel": (4.134239e9 + 5.2864e6) / 129_750_000,        # 31.90 B per term
+    "gen_kernel<Emit>": (0.15681152e9 + 4.106085e9) / 129_750_000,  # 32.85 B per term
 }
 
 
