@@ -1,20 +1,26 @@
 // sm_103a kernels of the sort-based Epstein-Nesbet PT2 path.
 //
 // Path (Algorithm 2 with hash-defined constraint classes):
-//   gen<ClassCount>  work list: terms per alpha-hash class (sizes the passes)
+//   at load          H_ii, E0 - H_ii and the orbital energies g(x) of every
+//                    reference determinant
+//   gen<ClassCount>  work list: terms per alpha-hash class (sizes the passes);
+//   gen<BetaCount>   for an alpha class too heavy for one pass, its terms per
+//                    beta-hash class (splits it into several passes)
 //   per pass:
 //     gen<TileCount>  terms per hash tile of the pass
-//     scan            tile offsets
+//     scan            tile offsets (and the 32-bit slot cursors)
 //     gen<Emit>       every single/double of every reference determinant whose
-//                     alpha word falls in the pass: key, H_ai c_i (Slater-Condon,
+//                     key falls in the pass: key, H_ai c_i (Slater-Condon,
 //                     fermionic phase) and E0 - H_aa (exact incremental diagonal),
 //                     written into its tile
 //     ref partition   reference keys of the pass, grouped by tile and sorted
-//     tile            per tile, in shared memory: counting sort by key hash then
-//                     insertion sort by the 128-bit key (equal keys adjacent),
-//                     reduce_by_key, explicit filter of reference keys by binary
-//                     search, num^2 / (E0 - H_aa) accumulated exactly
-//     big tile        tiles larger than shared memory, grouped in chunks
+//     tile            per tile, in shared memory: stable LSD radix sort of the
+//                     keys' 24-bit hashes (equal keys adjacent, collisions
+//                     checked on the full key), reduce by key, explicit filter
+//                     of reference keys by binary search, num^2 / (E0 - H_aa)
+//                     accumulated exactly
+//     big tile        tiles larger than shared memory, in chunks reduced to
+//                     exact partials
 //
 // FP64 is the scarce unit on this GPU, so every quantity with a natural exact
 // integer form is kept as one: the diagonal difference (int64, 2^-48 Ha), the
