@@ -47,7 +47,7 @@ def dist_env():
 def workload(n_det=None):
     from paper_1808_02049_gb300 import inputs
 
-    return inputs.make_config(1, n_det=n_det or None)
+    return inputs.make_workload("large", n_det=n_det or None)
 
 
 def workload_name(n_det):
@@ -80,7 +80,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"pt2_bench_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         try:

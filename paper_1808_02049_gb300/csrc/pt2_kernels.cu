@@ -2080,7 +2080,7 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
             const unsigned long long off = p.tile_off[t];
             const unsigned long long cnt = p.tile_off[t + 1] - off;
             bool bad = false;
-            // round 1: Rec32 chunks -> reduced Rec48 in bufA
+            // chunks of records -> exact partials (Rec48) in bufA
             unsigned long long u = 0;
             for (unsigned long long cs = 0; !bad && cs < cnt; cs += kBigChunk) {
                 const int m = (int)min((unsigned long long)kBigChunk, cnt - cs);

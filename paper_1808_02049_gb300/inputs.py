@@ -42,18 +42,18 @@ __all__ = [
     "Reference",
     "make_integrals",
     "make_reference",
-    "make_config",
+    "make_workload",
     "batch_instance_params",
-    "CONFIGS",
-    "config_seed",
+    "WORKLOADS",
+    "workload_seed",
 ]
 
 SEED_BASE = 20181806
 
 
-def config_seed(config: int, instance: int = 0) -> int:
-    """Seed of a named workload: base + 1000 * config + instance."""
-    return SEED_BASE + 1000 * config + instance
+def workload_seed(index: int, instance: int = 0) -> int:
+    """Seed of a workload with seed index `index`: base + 1000 * index + instance."""
+    return SEED_BASE + 1000 * index + instance
 
 
 @dataclasses.dataclass
@@ -197,39 +197,44 @@ def _count_within(n_orb: int, n: int, max_level: int) -> int:
     return tot
 
 
-# The named workloads: (electrons per spin, spatial orbitals, N_det, max level).
-CONFIGS = {
-    0: dict(n_elec_per_spin=4, n_orb=16, n_det=1000, max_level=3),
-    1: dict(n_elec_per_spin=10, n_orb=40, n_det=100_000, max_level=4),
-    2: dict(n_elec_per_spin=12, n_orb=60, n_det=1_000_000, max_level=4),
+# The named single-solve workloads: electrons per spin, spatial orbitals,
+# N_det, maximum excitation level, and the index their seeds derive from.
+WORKLOADS = {
+    # 8 electrons in 16 orbitals, 1,000 determinants: about 3.2e6 terms
+    "small": dict(n_elec_per_spin=4, n_orb=16, n_det=1000, max_level=3, seed_index=0),
+    # 20 electrons in 40 orbitals, 100,000 determinants: 1.2975e10 terms
+    "large": dict(n_elec_per_spin=10, n_orb=40, n_det=100_000, max_level=4, seed_index=1),
+    # 24 electrons in 60 orbitals, 1,000,000 determinants: 4.8e11 terms
+    "million": dict(n_elec_per_spin=12, n_orb=60, n_det=1_000_000, max_level=4, seed_index=2),
 }
+BATCH_SEED_INDEX = 3  # the 64-instance batched workload
 
 
-def make_config(config: int, n_det: int | None = None):
-    """(System, Reference) of a named single-solve workload (0, 1 or 2)."""
-    c = CONFIGS[config]
-    seed = config_seed(config)
+def make_workload(name: str, n_det: int | None = None):
+    """(System, Reference) of a named single-solve workload ("small", "large" or "million")."""
+    c = WORKLOADS[name]
+    seed = workload_seed(c["seed_index"])
     sys_ = make_integrals(c["n_orb"], seed)
     nd = c["n_det"] if n_det is None else n_det
     ref = make_reference(c["n_orb"], c["n_elec_per_spin"], nd, c["max_level"], seed + 1)
     return sys_, ref
 
 
-def batch_instance_params(k: int, base_config: int = 3):
+def batch_instance_params(k: int):
     """Size of instance k of the batched workload (64 uneven instances).
 
     n_orb ~ U{16..40}, electrons per spin ~ U{4..10} (kept below n_orb),
     N_det log-uniform in [1e3, 5e4].  The maximum excitation level is 4 when
     N_det exceeds half the number of determinants within triples of HF, else 3.
     """
-    rng = np.random.Generator(np.random.PCG64(config_seed(base_config, k)))
+    rng = np.random.Generator(np.random.PCG64(workload_seed(BATCH_SEED_INDEX, k)))
     n_orb = int(rng.integers(16, 41))
     n = int(rng.integers(4, 11))
     n = min(n, n_orb - 1)
     n_det = int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4)))))
     max_level = 4 if n_det > _count_within(n_orb, n, 3) // 2 else 3
     return dict(n_orb=n_orb, n_elec_per_spin=n, n_det=n_det, max_level=max_level,
-                seed=config_seed(base_config, k) + 7)
+                seed=workload_seed(BATCH_SEED_INDEX, k) + 7)
 
 
 def make_instance(params: dict):

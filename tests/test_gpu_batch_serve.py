@@ -112,7 +112,7 @@ def test_served_request_timeout_and_busy_reference():
     from paper_1808_02049_gb300 import build
 
     build.build_library()
-    s, r = inputs.make_config(1, n_det=40000)  # ~5e9 terms: runs for a while
+    s, r = inputs.make_workload("large", n_det=40000)  # ~5e9 terms: runs for a while
     with pt2.Context(0) as c:
         sid = c.load_system(s.h, s.eri)
         e0 = float(c.diagonal(sid, r.keys).min() - 0.1)

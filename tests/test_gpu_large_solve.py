@@ -21,11 +21,11 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 @pytest.fixture(scope="module")
-def cfg1():
+def large():
     from paper_1808_02049_gb300 import build
 
     build.build_library()
-    s, r = inputs.make_config(1)
+    s, r = inputs.make_workload("large")
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     c = pt2.Context(0)
     sid = c.load_system(s.h, s.eri)
@@ -34,8 +34,8 @@ def cfg1():
     c.close()
 
 
-def test_full_size_properties(cfg1):
-    c, rid = cfg1["c"], cfg1["rid"]
+def test_full_size_properties(large):
+    c, rid = large["c"], large["rid"]
     a = c.run(rid)
     n, v = 10, 30
     T = 2 * n * v + 2 * math.comb(n, 2) * math.comb(v, 2) + (n * v) ** 2
@@ -55,8 +55,8 @@ def test_full_size_properties(cfg1):
 
 
 @pytest.mark.parametrize("cls", [(49999, 7), (50021, 123)])
-def test_sampled_constraint_class_matches_oracle(cfg1, cls):
-    c, s, r, e0, rid = cfg1["c"], cfg1["s"], cfg1["r"], cfg1["e0"], cfg1["rid"]
+def test_sampled_constraint_class_matches_oracle(large, cls):
+    c, s, r, e0, rid = large["c"], large["s"], large["r"], large["e0"], large["rid"]
     got = c.run(rid, constraint=cls)
     ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=cls)
     assert got["n_terms"] == ref["n_terms"]

@@ -27,11 +27,11 @@ N_ORB, N_EL = 60, 12
 
 
 @pytest.fixture(scope="module")
-def cfg2():
+def million():
     from paper_1808_02049_gb300 import build
 
     build.build_library()
-    s, r = inputs.make_config(2)
+    s, r = inputs.make_workload("million")
     assert r.n_det == N_DET
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     c = pt2.Context(0)
@@ -41,9 +41,9 @@ def cfg2():
     c.close()
 
 
-def test_full_size_with_heavy_alpha_class(cfg2):
-    c, rid = cfg2["c"], cfg2["rid"]
-    alpha = cfg2["r"].keys[0::2]
+def test_full_size_with_heavy_alpha_class(million):
+    c, rid = million["c"], million["rid"]
+    alpha = million["r"].keys[0::2]
     assert np.unique(alpha, return_counts=True)[1].max() > 200_000
     a = c.run(rid)
     n, v = N_EL, N_ORB - N_EL
@@ -61,11 +61,11 @@ def test_full_size_with_heavy_alpha_class(cfg2):
 
 
 @pytest.mark.parametrize("level", [3, 4])
-def test_one_alpha_string_matches_oracle(cfg2, level):
+def test_one_alpha_string_matches_oracle(million, level):
     # the smallest alpha string of the reference that is a triple (quadruple)
     # excitation of the Hartree-Fock one: a few thousand (hundred) reference
     # determinants lie within a double excitation of it
-    c, s, r, e0, rid = cfg2["c"], cfg2["s"], cfg2["r"], cfg2["e0"], cfg2["rid"]
+    c, s, r, e0, rid = million["c"], million["s"], million["r"], million["e0"], million["rid"]
     alpha = r.keys[0::2]
     hf = (1 << N_EL) - 1
     dist = np.array([bin(int(x) ^ hf).count("1") for x in alpha])

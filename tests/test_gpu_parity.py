@@ -37,8 +37,8 @@ def ctx():
 
 
 @pytest.fixture(scope="module")
-def cfg0(ctx):
-    s, r = inputs.make_config(0)
+def small(ctx):
+    s, r = inputs.make_workload("small")
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     sid = ctx.load_system(s.h, s.eri)
     rid = ctx.load_reference(sid, r.keys, r.coef, e0)
@@ -63,16 +63,16 @@ def sort_keys(k, *vals):
     return (k[order],) + tuple(v[order] for v in vals)
 
 
-def test_diagonal_matches_oracle(ctx, cfg0):
-    s, r = cfg0["s"], cfg0["r"]
-    got = ctx.diagonal(cfg0["sid"], r.keys)
+def test_diagonal_matches_oracle(ctx, small):
+    s, r = small["s"], small["r"]
+    got = ctx.diagonal(small["sid"], r.keys)
     np.testing.assert_allclose(got, oracle.diagonals(s.h, s.eri, r.keys), rtol=0, atol=1e-12)
 
 
 @pytest.mark.parametrize("det", [0, 1, 123, 999])
-def test_det_terms_match_oracle(ctx, cfg0, det):
-    s, r = cfg0["s"], cfg0["r"]
-    k, v, d = ctx.det_terms(cfg0["rid"], det, 4000)
+def test_det_terms_match_oracle(ctx, small, det):
+    s, r = small["s"], small["r"]
+    k, v, d = ctx.det_terms(small["rid"], det, 4000)
     ok, ov, od = oracle.det_terms(s.h, s.eri, r.keys[2 * det], r.keys[2 * det + 1], r.coef[det])
     assert k.shape == ok.shape == (3192, 2)
     k, v, d = sort_keys(k, v, d)
@@ -82,14 +82,14 @@ def test_det_terms_match_oracle(ctx, cfg0, det):
     np.testing.assert_allclose(d, od, rtol=0, atol=1e-11)
 
 
-def test_e2_config0_matches_oracle(ctx, cfg0):
-    got = ctx.run(cfg0["rid"])
-    assert_same_result(got, cfg0["ref"])
+def test_e2_small_workload_matches_oracle(ctx, small):
+    got = ctx.run(small["rid"])
+    assert_same_result(got, small["ref"])
 
 
-def test_external_set_dump_matches_oracle(ctx, cfg0):
-    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
-    k, num, haa = ctx.dump_external(cfg0["rid"], cfg0["ref"]["n_external"] + 10)
+def test_external_set_dump_matches_oracle(ctx, small):
+    s, r, e0 = small["s"], small["r"], small["e0"]
+    k, num, haa = ctx.dump_external(small["rid"], small["ref"]["n_external"] + 10)
     ok, onum, ohaa, _ = oracle.dump_external(s.h, s.eri, r.keys, r.coef, e0)
     k, num, haa = sort_keys(k, num, haa)
     assert np.array_equal(k, ok)
@@ -97,17 +97,17 @@ def test_external_set_dump_matches_oracle(ctx, cfg0):
     np.testing.assert_allclose(haa, ohaa, rtol=0, atol=1e-11)
 
 
-def test_run_is_bit_identical_across_runs(ctx, cfg0):
-    a = ctx.run(cfg0["rid"])
-    b = ctx.run(cfg0["rid"])
+def test_run_is_bit_identical_across_runs(ctx, small):
+    a = ctx.run(small["rid"])
+    b = ctx.run(small["rid"])
     assert a["e2"] == b["e2"]
     assert a == {**b, "seconds": a["seconds"]}
 
 
 @pytest.mark.parametrize("tile_target", [16, 256, 1024])
-def test_tile_sizes_and_oversize_path(ctx, cfg0, tile_target):
-    got = ctx.run(cfg0["rid"], tile_target=tile_target)
-    assert_same_result(got, cfg0["ref"])
+def test_tile_sizes_and_oversize_path(ctx, small, tile_target):
+    got = ctx.run(small["rid"], tile_target=tile_target)
+    assert_same_result(got, small["ref"])
     if tile_target == 1024:
         assert got["n_oversize"] > 0  # tiles above shared-memory capacity took the chunked path
 
@@ -117,7 +117,7 @@ def test_oversize_tiles_with_mostly_distinct_keys(ctx):
     # terms is a distinct key, so at the largest tile target about half of the
     # tiles exceed shared memory with more distinct keys than one chunk holds;
     # their partials are split by hash before the final reduction.
-    s, r = inputs.make_config(1, n_det=3)
+    s, r = inputs.make_workload("large", n_det=3)
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     sid = ctx.load_system(s.h, s.eri)
     rid = ctx.load_reference(sid, r.keys, r.coef, e0)
@@ -133,60 +133,60 @@ def test_oversize_tiles_with_mostly_distinct_keys(ctx):
         ctx.unload(sid)
 
 
-def test_e2_is_bit_identical_for_any_tiling_and_pass_plan(ctx, cfg0):
+def test_e2_is_bit_identical_for_any_tiling_and_pass_plan(ctx, small):
     # numerators and the energy are summed exactly in fixed point, so the
     # result cannot depend on how terms are split into passes and tiles
-    base = ctx.run(cfg0["rid"])
+    base = ctx.run(small["rid"])
     for kw in [dict(tile_target=16), dict(tile_target=1024), dict(pass_budget_bytes=12 << 20),
                dict(pass_budget_bytes=40 << 20, tile_target=100)]:
-        got = ctx.run(cfg0["rid"], **kw)
+        got = ctx.run(small["rid"], **kw)
         assert got["e2"] == base["e2"], kw
         assert (got["digest_sum"], got["digest_xor"], got["n_external"]) == \
             (base["digest_sum"], base["digest_xor"], base["n_external"])
 
 
-def test_heavy_alpha_class_is_split_by_beta_class(ctx, cfg0):
+def test_heavy_alpha_class_is_split_by_beta_class(ctx, small):
     # 288 of the 1000 determinants share the Hartree-Fock alpha string, so its
     # alpha class holds at least 288 * (4*12 + 6*66) = 127,872 terms; a 1 MB
     # pass budget holds about 32,000, so that class must be split into passes
     # by beta class (the run fails otherwise) and give the same result
-    alpha = cfg0["r"].keys[0::2]
+    alpha = small["r"].keys[0::2]
     assert np.unique(alpha, return_counts=True)[1].max() == 288
-    base = ctx.run(cfg0["rid"])
-    got = ctx.run(cfg0["rid"], pass_budget_bytes=1 << 20)
+    base = ctx.run(small["rid"])
+    got = ctx.run(small["rid"], pass_budget_bytes=1 << 20)
     assert got["n_passes"] > 90
-    assert_same_result(got, cfg0["ref"])
+    assert_same_result(got, small["ref"])
     assert got["e2"] == base["e2"]
     assert (got["digest_sum"], got["digest_xor"]) == (base["digest_sum"], base["digest_xor"])
 
 
-def test_many_passes(ctx, cfg0):
+def test_many_passes(ctx, small):
     # a 12 MB pass budget forces several memory-bounded passes
-    got = ctx.run(cfg0["rid"], pass_budget_bytes=12 << 20)
+    got = ctx.run(small["rid"], pass_budget_bytes=12 << 20)
     assert got["n_passes"] >= 5
-    assert_same_result(got, cfg0["ref"])
+    assert_same_result(got, small["ref"])
 
 
-def test_constraint_classes(ctx, cfg0):
-    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
+def test_constraint_classes(ctx, small):
+    s, r, e0 = small["s"], small["r"], small["e0"]
     m = 5
     tot = 0.0
     for k in range(m):
-        got = ctx.run(cfg0["rid"], constraint=(m, k))
+        got = ctx.run(small["rid"], constraint=(m, k))
         ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=(m, k))
         assert_same_result(got, ref)
         tot += got["e2"]
-    assert e2_close(tot, cfg0["ref"]["e2"])
+    assert e2_close(tot, small["ref"]["e2"])
 
 
-def test_permutation_invariance_is_bit_exact(ctx, cfg0):
-    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
+def test_permutation_invariance_is_bit_exact(ctx, small):
+    s, r, e0 = small["s"], small["r"], small["e0"]
     perm = np.random.default_rng(11).permutation(r.n_det)
     pk = np.empty_like(r.keys)
     pk[0::2], pk[1::2] = r.keys[0::2][perm], r.keys[1::2][perm]
-    rid = ctx.load_reference(cfg0["sid"], pk, r.coef[perm], e0)
+    rid = ctx.load_reference(small["sid"], pk, r.coef[perm], e0)
     try:
-        a = ctx.run(cfg0["rid"])
+        a = ctx.run(small["rid"])
         b = ctx.run(rid)
     finally:
         ctx.unload(rid)
@@ -194,10 +194,10 @@ def test_permutation_invariance_is_bit_exact(ctx, cfg0):
     assert (a["digest_sum"], a["digest_xor"]) == (b["digest_sum"], b["digest_xor"])
 
 
-def test_scaling_and_spin_swap(ctx, cfg0):
-    s, r, e0 = cfg0["s"], cfg0["r"], cfg0["e0"]
-    base = ctx.run(cfg0["rid"])["e2"]
-    rid = ctx.load_reference(cfg0["sid"], r.keys, 2.0 * r.coef, e0)
+def test_scaling_and_spin_swap(ctx, small):
+    s, r, e0 = small["s"], small["r"], small["e0"]
+    base = ctx.run(small["rid"])["e2"]
+    rid = ctx.load_reference(small["sid"], r.keys, 2.0 * r.coef, e0)
     try:
         dbl = ctx.run(rid)["e2"]
     finally:
@@ -205,7 +205,7 @@ def test_scaling_and_spin_swap(ctx, cfg0):
     assert abs(dbl - 4.0 * base) <= 1e-14 * abs(base)
     sw = r.keys.copy()
     sw[0::2], sw[1::2] = r.keys[1::2], r.keys[0::2]
-    rid = ctx.load_reference(cfg0["sid"], sw, r.coef, e0)
+    rid = ctx.load_reference(small["sid"], sw, r.coef, e0)
     try:
         swp = ctx.run(rid)["e2"]
     finally:
@@ -289,22 +289,22 @@ def test_64_orbitals_top_bit(ctx):
     assert_same_result(got, ref)
 
 
-def test_invalid_inputs_are_rejected(ctx, cfg0):
-    s, r = cfg0["s"], cfg0["r"]
+def test_invalid_inputs_are_rejected(ctx, small):
+    s, r = small["s"], small["r"]
     bad = r.keys.copy()
     bad[2], bad[3] = bad[0], bad[1]
     with pytest.raises(pt2.Pt2Error) as e:
-        ctx.load_reference(cfg0["sid"], bad, r.coef, -1.0)
+        ctx.load_reference(small["sid"], bad, r.coef, -1.0)
     assert e.value.code == pt2.PT2_ERR_INVALID
     bad = r.keys.copy()
     bad[0] = np.uint64(bad[0]) | np.uint64(1 << 40)
     with pytest.raises(pt2.Pt2Error) as e:
-        ctx.load_reference(cfg0["sid"], bad, r.coef, -1.0)
+        ctx.load_reference(small["sid"], bad, r.coef, -1.0)
     assert e.value.code == pt2.PT2_ERR_INVALID
     coef = r.coef.copy()
     coef[3] = np.nan
     with pytest.raises(pt2.Pt2Error) as e:
-        ctx.load_reference(cfg0["sid"], r.keys, coef, -1.0)
+        ctx.load_reference(small["sid"], r.keys, coef, -1.0)
     assert e.value.code == pt2.PT2_ERR_INVALID
     hb = s.h.copy()
     hb[0, 1] += 1e-6
@@ -318,10 +318,10 @@ def test_invalid_inputs_are_rejected(ctx, cfg0):
         ctx.run(987654)
     assert e.value.code == pt2.PT2_ERR_NOT_FOUND
     with pytest.raises(pt2.Pt2Error) as e:
-        ctx.run(cfg0["rid"], constraint=(3, 5))
+        ctx.run(small["rid"], constraint=(3, 5))
     assert e.value.code == pt2.PT2_ERR_INVALID
     with pytest.raises(pt2.Pt2Error) as e:
-        ctx.unload(cfg0["sid"])  # still used by a reference
+        ctx.unload(small["sid"])  # still used by a reference
     assert e.value.code == pt2.PT2_ERR_INVALID
 
 

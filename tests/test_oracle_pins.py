@@ -129,8 +129,8 @@ def T(n, v):
     return 2 * n * v + 2 * math.comb(n, 2) * math.comb(v, 2) + (n * v) ** 2
 
 
-def test_term_count_closed_form_config0():
-    s, r = inputs.make_config(0)
+def test_term_count_closed_form_small_workload():
+    s, r = inputs.make_workload("small")
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     res = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
     n, v = 4, 12
@@ -142,7 +142,7 @@ def test_term_count_closed_form_config0():
 
 
 def test_det_terms_count_and_uniqueness():
-    s, r = inputs.make_config(0)
+    s, r = inputs.make_workload("small")
     for i in (0, 17, 999):
         k, v, _ = oracle.det_terms(s.h, s.eri, r.keys[2 * i], r.keys[2 * i + 1], r.coef[i])
         assert k.shape[0] == T(4, 12)
@@ -183,7 +183,7 @@ def test_subtraction_identity_eigenvector_reference():
 
 
 def test_scaling_swap_permutation_invariants():
-    s, r = inputs.make_config(0, n_det=200)
+    s, r = inputs.make_workload("small", n_det=200)
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     base = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
     dbl = oracle.pt2(s.h, s.eri, r.keys, 2.0 * r.coef, e0)
@@ -202,7 +202,7 @@ def test_scaling_swap_permutation_invariants():
 
 
 def test_constraint_classes_partition_the_sum():
-    s, r = inputs.make_config(0, n_det=150)
+    s, r = inputs.make_workload("small", n_det=150)
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     base = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
     m = 7
@@ -225,7 +225,7 @@ def test_single_alpha_string_classes_partition_the_sum():
     # a wrongly skipped determinant would lose its terms.
     import itertools
 
-    s, r = inputs.make_config(0, n_det=60)
+    s, r = inputs.make_workload("small", n_det=60)
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
     base = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
     mod = 1 << 40
@@ -246,7 +246,7 @@ def test_single_alpha_string_classes_partition_the_sum():
 
 
 def test_oracle_rejects_invalid_reference():
-    s, r = inputs.make_config(0, n_det=10)
+    s, r = inputs.make_workload("small", n_det=10)
     bad = r.keys.copy()
     bad[2] = bad[0]
     bad[3] = bad[1]  # duplicate determinant

@@ -28,7 +28,7 @@ def test_noalloc_terms_match_allocating_entry_point():
     from paper_1808_02049_gb300 import build
 
     build.build_library()
-    s, r = inputs.make_config(0)
+    s, r = inputs.make_workload("small")
     with pt2.Context(0) as ctx:
         sid = ctx.load_system(s.h, s.eri)
         e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
