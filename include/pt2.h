@@ -115,6 +115,15 @@ typedef struct {
 #define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times); a batch created
                                  with it runs its steps one by one instead of replaying its graph */
 #define PT2_FLAG_AUTOTUNE 2u  /* pt2_batch_create: tune the tile target per size class first */
+/* Spin-flip symmetry (the subsection on Z2 spin symmetry for S_z = 0): for a reference closed under
+ * exchange of the alpha and beta strings with c(beta, alpha) = c(alpha, beta),
+ * the contributions of (alpha', beta') and (beta', alpha') to E2 are equal, so
+ * only excited determinants with alpha' >= beta' (as 64-bit words) are
+ * generated, sorted and reduced; those with alpha' > beta' count twice.  E2 is
+ * that of the full sum; n_terms, n_unique, n_in_ref, n_external, the digest,
+ * min_abs_denom and n_pos_denom then describe the kept half (alpha' >= beta').
+ * PT2_ERR_INVALID if the reference is not symmetric. */
+#define PT2_FLAG_SPIN_SYMMETRIC 4u
 
 typedef struct {
     double e2;                /* the PT2 energy, Hartree */

@@ -147,6 +147,7 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.bclass_lo = 0;
     p.bclass_hi = kNumClasses;
     p.heavy_class = 0;
+    p.sym = 0;
     p.cons_mod = 1;
     p.err = (uint32_t *)c->err_word.ptr;
     return p;
@@ -359,12 +360,25 @@ int pt2_load_reference(pt2_ctx *c, uint32_t system_id, uint64_t n_det, const uin
             return fail(c, PT2_ERR_INVALID, "determinant %llu has a different electron count", (unsigned long long)i);
     }
     if (!finite_all(coef, n_det) || !std::isfinite(e0)) return fail(c, PT2_ERR_INVALID, "non-finite coefficient or E0");
+    bool flip_symmetric = na == nb;
     {
-        std::vector<std::pair<uint64_t, uint64_t>> k(n_det);
-        for (uint64_t i = 0; i < n_det; ++i) k[i] = {keys[2 * i], keys[2 * i + 1]};
+        // sorted (alpha, beta, index): duplicates, and whether every determinant's
+        // mirror (beta, alpha) is present with the same coefficient
+        struct K {
+            uint64_t a, b, i;
+            bool operator<(const K &o) const { return a < o.a || (a == o.a && b < o.b); }
+        };
+        std::vector<K> k(n_det);
+        for (uint64_t i = 0; i < n_det; ++i) k[i] = {keys[2 * i], keys[2 * i + 1], i};
         std::sort(k.begin(), k.end());
         for (uint64_t i = 1; i < n_det; ++i)
-            if (k[i] == k[i - 1]) return fail(c, PT2_ERR_INVALID, "duplicate determinant in the reference");
+            if (k[i].a == k[i - 1].a && k[i].b == k[i - 1].b)
+                return fail(c, PT2_ERR_INVALID, "duplicate determinant in the reference");
+        for (uint64_t i = 0; flip_symmetric && i < n_det; ++i) {
+            const K m{k[i].b, k[i].a, 0};
+            auto it = std::lower_bound(k.begin(), k.end(), m);
+            flip_symmetric = it != k.end() && it->a == m.a && it->b == m.b && coef[it->i] == coef[k[i].i];
+        }
     }
     cudaSetDevice(c->device);
     auto r = std::make_unique<RefRes>();
@@ -373,6 +387,7 @@ int pt2_load_reference(pt2_ctx *c, uint32_t system_id, uint64_t n_det, const uin
     r->na = na;
     r->nb = nb;
     r->e0 = e0;
+    r->flip_symmetric = flip_symmetric;
     int rc;
     if ((rc = dev_alloc(c, r->keys, n_det * 16, "reference keys")) ||
         (rc = dev_alloc(c, r->coef, n_det * 8, "coefficients")) ||

@@ -71,6 +71,12 @@ int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)
     j.gp = gen_params(c, *j.s, *j.r);
     j.gp.cons_mod = j.o.constraint_mod > 1 ? j.o.constraint_mod : 1;
     j.gp.cons_rem = j.o.constraint_mod > 1 ? j.o.constraint_rem : 0;
+    if (j.o.flags & PT2_FLAG_SPIN_SYMMETRIC) {
+        if (!j.r->flip_symmetric)
+            return fail(c, PT2_ERR_INVALID,
+                        "spin-flip symmetry needs a reference closed under alpha <-> beta exchange with equal coefficients");
+        j.gp.sym = 1;
+    }
     return PT2_OK;
 }
 
@@ -332,6 +338,7 @@ void fill_step(pt2_ctx *c, const StepPlan &sp, StepDev &h)
         h.det_base[i] = cta;
         h.tile_base[i] = tb;
         h.e0[i] = j.r->e0;
+        h.sym[i] = j.gp.sym;
         h.expected[i] = P.records;
         h.acc[i] = j.acc;
         h.n_big[i] = 0;
@@ -358,7 +365,8 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     cudaEvent_t *E = &c->ev[2];
     if (prof) CK(cudaEventRecord(E[0], st), "event");
     CK(cudaMemsetAsync(c->tile_counts.ptr, 0, sp.n_tiles * 4, st), "memset");
-    GenBatch gb{d->params, d->det_base, n, 0, {}};
+    GenBatch gb{d->params, d->det_base, n, 0, {}, 0};
+    for (const StepItem &it : sp.items) gb.sym_any |= it.job->gp.sym != 0;
     if (n == 1) gb.one = step_item_params(c, sp, 0, 0);
     const int smem = step_smem(sp);
     CK(gen_launch(c, kModeTileCount, gb, sp.n_ctas, smem), "tile count kernel");
@@ -404,6 +412,8 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     tp.n_tiles = sp.n_tiles;
     tp.tile_base = d->tile_base;
     tp.e0 = d->e0;
+    tp.sym = d->sym;
+    tp.sym_any = gb.sym_any;
     tp.acc = d->acc;
     tp.n_big = d->n_big;
     tp.big_max = reinterpret_cast<unsigned long long *>(c->big_max.ptr);

@@ -107,6 +107,7 @@ struct GenParams {
     uint32_t class_lo, class_hi;  // alpha classes [lo, hi) belong to the pass
     uint32_t bclass_lo, bclass_hi;  // and, within them, beta classes [lo, hi) (all: 0, kNumClasses)
     uint32_t heavy_class;         // beta-count mode: the alpha class whose beta classes are counted
+    uint32_t sym;                 // spin-flip symmetric run: only terms with alpha' >= beta'
     uint64_t cons_mod, cons_rem;  // alpha % mod == rem (mod <= 1: none)
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance
@@ -134,6 +135,7 @@ struct GenBatch {
     // n_inst == 1: the instance's parameters, read from the launch arguments
     // (constant bank) instead of the device table
     GenParams one;
+    int sym_any;  // some instance is a spin-flip symmetric run: launch the variant that checks
 };
 
 // Run accumulator: every field is an exact integer reduction.
@@ -159,6 +161,7 @@ struct TileParams {
     uint64_t n_tiles;                    // over all instances
     const unsigned long long *tile_base; // n_inst + 1
     const double *e0;                    // per instance
+    const uint32_t *sym;                 // per instance: spin-flip symmetric run (keys with alpha > beta count twice)
     RunAcc *const *acc;                  // per instance
     unsigned int *n_big;                 // per instance: oversize tiles of the pass
     unsigned long long *big_max;         // largest oversize tile (diagnostic)
@@ -173,6 +176,7 @@ struct TileParams {
     // oversize path scratch: per CTA two buffers of scratch_cap Rec48
     Rec48 *scratch;
     unsigned long long scratch_cap;
+    int sym_any;  // some instance is a spin-flip symmetric run: launch the variant that checks
 };
 
 // Reference determinants of a step: global index g belongs to the instance

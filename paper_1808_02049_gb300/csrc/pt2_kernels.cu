@@ -356,6 +356,12 @@ struct GenFixed {
 // beta class of a beta-string hash (splits the heavy alpha classes)
 __device__ __forceinline__ uint32_t bclass_of(uint64_t zcb) { return (uint32_t)(zcb >> (64 - kClassBits)); }
 
+// The string W after the single excitation packed in `info` (r in bits 0-7, a in 8-15).
+__device__ __forceinline__ uint64_t single_word(uint64_t W, uint32_t info)
+{
+    return W ^ (1ull << (info & 0xFFu)) ^ (1ull << ((info >> 8) & 0xFFu));
+}
+
 
 // Counter updates on global memory.  The counters may be reached through
 // pointers read from a device table, so the global state space is named
@@ -440,8 +446,9 @@ __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, i
 }
 
 // All singles and doubles of determinant `det` of one instance (the body of
-// both generator kernels).
-template <int MODE>
+// both generator kernels).  SYM: the instance may be a spin-flip symmetric run
+// (the check costs registers, so the emission of ordinary runs leaves it out).
+template <int MODE, bool SYM>
 __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -466,6 +473,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     // class in [bclass_lo, bclass_hi); most passes take every beta class
     const bool bfull = p.bclass_lo == 0 && p.bclass_hi >= (uint32_t)kNumClasses;
     const uint32_t blo = p.bclass_lo, bhi = p.bclass_hi;
+    // spin-flip symmetric run: a term is kept only if its alpha string, as a
+    // 64-bit word, is not below its beta string (every mode applies the same rule)
+    const bool sym = SYM && p.sym != 0;
     const int N = p.sys.n;
     const int na = p.na, nb = p.nb, nva = N - na, nvb = N - nb;
     const double *__restrict__ eri = p.sys.eri;
@@ -613,11 +623,38 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
     if constexpr (MODE == kModeClassCount) {
         // work list (the paper's first pass over the wavefunction): terms per class
-        if (tid == 0 && a_in)
-            atomicAdd(&hist[class_of(F.ZcA)], (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
-        for (int k = tid; k < n_sa_pass; k += kGenThreads) {
-            int s = sa_pass[k];
-            atomicAdd(&hist[class_of(sa_zt[s])], (uint32_t)(1 + p.n_sb));
+        if (!sym) {
+            if (tid == 0 && a_in)
+                atomicAdd(&hist[class_of(F.ZcA)], (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
+            for (int k = tid; k < n_sa_pass; k += kGenThreads) {
+                int s = sa_pass[k];
+                atomicAdd(&hist[class_of(sa_zt[s])], (uint32_t)(1 + p.n_sb));
+            }
+        } else {
+            // kept terms only: an alpha single itself (beta string B) and its
+            // alpha-beta doubles, one alpha single per warp
+            for (int k = warp; k < n_sa_pass; k += nw) {
+                const int s = sa_pass[k];
+                const uint64_t a2 = single_word(A, sa_info[s]);
+                uint32_t cnt = 0;
+                for (int sb = lane; sb < p.n_sb; sb += 32) cnt += single_word(B, sb_info[sb]) <= a2;
+                cnt = __reduce_add_sync(0xffffffffu, cnt);
+                if (lane == 0) atomicAdd(&hist[class_of(sa_zt[s])], cnt + (a2 >= B ? 1u : 0u));
+            }
+            if (a_in) {  // beta singles and beta-beta doubles keep alpha string A
+                uint32_t cnt = 0;
+                for (int sb = tid; sb < p.n_sb; sb += kGenThreads) cnt += single_word(B, sb_info[sb]) <= A;
+                for (int pi = warp; pi < n_occ_pairs_b; pi += nw) {
+                    const int pr = pairs[pi];
+                    const uint64_t b12 = B ^ (1ull << F.occB[pr & 0xFF]) ^ (1ull << F.occB[pr >> 8]);
+                    for (int t = lane; t < n_vir_pairs_b; t += 32) {
+                        const int pv = pairs[t];
+                        cnt += (b12 ^ (1ull << F.virB[pv & 0xFF]) ^ (1ull << F.virB[pv >> 8])) <= A;
+                    }
+                }
+                cnt = __reduce_add_sync(0xffffffffu, cnt);
+                if (lane == 0 && cnt) atomicAdd(&hist[class_of(F.ZcA)], cnt);
+            }
         }
         for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
             int pr = pairs[pi];
@@ -629,6 +666,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
                 if (!cons_ok(p.cons_mod, p.cons_rem, al)) continue;
+                if (sym && al < B) continue;
                 atomicAdd(&hist[class_of(z12 ^ F.zc[a1] ^ F.zc[a2])], 1u);
             }
         }
@@ -643,10 +681,27 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         // beta string of a beta single; beta-beta doubles one of their own
         const uint32_t K = p.heavy_class;
         const uint32_t per_sb = (uint32_t)n_sa_pass + (a_in ? 1u : 0u);
-        if (per_sb)
-            for (int sb = tid; sb < p.n_sb; sb += kGenThreads) atomicAdd(&hist[bclass_of(sb_zt[sb])], per_sb);
+        if (!sym) {
+            if (per_sb)
+                for (int sb = tid; sb < p.n_sb; sb += kGenThreads) atomicAdd(&hist[bclass_of(sb_zt[sb])], per_sb);
+        } else if (per_sb) {
+            // a beta single's string B' is kept under A (if A is in K) and
+            // under each alpha single of K that is not below it
+            for (int sb = tid; sb < p.n_sb; sb += kGenThreads) {
+                const uint64_t b2 = single_word(B, sb_info[sb]);
+                uint32_t cnt = a_in && A >= b2;
+                for (int k = 0; k < n_sa_pass; ++k) cnt += single_word(A, sa_info[sa_pass[k]]) >= b2;
+                if (cnt) atomicAdd(&hist[bclass_of(sb_zt[sb])], cnt);
+            }
+        }
         uint32_t keepB = 0;  // terms of class K whose beta string is B
-        if (tid == 0) keepB = (uint32_t)n_sa_pass;
+        if (tid == 0) {
+            if (!sym) {
+                keepB = (uint32_t)n_sa_pass;
+            } else {
+                for (int k = 0; k < n_sa_pass; ++k) keepB += single_word(A, sa_info[sa_pass[k]]) >= B;
+            }
+        }
         for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
             int pr = pairs[pi];
             int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
@@ -656,7 +711,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 int pv = pairs[t];
                 int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 if (class_of(z12 ^ F.zc[a1] ^ F.zc[a2]) != K) continue;
-                if (!cons_ok(p.cons_mod, p.cons_rem, a12 ^ (1ull << a1) ^ (1ull << a2))) continue;
+                const uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
+                if (!cons_ok(p.cons_mod, p.cons_rem, al)) continue;
+                if (sym && al < B) continue;
                 ++keepB;
             }
         }
@@ -666,9 +723,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 int pr = pairs[pi];
                 int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
                 uint64_t z12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
+                const uint64_t b12 = B ^ (1ull << r1) ^ (1ull << r2);
                 for (int t = lane; t < n_vir_pairs_b; t += 32) {
                     int pv = pairs[t];
-                    atomicAdd(&hist[bclass_of(z12 ^ F.zcb[F.virB[pv & 0xFF]] ^ F.zcb[F.virB[pv >> 8]])], 1u);
+                    const int v1 = F.virB[pv & 0xFF], v2 = F.virB[pv >> 8];
+                    if (sym && (b12 ^ (1ull << v1) ^ (1ull << v2)) > A) continue;
+                    atomicAdd(&hist[bclass_of(z12 ^ F.zcb[v1] ^ F.zcb[v2])], 1u);
                 }
             }
         __syncthreads();
@@ -758,7 +818,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             emit_batch<MODE>(
                 out, k0, kGenThreads, n_sa_pass,
                 [&](int k, uint64_t &zt) {
-                    zt = sa_zt[sa_pass[k]] ^ ZtbB;
+                    const int s = sa_pass[k];
+                    if (sym && single_word(A, sa_info[s]) < B) return false;
+                    zt = sa_zt[s] ^ ZtbB;
                     return true;
                 },
                 [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
@@ -785,7 +847,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 emit_batch<MODE>(
                     out, s0, kGenThreads, n_sb,
                     [&](int k, uint64_t &zt) {
-                        zt = ZtaA ^ sb_zt[sb_at(k)];
+                        const int s = sb_at(k);
+                        if (sym && single_word(B, sb_info[s]) > A) return false;
+                        zt = ZtaA ^ sb_zt[s];
                         return true;
                     },
                     [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
@@ -831,7 +895,9 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 emit_batch<MODE>(
                     out, sb0, 32, n_sb,
                     [&](int k, uint64_t &zt) {
-                        zt = ztA ^ sb_zt[sb_at(k)];
+                        const int sb = sb_at(k);
+                        if (sym && single_word(B, sb_info[sb]) > a2) return false;
+                        zt = ztA ^ sb_zt[sb];
                         return true;
                     },
                     [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den) {
@@ -917,13 +983,16 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 if (spin == 0) {
                                     uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
                                     if (cl < class_lo || cl >= class_hi) return false;
-                                    if (!cons_ok(cons_mod, cons_rem, w12 ^ (1ull << a1) ^ (1ull << a2))) return false;
+                                    const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
+                                    if (!cons_ok(cons_mod, cons_rem, w2)) return false;
+                                    if (sym && w2 < B) return false;
                                     zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
                                 } else {
                                     if (!bfull) {
                                         const uint32_t bc = bclass_of(zcb12 ^ F.zcb[a1] ^ F.zcb[a2]);
                                         if (bc < blo || bc >= bhi) return false;
                                     }
+                                    if (sym && (w12 ^ (1ull << a1) ^ (1ull << a2)) > A) return false;
                                     zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
                                 }
                                 return true;
@@ -967,11 +1036,11 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
 // Generator over the determinants of several instances (one CTA each).
 // Four CTAs per SM (64 registers): more warps hide the L2 round trips of the slot atomics.
-template <int MODE>
+template <int MODE, bool SYM>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_kernel(const GenBatch b)
 {
     if (b.n_inst == 1) {
-        gen_body<MODE>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
+        gen_body<MODE, SYM>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
         return;
     }
     // instance of this CTA (thread 0 searches, the others read the result);
@@ -991,14 +1060,14 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_kernel(const GenBatch b)
     }
     __syncthreads();
     const GenParams *__restrict__ gp = b.params + sinst;
-    gen_body<MODE>(*gp, sdet);
+    gen_body<MODE, SYM>(*gp, sdet);
 }
 
 // Generator for one determinant with its parameters passed by value.
 template <int MODE>
 __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel_one(const GenParams p)
 {
-    gen_body<MODE>(p, p.det_begin);
+    gen_body<MODE, false>(p, p.det_begin);
 }
 
 // ============================================================= diagonal
@@ -1408,8 +1477,11 @@ __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long 
 
 // One unique key: explicit filter against the reference slice, then the
 // Epstein-Nesbet term num^2 / (E0 - H_aa) of Eq. 3, added exactly.
-__device__ __forceinline__ void finish_key(const TileParams &p, double e0, const uint64_t *rk, unsigned long long nrk,
-                                           uint64_t a, uint64_t b, double num, int64_t den, KeyStats &st)
+// In a spin-flip symmetric run (sym) a key with a > b stands for itself and
+// its mirror (b, a), whose term is the same, so it counts twice.
+__device__ __forceinline__ void finish_key(const TileParams &p, double e0, bool sym, const uint64_t *rk,
+                                           unsigned long long nrk, uint64_t a, uint64_t b, double num, int64_t den,
+                                           KeyStats &st)
 {
     st.n_unique++;
     if (in_slice(rk, nrk, a, b)) {
@@ -1418,6 +1490,7 @@ __device__ __forceinline__ void finish_key(const TileParams &p, double e0, const
     }
     double d = den_to_double(den);
     double term = (num * num) * recip(d, den);
+    if (sym && a != b) term += term;
     fx_add_double(st.e2_lo, st.e2_hi, term, st.err);
     st.n_ext++;
     uint64_t ad = den < 0 ? (uint64_t)(-den) : (uint64_t)den;
@@ -1842,10 +1915,10 @@ __device__ void exact_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32
 }
 
 // One unique key into the statistics (filter + Eq. 3 term).
-__device__ __forceinline__ void finish_keyval(const TileParams &p, double e0, const uint64_t *rk,
+__device__ __forceinline__ void finish_keyval(const TileParams &p, double e0, bool sym, const uint64_t *rk,
                                               unsigned long long nrk, const KeyVal &v, KeyStats &st)
 {
-    finish_key(p, e0, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
+    finish_key(p, e0, sym, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
 }
 
 // Shared memory of the main tile kernel (several CTAs share an SM, so one CTA's
@@ -1906,6 +1979,7 @@ __device__ __forceinline__ int tile_instance(const unsigned long long *__restric
 // tile metadata one tile ahead, so each tile's TMA load starts at once.
 // Tiles of one instance are consecutive, so a CTA's statistics are flushed
 // to an instance's accumulator when its tiles move on to the next instance.
+template <bool SYM>
 __global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1924,6 +1998,7 @@ __global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(cons
     int cur = tile_instance(p.tile_base, p.n_inst, blockIdx.x);
     unsigned long long cur_end = p.tile_base[cur + 1];
     double e0 = p.e0[cur];
+    bool sym = SYM && p.sym[cur] != 0;
     bool dirty = false;
     uint32_t phase = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G) {
@@ -1934,6 +2009,7 @@ __global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(cons
             cur = tile_instance(p.tile_base, p.n_inst, t);
             cur_end = p.tile_base[cur + 1];
             e0 = p.e0[cur];
+            sym = SYM && p.sym[cur] != 0;
         }
         const int inst = cur;
         if (threadIdx.x == 0) {
@@ -1961,7 +2037,7 @@ __global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(cons
             mbar_wait_bounded(&M.bar[0], phase, p.err);
             phase ^= 1u;
             const bool ok = sort_reduce_chunk(M.recs, cnt, M.S, st.err,
-                                              [&](const KeyVal &v) { finish_keyval(p, e0, rk, rcnt, v, st); });
+                                              [&](const KeyVal &v) { finish_keyval(p, e0, sym, rk, rcnt, v, st); });
             if (!ok && threadIdx.x == 0) push_oversize(p, inst, t, cntl);  // exact path for a hash collision
             dirty = true;
         }
@@ -1977,7 +2053,8 @@ cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
     if (p.n_tiles == 0) return cudaSuccess;
     size_t sm = tile_smem_bytes();
     unsigned g = (unsigned)(p.n_tiles < (uint64_t)n_ctas ? p.n_tiles : (uint64_t)n_ctas);
-    tile_kernel<<<g, kTileThreads, sm, s>>>(p);
+    if (p.sym_any) tile_kernel<true><<<g, kTileThreads, sm, s>>>(p);
+    else tile_kernel<false><<<g, kTileThreads, sm, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -2035,6 +2112,7 @@ __device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst
 // the next instance.  The partial lists live in a fixed per-CTA scratch of
 // two buffers of scratch_cap records; a tile whose partials outgrow it sets
 // kErrScratch.
+template <bool SYM>
 __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -2057,6 +2135,7 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
     const unsigned int total = M.big_pre[p.n_inst];
     int inst = -1;
     double e0 = 0.0;
+    bool sym = false;
     KeyStats st;
     st.clear();
     {
@@ -2075,6 +2154,7 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
                 }
                 inst = lo;
                 e0 = p.e0[inst];
+                sym = SYM && p.sym[inst] != 0;
             }
             const uint64_t t = p.big_list[p.tile_base[inst] + (idx - M.big_pre[inst])];
             const unsigned long long off = p.tile_off[t];
@@ -2108,7 +2188,7 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
             // on its own.  Exact sums make the result independent of the split.
             unsigned long long nrk;
             const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
-            auto fin = [&](const KeyVal &v) { finish_keyval(p, e0, rk, nrk, v, st); };
+            auto fin = [&](const KeyVal &v) { finish_keyval(p, e0, sym, rk, nrk, v, st); };
             auto finish_list = [&](const Rec48 *src, int m) {
                 for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
                 __syncthreads();
@@ -2169,7 +2249,8 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
 cudaError_t launch_big_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 {
     if (n_ctas <= 0) return cudaSuccess;
-    big_tile_kernel<<<n_ctas, kBigThreads, big_smem_bytes(), s>>>(p);
+    if (p.sym_any) big_tile_kernel<true><<<n_ctas, kBigThreads, big_smem_bytes(), s>>>(p);
+    else big_tile_kernel<false><<<n_ctas, kBigThreads, big_smem_bytes(), s>>>(p);
     return cudaGetLastError();
 }
 
@@ -2260,11 +2341,19 @@ void gen_layout(GenParams &p, GenMode mode)
 cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int smem_bytes, cudaStream_t s)
 {
     if (n_ctas == 0) return cudaSuccess;
+    // the counting modes always check (they have registers to spare)
+    const unsigned g = (unsigned)n_ctas;
     switch (mode) {
-    case kModeClassCount: gen_kernel<kModeClassCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
-    case kModeTileCount: gen_kernel<kModeTileCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
-    case kModeEmit: gen_kernel<kModeEmit><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
-    case kModeBetaCount: gen_kernel<kModeBetaCount><<<(unsigned)n_ctas, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeClassCount: gen_kernel<kModeClassCount, true><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeBetaCount: gen_kernel<kModeBetaCount, true><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeTileCount:
+        if (b.sym_any) gen_kernel<kModeTileCount, true><<<g, kGenThreads, smem_bytes, s>>>(b);
+        else gen_kernel<kModeTileCount, false><<<g, kGenThreads, smem_bytes, s>>>(b);
+        break;
+    case kModeEmit:
+        if (b.sym_any) gen_kernel<kModeEmit, true><<<g, kGenThreads, smem_bytes, s>>>(b);
+        else gen_kernel<kModeEmit, false><<<g, kGenThreads, smem_bytes, s>>>(b);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -2291,23 +2380,28 @@ cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm)
 {
     const int g = gen_smem_max();
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(gen_kernel<kModeClassCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
+    const void *gens[] = {(const void *)gen_kernel<kModeClassCount, true>,
+                          (const void *)gen_kernel<kModeBetaCount, true>,
+                          (const void *)gen_kernel<kModeTileCount, false>,
+                          (const void *)gen_kernel<kModeTileCount, true>,
+                          (const void *)gen_kernel<kModeEmit, false>,
+                          (const void *)gen_kernel<kModeEmit, true>,
+                          (const void *)gen_kernel_one<kModeDetTerms>};
+    for (const void *f : gens)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    for (const void *f : {(const void *)tile_kernel<false>, (const void *)tile_kernel<true>})
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes())))
+            return e;
+    for (const void *f : {(const void *)big_tile_kernel<false>, (const void *)big_tile_kernel<true>})
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem_bytes())))
+            return e;
+    // the persistent kernels launch exactly the CTAs that fit at once (both
+    // variants have the same launch bounds and shared memory)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(tile_per_sm, tile_kernel<false>, kTileThreads,
+                                                           tile_smem_bytes())))
         return e;
-    if ((e = cudaFuncSetAttribute(gen_kernel<kModeTileCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
-        return e;
-    if ((e = cudaFuncSetAttribute(gen_kernel<kModeEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
-    if ((e = cudaFuncSetAttribute(gen_kernel<kModeBetaCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
-        return e;
-    if ((e = cudaFuncSetAttribute(gen_kernel_one<kModeDetTerms>, cudaFuncAttributeMaxDynamicSharedMemorySize, g)))
-        return e;
-    if ((e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem_bytes())))
-        return e;
-    if ((e = cudaFuncSetAttribute(big_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem_bytes())))
-        return e;
-    // the persistent kernels launch exactly the CTAs that fit at once
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(tile_per_sm, tile_kernel, kTileThreads, tile_smem_bytes())))
-        return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(big_per_sm, big_tile_kernel, kBigThreads, big_smem_bytes())))
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(big_per_sm, big_tile_kernel<false>, kBigThreads,
+                                                           big_smem_bytes())))
         return e;
     if (*tile_per_sm < 1 || *big_per_sm < 1) return cudaErrorInvalidConfiguration;
     return cudaSuccess;

@@ -35,6 +35,7 @@ struct RefRes {
     double e0 = 0.0;
     DevBuf keys, coef, hii, d0;
     DevBuf g;      // per determinant: (h_xx + p(x)) * 2^48 for the n alpha then the n beta spin-orbitals
+    bool flip_symmetric = false;  // closed under alpha <-> beta exchange with equal coefficients
     int busy = 0;  // requests of the serving engine that use it
 };
 
@@ -77,6 +78,7 @@ struct StepDev {
     unsigned long long det_base[kMaxBatch + 1];
     unsigned long long tile_base[kMaxBatch + 1];
     double e0[kMaxBatch];
+    uint32_t sym[kMaxBatch];
     unsigned long long expected[kMaxBatch];
     RunAcc *acc[kMaxBatch];
     unsigned int n_big[kMaxBatch];

@@ -42,6 +42,7 @@ __all__ = [
     "Reference",
     "make_integrals",
     "make_reference",
+    "make_symmetric_reference",
     "make_workload",
     "batch_instance_params",
     "WORKLOADS",
@@ -182,6 +183,73 @@ def make_reference(n_orb: int, n_elec_per_spin: int, n_det: int, max_level: int,
     coef[0] = 0.95
     if n_det > 1:
         z = rng.normal(0.0, 1.0, size=n_det - 1) * np.exp(-0.5 * level[1:].astype(np.float64))
+        z *= math.sqrt(1.0 - 0.95 ** 2) / np.linalg.norm(z)
+        coef[1:] = z
+    return Reference(n_alpha=n, n_beta=n, keys=keys, coef=coef, level=level)
+
+
+def make_symmetric_reference(n_orb: int, n_elec_per_spin: int, n_det: int, max_level: int,
+                             seed: int) -> Reference:
+    """A reference closed under exchange of the alpha and beta strings.
+
+    Determinants are drawn as in make_reference (HF plus random excitations,
+    deduplicated); each one with alpha != beta brings its mirror (beta, alpha)
+    with the same coefficient, so c(beta, alpha) = c(alpha, beta) for every
+    pair (the wavefunction is then an eigenvector of the spin flip).  n_det
+    counts the mirrors; HF (alpha = beta) is its own mirror.
+    """
+    n = int(n_elec_per_spin)
+    if not (0 < n < n_orb <= 64):
+        raise ValueError("need 0 < n_elec_per_spin < n_orb <= 64")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hf = (1 << n) - 1
+    pairs = [(hf, hf)]
+    levels = [0]
+    seen = {(hf, hf)}
+    have = 1
+    while have < n_det:
+        batch = max(1024, n_det - have)
+        lvl = 1 + np.floor(rng.random(batch) * max_level).astype(np.int64)
+        a, b = _draw_excitations(rng, n_orb, n, lvl, batch)
+        for x, y, l in zip(a.tolist(), b.tolist(), lvl.tolist()):
+            if (x, y) in seen:
+                continue
+            need = 1 if x == y else 2
+            if have + need > n_det:
+                continue
+            seen.add((x, y))
+            seen.add((y, x))
+            pairs.append((x, y))
+            levels.append(l)
+            have += need
+            if have == n_det:
+                break
+    alpha, beta, level = [], [], []
+    for (x, y), l in zip(pairs, levels):
+        alpha.append(x)
+        beta.append(y)
+        level.append(l)
+        if x != y:
+            alpha.append(y)
+            beta.append(x)
+            level.append(l)
+    keys = np.empty(2 * n_det, dtype=np.uint64)
+    keys[0::2] = np.array(alpha, dtype=np.uint64)
+    keys[1::2] = np.array(beta, dtype=np.uint64)
+    level = np.array(level, dtype=np.int8)
+    coef = np.empty(n_det)
+    coef[0] = 0.95
+    if n_det > 1:
+        # one draw per mirror pair, shared by both members
+        z = np.empty(n_det - 1)
+        i = 1
+        for (x, y), l in zip(pairs[1:], levels[1:]):
+            v = rng.normal(0.0, 1.0) * math.exp(-0.5 * l)
+            z[i - 1] = v
+            i += 1
+            if x != y:
+                z[i - 1] = v
+                i += 1
         z *= math.sqrt(1.0 - 0.95 ** 2) / np.linalg.norm(z)
         coef[1:] = z
     return Reference(n_alpha=n, n_beta=n, keys=keys, coef=coef, level=level)
