@@ -110,6 +110,16 @@ typedef struct {
     uint32_t tile_target;       /* mean terms per hash tile, at most 1024
                                    (0 = default 832, or the tuned value) */
     uint32_t flags;             /* PT2_FLAG_* below */
+    double numerator_cutoff;    /* 0 = exact.  Otherwise a contribution c_i H_ai
+                                   with |c_i H_ai| < numerator_cutoff is
+                                   ignored before it gets a record, a
+                                   denominator or a sort (the Results section
+                                   and the subsection on the matrix-element
+                                   cutoff use 1e-8); a determinant all of
+                                   whose contributions are ignored is not in
+                                   the external set.  n_terms counts the kept
+                                   contributions.  PT2_ERR_INVALID if negative
+                                   or not finite. */
 } pt2_opts;
 
 #define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times); a batch created

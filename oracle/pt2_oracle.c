@@ -44,6 +44,12 @@
  * excitation changes at most two alpha orbitals, so a reference determinant
  * whose alpha word differs from rem in more than four bits contributes
  * nothing to it and is not enumerated.
+ *
+ * Optional numerator cutoff (the Results section and the subsection on the
+ * matrix-element cutoff): a contribution c_i H_ai with |c_i H_ai| below the
+ * cutoff is ignored before it reaches the map, so an excited determinant all
+ * of whose contributions are below it is not in S.  Cutoff 0 keeps every
+ * contribution.  n_terms then counts the kept contributions.
  */
 #include <math.h>
 #include <stdint.h>
@@ -321,6 +327,21 @@ static void visit_map(void *ctx, uint64_t a, uint64_t b, double v)
     if (map_add(m, a, b, v)) m->size = (size_t)-1; /* allocation failure marker */
 }
 
+typedef struct {
+    map_t *m;
+    double cutoff;
+    uint64_t kept;
+} cut_ctx;
+
+/* The numerator cutoff in front of the map: contributions below it are dropped. */
+static void visit_cut(void *ctx, uint64_t a, uint64_t b, double v)
+{
+    cut_ctx *k = (cut_ctx *)ctx;
+    if (!(fabs(v) >= k->cutoff)) return;
+    k->kept++;
+    visit_map(k->m, a, b, v);
+}
+
 /* ------------------------------------------------------------ the energy */
 
 typedef struct {
@@ -391,11 +412,12 @@ static int check_ref(int n_orb, int64_t n_det, const uint64_t *keys)
  */
 int64_t oracle_pt2(int n_orb, const double *h, const double *eri, int64_t n_det,
                    const uint64_t *keys, const double *coef, double e0,
-                   uint64_t cons_mod, uint64_t cons_rem, int include_ref,
+                   uint64_t cons_mod, uint64_t cons_rem, int include_ref, double cutoff,
                    oracle_result *out, uint64_t *dump_keys, double *dump_num,
                    double *dump_haa, int64_t dump_cap)
 {
     if (check_ref(n_orb, n_det, keys)) return -1;
+    if (!(cutoff >= 0.0) || isinf(cutoff)) return -1;
     sys_t s = {n_orb, h, eri};
     constraint_t cons = {cons_mod, cons_rem};
     memset(out, 0, sizeof(*out));
@@ -403,13 +425,14 @@ int64_t oracle_pt2(int n_orb, const double *h, const double *eri, int64_t n_det,
 
     map_t m;
     if (map_init(&m, 1 << 16)) return -2;
-    uint64_t nterms = 0;
+    cut_ctx cc = {&m, cutoff, 0};
     const int exact_alpha = cons_mod > 1 && (n_orb >= 64 || cons_mod > (1ull << n_orb) - 1ull);
     for (int64_t i = 0; i < n_det; ++i) {
         if (exact_alpha && __builtin_popcountll(keys[2 * i] ^ cons_rem) > 4) continue;
-        nterms += enumerate_det(&s, keys[2 * i], keys[2 * i + 1], coef[i], &cons, visit_map, &m);
+        enumerate_det(&s, keys[2 * i], keys[2 * i + 1], coef[i], &cons, visit_cut, &cc);
         if (m.size == (size_t)-1) { map_free(&m); return -2; }
     }
+    const uint64_t nterms = cc.kept;
 
     /* reference keys, sorted, for the explicit filter */
     key_t *rk = malloc((size_t)(n_det ? n_det : 1) * sizeof(key_t));

@@ -148,6 +148,7 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.bclass_hi = kNumClasses;
     p.heavy_class = 0;
     p.sym = 0;
+    p.cutoff = 0.0;
     p.cons_mod = 1;
     p.err = (uint32_t *)c->err_word.ptr;
     return p;

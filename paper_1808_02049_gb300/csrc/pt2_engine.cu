@@ -77,6 +77,9 @@ int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)
                         "spin-flip symmetry needs a reference closed under alpha <-> beta exchange with equal coefficients");
         j.gp.sym = 1;
     }
+    if (!(j.o.numerator_cutoff >= 0.0) || std::isinf(j.o.numerator_cutoff))
+        return fail(c, PT2_ERR_INVALID, "numerator_cutoff must be finite and non-negative");
+    j.gp.cutoff = j.o.numerator_cutoff;
     return PT2_OK;
 }
 
@@ -105,6 +108,9 @@ cudaError_t gen_launch(pt2_ctx *c, GenMode mode, GenBatch b, uint64_t n_ctas, in
     return cudaSuccess;
 }
 
+// Checks a job's generator launches need (kFiltSym | kFiltCut).
+int job_filt(const Job &j) { return (j.gp.sym ? kFiltSym : 0) | (j.gp.cutoff > 0.0 ? kFiltCut : 0); }
+
 // Terms per beta class among the terms of alpha class k of a job (one
 // beta-count launch over the job's determinants).
 int beta_counts(pt2_ctx *c, const Job &j, uint32_t k, std::vector<unsigned long long> &out)
@@ -116,7 +122,7 @@ int beta_counts(pt2_ctx *c, const Job &j, uint32_t k, std::vector<unsigned long 
     gen_layout(g, kModeBetaCount);
     cudaStream_t st = c->stream;
     CK(cudaMemsetAsync(c->class_counts.ptr, 0, kNumClasses * 8, st), "memset");
-    GenBatch b{nullptr, nullptr, 1, 0, g};
+    GenBatch b{nullptr, nullptr, 1, 0, g, job_filt(j)};
     CK(gen_launch(c, kModeBetaCount, b, j.r->n_det, g.smem_bytes), "beta count kernel");
     out.assign(kNumClasses, 0);
     CK(cudaMemcpyAsync(out.data(), c->class_counts.ptr, kNumClasses * 8, cudaMemcpyDeviceToHost, st), "copy");
@@ -143,8 +149,9 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
     GenParams *hp = reinterpret_cast<GenParams *>(c->steps_pinned);
     unsigned long long *hb = reinterpret_cast<unsigned long long *>(hp + n);
     uint64_t cta = 0;
-    int smem = 0;
+    int smem = 0, filt = 0;
     for (size_t i = 0; i < n; ++i) {
+        filt |= job_filt(*jobs[i]);
         GenParams g = jobs[i]->gp;
         g.class_lo = 0;
         g.class_hi = kNumClasses;
@@ -163,7 +170,7 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
     GenBatch b{reinterpret_cast<const GenParams *>(c->gen_tab.ptr),
                reinterpret_cast<const unsigned long long *>(static_cast<char *>(c->gen_tab.ptr) +
                                                             n * sizeof(GenParams)),
-               (int)n, 0, hp[0]};
+               (int)n, 0, hp[0], filt};
     CK(gen_launch(c, kModeClassCount, b, cta, smem), "class count kernel");
     std::vector<unsigned long long> cls(n * kNumClasses);
     CK(cudaMemcpyAsync(cls.data(), c->class_counts.ptr, n * kNumClasses * 8, cudaMemcpyDeviceToHost, st), "copy");
@@ -366,7 +373,7 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     if (prof) CK(cudaEventRecord(E[0], st), "event");
     CK(cudaMemsetAsync(c->tile_counts.ptr, 0, sp.n_tiles * 4, st), "memset");
     GenBatch gb{d->params, d->det_base, n, 0, {}, 0};
-    for (const StepItem &it : sp.items) gb.sym_any |= it.job->gp.sym != 0;
+    for (const StepItem &it : sp.items) gb.filt |= job_filt(*it.job);
     if (n == 1) gb.one = step_item_params(c, sp, 0, 0);
     const int smem = step_smem(sp);
     CK(gen_launch(c, kModeTileCount, gb, sp.n_ctas, smem), "tile count kernel");
@@ -413,7 +420,7 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     tp.tile_base = d->tile_base;
     tp.e0 = d->e0;
     tp.sym = d->sym;
-    tp.sym_any = gb.sym_any;
+    tp.sym_any = (gb.filt & kFiltSym) != 0;
     tp.acc = d->acc;
     tp.n_big = d->n_big;
     tp.big_max = reinterpret_cast<unsigned long long *>(c->big_max.ptr);

@@ -108,6 +108,7 @@ struct GenParams {
     uint32_t bclass_lo, bclass_hi;  // and, within them, beta classes [lo, hi) (all: 0, kNumClasses)
     uint32_t heavy_class;         // beta-count mode: the alpha class whose beta classes are counted
     uint32_t sym;                 // spin-flip symmetric run: only terms with alpha' >= beta'
+    double cutoff;                // numerator cutoff: contributions |c_i H_ai| below it are dropped (0: none)
     uint64_t cons_mod, cons_rem;  // alpha % mod == rem (mod <= 1: none)
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance
@@ -127,6 +128,10 @@ struct GenParams {
 // cta_offset + blockIdx.x) belongs to the instance with
 // det_base[i] <= g < det_base[i + 1] and handles its determinant
 // params[i].det_begin + g - det_base[i].
+// Checks a generator variant carries (template argument): the spin-flip
+// drop rule and the numerator cutoff.
+constexpr int kFiltSym = 1, kFiltCut = 2;
+
 struct GenBatch {
     const GenParams *params;
     const unsigned long long *det_base;  // n_inst + 1
@@ -135,7 +140,7 @@ struct GenBatch {
     // n_inst == 1: the instance's parameters, read from the launch arguments
     // (constant bank) instead of the device table
     GenParams one;
-    int sym_any;  // some instance is a spin-flip symmetric run: launch the variant that checks
+    int filt;     // kFiltSym | kFiltCut: the checks some instance needs (selects the kernel variant)
 };
 
 // Run accumulator: every field is an exact integer reduction.

@@ -356,6 +356,38 @@ struct GenFixed {
 // beta class of a beta-string hash (splits the heavy alpha classes)
 __device__ __forceinline__ uint32_t bclass_of(uint64_t zcb) { return (uint32_t)(zcb >> (64 - kClassBits)); }
 
+// Matrix elements without sign and coefficient, shared by every generator mode
+// so that the numerator cutoff takes the same decision in the counting and
+// the emitting launches (the same operations in the same order).
+// Single r -> a of a string with occupied list occ_s (n_s), the other spin's
+// string having occupied list occ_o (n_o): h_ar + sum_j ((ar|jj) - (aj|jr))
+// over the same spin + sum_j (ar|jj) over the other spin.
+__device__ __forceinline__ double single_value(const double *__restrict__ ht, const double *__restrict__ eri, int N,
+                                               const int *occ_s, int n_s, const int *occ_o, int n_o, int r, int a)
+{
+    double v = ht[a * N + r];
+    for (int q = 0; q < n_s; ++q) {
+        const int j = occ_s[q];
+        v += eri[(((size_t)a * N + r) * N + j) * N + j] - eri[(((size_t)a * N + j) * N + j) * N + r];
+    }
+    for (int q = 0; q < n_o; ++q) {
+        const int j = occ_o[q];
+        v += eri[(((size_t)a * N + r) * N + j) * N + j];
+    }
+    return v;
+}
+
+// Same-spin double r1 r2 -> a1 a2: (a1 r1|a2 r2) - (a1 r2|a2 r1), read as
+// (r2 a2|r1 a1) - (r1 a2|r2 a1) so that a1 varies fastest in memory.
+__device__ __forceinline__ double same_double_value(const double *__restrict__ eri, int N, int r1, int r2, int a1,
+                                                    int a2)
+{
+    return __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) - __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
+}
+
+// Kept by the numerator cutoff: |c v| >= cut (the sign of the element does not matter).
+__device__ __forceinline__ bool above_cut(double c, double v, double cut) { return fabs(c * v) >= cut; }
+
 // The string W after the single excitation packed in `info` (r in bits 0-7, a in 8-15).
 __device__ __forceinline__ uint64_t single_word(uint64_t W, uint32_t info)
 {
@@ -446,9 +478,10 @@ __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, i
 }
 
 // All singles and doubles of determinant `det` of one instance (the body of
-// both generator kernels).  SYM: the instance may be a spin-flip symmetric run
-// (the check costs registers, so the emission of ordinary runs leaves it out).
-template <int MODE, bool SYM>
+// both generator kernels).  FILT (kFiltSym | kFiltCut): the instance may be a
+// spin-flip symmetric run, or have a numerator cutoff (the checks cost
+// registers, so the emission of ordinary runs leaves them out).
+template <int MODE, int FILT>
 __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -475,7 +508,13 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     const uint32_t blo = p.bclass_lo, bhi = p.bclass_hi;
     // spin-flip symmetric run: a term is kept only if its alpha string, as a
     // 64-bit word, is not below its beta string (every mode applies the same rule)
-    const bool sym = SYM && p.sym != 0;
+    const bool sym = (FILT & kFiltSym) && p.sym != 0;
+    // numerator cutoff (Results section; subsection on the matrix-element
+    // cutoff): a contribution c_i H_ai with |c_i H_ai| below it is dropped
+    // before its slot is taken, so it gets no record, denominator or sort
+    constexpr bool kCut = (FILT & kFiltCut) != 0;
+    const double cut = kCut ? p.cutoff : 0.0;
+    const bool cutting = kCut && cut > 0.0;
     const int N = p.sys.n;
     const int na = p.na, nb = p.nb, nva = N - na, nvb = N - nb;
     const double *__restrict__ eri = p.sys.eri;
@@ -623,7 +662,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
     if constexpr (MODE == kModeClassCount) {
         // work list (the paper's first pass over the wavefunction): terms per class
-        if (!sym) {
+        if (!sym && !cutting) {
             if (tid == 0 && a_in)
                 atomicAdd(&hist[class_of(F.ZcA)], (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
             for (int k = tid; k < n_sa_pass; k += kGenThreads) {
@@ -631,25 +670,50 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 atomicAdd(&hist[class_of(sa_zt[s])], (uint32_t)(1 + p.n_sb));
             }
         } else {
-            // kept terms only: an alpha single itself (beta string B) and its
+            // kept terms only (the drop rule of a symmetric run, the numerator
+            // cutoff): an alpha single itself (beta string B) and its
             // alpha-beta doubles, one alpha single per warp
             for (int k = warp; k < n_sa_pass; k += nw) {
                 const int s = sa_pass[k];
-                const uint64_t a2 = single_word(A, sa_info[s]);
+                const uint32_t info = sa_info[s];
+                const int rA = info & 0xFF, aA = (info >> 8) & 0xFF;
+                const uint64_t a2 = single_word(A, info);
+                const double *slice = eri + ((size_t)rA * N + aA) * N * N;
                 uint32_t cnt = 0;
-                for (int sb = lane; sb < p.n_sb; sb += 32) cnt += single_word(B, sb_info[sb]) <= a2;
+                for (int sb = lane; sb < p.n_sb; sb += 32) {
+                    const uint32_t bi = sb_info[sb];
+                    if (sym && single_word(B, bi) > a2) continue;
+                    if (cutting && !above_cut(c, __ldg(slice + (bi & 0xFF) * N + ((bi >> 8) & 0xFF)), cut)) continue;
+                    ++cnt;
+                }
                 cnt = __reduce_add_sync(0xffffffffu, cnt);
-                if (lane == 0) atomicAdd(&hist[class_of(sa_zt[s])], cnt + (a2 >= B ? 1u : 0u));
+                if (lane == 0) {
+                    if ((!sym || a2 >= B) &&
+                        (!cutting || above_cut(c, single_value(ht, eri, N, F.occA, na, F.occB, nb, rA, aA), cut)))
+                        ++cnt;
+                    if (cnt) atomicAdd(&hist[class_of(sa_zt[s])], cnt);
+                }
             }
             if (a_in) {  // beta singles and beta-beta doubles keep alpha string A
                 uint32_t cnt = 0;
-                for (int sb = tid; sb < p.n_sb; sb += kGenThreads) cnt += single_word(B, sb_info[sb]) <= A;
+                for (int sb = tid; sb < p.n_sb; sb += kGenThreads) {
+                    const uint32_t bi = sb_info[sb];
+                    if (sym && single_word(B, bi) > A) continue;
+                    if (cutting &&
+                        !above_cut(c, single_value(ht, eri, N, F.occB, nb, F.occA, na, bi & 0xFF, (bi >> 8) & 0xFF), cut))
+                        continue;
+                    ++cnt;
+                }
                 for (int pi = warp; pi < n_occ_pairs_b; pi += nw) {
                     const int pr = pairs[pi];
-                    const uint64_t b12 = B ^ (1ull << F.occB[pr & 0xFF]) ^ (1ull << F.occB[pr >> 8]);
+                    const int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
+                    const uint64_t b12 = B ^ (1ull << r1) ^ (1ull << r2);
                     for (int t = lane; t < n_vir_pairs_b; t += 32) {
                         const int pv = pairs[t];
-                        cnt += (b12 ^ (1ull << F.virB[pv & 0xFF]) ^ (1ull << F.virB[pv >> 8])) <= A;
+                        const int v1 = F.virB[pv & 0xFF], v2 = F.virB[pv >> 8];
+                        if (sym && (b12 ^ (1ull << v1) ^ (1ull << v2)) > A) continue;
+                        if (cutting && !above_cut(c, same_double_value(eri, N, r1, r2, v1, v2), cut)) continue;
+                        ++cnt;
                     }
                 }
                 cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -667,6 +731,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
                 if (!cons_ok(p.cons_mod, p.cons_rem, al)) continue;
                 if (sym && al < B) continue;
+                if (cutting && !above_cut(c, same_double_value(eri, N, r1, r2, a1, a2), cut)) continue;
                 atomicAdd(&hist[class_of(z12 ^ F.zc[a1] ^ F.zc[a2])], 1u);
             }
         }
@@ -681,25 +746,44 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         // beta string of a beta single; beta-beta doubles one of their own
         const uint32_t K = p.heavy_class;
         const uint32_t per_sb = (uint32_t)n_sa_pass + (a_in ? 1u : 0u);
-        if (!sym) {
+        if (!sym && !cutting) {
             if (per_sb)
                 for (int sb = tid; sb < p.n_sb; sb += kGenThreads) atomicAdd(&hist[bclass_of(sb_zt[sb])], per_sb);
         } else if (per_sb) {
-            // a beta single's string B' is kept under A (if A is in K) and
-            // under each alpha single of K that is not below it
+            // a beta single's string B' is kept (drop rule, cutoff) as a beta
+            // single under A if A is in K, and in an alpha-beta double under
+            // each alpha single of K
             for (int sb = tid; sb < p.n_sb; sb += kGenThreads) {
-                const uint64_t b2 = single_word(B, sb_info[sb]);
-                uint32_t cnt = a_in && A >= b2;
-                for (int k = 0; k < n_sa_pass; ++k) cnt += single_word(A, sa_info[sa_pass[k]]) >= b2;
+                const uint32_t bi = sb_info[sb];
+                const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
+                const uint64_t b2 = single_word(B, bi);
+                uint32_t cnt = a_in && (!sym || A >= b2) &&
+                               (!cutting || above_cut(c, single_value(ht, eri, N, F.occB, nb, F.occA, na, rB, aB), cut));
+                for (int k = 0; k < n_sa_pass; ++k) {
+                    const uint32_t info = sa_info[sa_pass[k]];
+                    if (sym && single_word(A, info) < b2) continue;
+                    if (cutting) {
+                        const double *slice = eri + ((size_t)(info & 0xFF) * N + ((info >> 8) & 0xFF)) * N * N;
+                        if (!above_cut(c, __ldg(slice + rB * N + aB), cut)) continue;
+                    }
+                    ++cnt;
+                }
                 if (cnt) atomicAdd(&hist[bclass_of(sb_zt[sb])], cnt);
             }
         }
         uint32_t keepB = 0;  // terms of class K whose beta string is B
         if (tid == 0) {
-            if (!sym) {
+            if (!sym && !cutting) {
                 keepB = (uint32_t)n_sa_pass;
             } else {
-                for (int k = 0; k < n_sa_pass; ++k) keepB += single_word(A, sa_info[sa_pass[k]]) >= B;
+                for (int k = 0; k < n_sa_pass; ++k) {
+                    const uint32_t info = sa_info[sa_pass[k]];
+                    if (sym && single_word(A, info) < B) continue;
+                    if (cutting && !above_cut(c, single_value(ht, eri, N, F.occA, na, F.occB, nb, info & 0xFF,
+                                                              (info >> 8) & 0xFF), cut))
+                        continue;
+                    ++keepB;
+                }
             }
         }
         for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
@@ -714,6 +798,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 const uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
                 if (!cons_ok(p.cons_mod, p.cons_rem, al)) continue;
                 if (sym && al < B) continue;
+                if (cutting && !above_cut(c, same_double_value(eri, N, r1, r2, a1, a2), cut)) continue;
                 ++keepB;
             }
         }
@@ -728,6 +813,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     int pv = pairs[t];
                     const int v1 = F.virB[pv & 0xFF], v2 = F.virB[pv >> 8];
                     if (sym && (b12 ^ (1ull << v1) ^ (1ull << v2)) > A) continue;
+                    if (cutting && !above_cut(c, same_double_value(eri, N, r1, r2, v1, v2), cut)) continue;
                     atomicAdd(&hist[bclass_of(z12 ^ F.zcb[v1] ^ F.zcb[v2])], 1u);
                 }
             }
@@ -820,6 +906,11 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 [&](int k, uint64_t &zt) {
                     const int s = sa_pass[k];
                     if (sym && single_word(A, sa_info[s]) < B) return false;
+                    if (cutting) {
+                        const uint32_t info = sa_info[s];
+                        const double v = single_value(ht, eri, N, F.occA, na, F.occB, nb, info & 0xFF, (info >> 8) & 0xFF);
+                        if (!above_cut(c, v, cut)) return false;
+                    }
                     zt = sa_zt[s] ^ ZtbB;
                     return true;
                 },
@@ -827,15 +918,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     const int s = sa_pass[k];
                     const uint32_t info = sa_info[s];
                     const int r = info & 0xFF, a = (info >> 8) & 0xFF;
-                    double v = ht[a * N + r];
-                    for (int q = 0; q < na; ++q) {
-                        int j = F.occA[q];
-                        v += eri[(((size_t)a * N + r) * N + j) * N + j] - eri[(((size_t)a * N + j) * N + j) * N + r];
-                    }
-                    for (int q = 0; q < nb; ++q) {
-                        int j = F.occB[q];
-                        v += eri[(((size_t)a * N + r) * N + j) * N + j];
-                    }
+                    const double v = single_value(ht, eri, N, F.occA, na, F.occB, nb, r, a);
                     ka = A ^ (1ull << r) ^ (1ull << a);
                     kb = B;
                     num = flip_sign(c * v, info >> 16);
@@ -849,6 +932,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     [&](int k, uint64_t &zt) {
                         const int s = sb_at(k);
                         if (sym && single_word(B, sb_info[s]) > A) return false;
+                        if (cutting) {
+                            const uint32_t info = sb_info[s];
+                            const double v =
+                                single_value(ht, eri, N, F.occB, nb, F.occA, na, info & 0xFF, (info >> 8) & 0xFF);
+                            if (!above_cut(c, v, cut)) return false;
+                        }
                         zt = ZtaA ^ sb_zt[s];
                         return true;
                     },
@@ -856,16 +945,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                         const int s = sb_at(k);
                         const uint32_t info = sb_info[s];
                         const int r = info & 0xFF, a = (info >> 8) & 0xFF;
-                        double v = ht[a * N + r];
-                        for (int q = 0; q < nb; ++q) {
-                            int j = F.occB[q];
-                            v += eri[(((size_t)a * N + r) * N + j) * N + j] -
-                                 eri[(((size_t)a * N + j) * N + j) * N + r];
-                        }
-                        for (int q = 0; q < na; ++q) {
-                            int j = F.occA[q];
-                            v += eri[(((size_t)a * N + r) * N + j) * N + j];
-                        }
+                        const double v = single_value(ht, eri, N, F.occB, nb, F.occA, na, r, a);
                         ka = A;
                         kb = B ^ (1ull << r) ^ (1ull << a);
                         num = flip_sign(c * v, info >> 16);
@@ -880,16 +960,15 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             const uint64_t ztA = sa_zt[s];
             int64_t baseD = 0;
             double cA = 0.0;
-            const double *slice = nullptr;
+            // (aA rA|aB rB) = (rA aA|rB aB): lanes take consecutive beta
+            // singles (same rB, ascending aB), so this layout is contiguous
+            const double *slice = eri + ((size_t)rA * N + aA) * N * N;
             if constexpr (kVal) {
                 // u[q] = J(aA, q) - J(rA, q): the alpha-beta cross terms of H_aa
                 for (int q = lane; q < N; q += 32) vec[q] = Jx[aA * N + q] - Jx[rA * N + q];
                 __syncwarp();
                 baseD = d0 - sa_delta[s];
                 cA = flip_sign(c, info >> 16);
-                // (aA rA|aB rB) = (rA aA|rB aB): lanes take consecutive beta
-                // singles (same rB, ascending aB), so this layout is contiguous
-                slice = eri + ((size_t)rA * N + aA) * N * N;
             }
             for (int sb0 = lane; sb0 < n_sb; sb0 += 32 * kGenBatch)
                 emit_batch<MODE>(
@@ -897,6 +976,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     [&](int k, uint64_t &zt) {
                         const int sb = sb_at(k);
                         if (sym && single_word(B, sb_info[sb]) > a2) return false;
+                        if (cutting) {
+                            const uint32_t bi = sb_info[sb];
+                            if (!above_cut(c, __ldg(slice + (bi & 0xFF) * N + ((bi >> 8) & 0xFF)), cut)) return false;
+                        }
                         zt = ztA ^ sb_zt[sb];
                         return true;
                     },
@@ -986,6 +1069,8 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                     const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
                                     if (!cons_ok(cons_mod, cons_rem, w2)) return false;
                                     if (sym && w2 < B) return false;
+                                    if (cutting && !above_cut(c, same_double_value(eri, N, r1, r2, a1, a2), cut))
+                                        return false;
                                     zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
                                 } else {
                                     if (!bfull) {
@@ -993,6 +1078,8 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                         if (bc < blo || bc >= bhi) return false;
                                     }
                                     if (sym && (w12 ^ (1ull << a1) ^ (1ull << a2)) > A) return false;
+                                    if (cutting && !above_cut(c, same_double_value(eri, N, r1, r2, a1, a2), cut))
+                                        return false;
                                     zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
                                 }
                                 return true;
@@ -1008,10 +1095,8 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
                                 const uint32_t par =
                                     __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                                // (a1 r1|a2 r2) - (a1 r2|a2 r1), read as (r2 a2|r1 a1) - (r1 a2|r2 a1):
                                 // a1 is the fastest-varying index across lanes
-                                const double e = __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) -
-                                                 __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
+                                const double e = same_double_value(eri, N, r1, r2, a1, a2);
                                 num = flip_sign(c * e, par);
                                 den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
                             });
@@ -1036,11 +1121,11 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
 // Generator over the determinants of several instances (one CTA each).
 // Four CTAs per SM (64 registers): more warps hide the L2 round trips of the slot atomics.
-template <int MODE, bool SYM>
+template <int MODE, int FILT>
 __global__ void __launch_bounds__(kGenThreads, 4) gen_kernel(const GenBatch b)
 {
     if (b.n_inst == 1) {
-        gen_body<MODE, SYM>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
+        gen_body<MODE, FILT>(b.one, b.one.det_begin + b.cta_offset + blockIdx.x);
         return;
     }
     // instance of this CTA (thread 0 searches, the others read the result);
@@ -1060,14 +1145,14 @@ __global__ void __launch_bounds__(kGenThreads, 4) gen_kernel(const GenBatch b)
     }
     __syncthreads();
     const GenParams *__restrict__ gp = b.params + sinst;
-    gen_body<MODE, SYM>(*gp, sdet);
+    gen_body<MODE, FILT>(*gp, sdet);
 }
 
 // Generator for one determinant with its parameters passed by value.
 template <int MODE>
 __global__ void __launch_bounds__(kGenThreads, 3) gen_kernel_one(const GenParams p)
 {
-    gen_body<MODE, false>(p, p.det_begin);
+    gen_body<MODE, 0>(p, p.det_begin);
 }
 
 // ============================================================= diagonal
@@ -2341,18 +2426,34 @@ void gen_layout(GenParams &p, GenMode mode)
 cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int smem_bytes, cudaStream_t s)
 {
     if (n_ctas == 0) return cudaSuccess;
-    // the counting modes always check (they have registers to spare)
+    // the counting modes always carry the symmetry check (they have registers to spare)
     const unsigned g = (unsigned)n_ctas;
+    const bool cut = (b.filt & kFiltCut) != 0;
+    constexpr int S = kFiltSym, C = kFiltCut;
     switch (mode) {
-    case kModeClassCount: gen_kernel<kModeClassCount, true><<<g, kGenThreads, smem_bytes, s>>>(b); break;
-    case kModeBetaCount: gen_kernel<kModeBetaCount, true><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeClassCount:
+        if (cut) gen_kernel<kModeClassCount, S | C><<<g, kGenThreads, smem_bytes, s>>>(b);
+        else gen_kernel<kModeClassCount, S><<<g, kGenThreads, smem_bytes, s>>>(b);
+        break;
+    case kModeBetaCount:
+        if (cut) gen_kernel<kModeBetaCount, S | C><<<g, kGenThreads, smem_bytes, s>>>(b);
+        else gen_kernel<kModeBetaCount, S><<<g, kGenThreads, smem_bytes, s>>>(b);
+        break;
     case kModeTileCount:
-        if (b.sym_any) gen_kernel<kModeTileCount, true><<<g, kGenThreads, smem_bytes, s>>>(b);
-        else gen_kernel<kModeTileCount, false><<<g, kGenThreads, smem_bytes, s>>>(b);
+        switch (b.filt & (S | C)) {
+        case 0: gen_kernel<kModeTileCount, 0><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        case S: gen_kernel<kModeTileCount, S><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        case C: gen_kernel<kModeTileCount, C><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        default: gen_kernel<kModeTileCount, S | C><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        }
         break;
     case kModeEmit:
-        if (b.sym_any) gen_kernel<kModeEmit, true><<<g, kGenThreads, smem_bytes, s>>>(b);
-        else gen_kernel<kModeEmit, false><<<g, kGenThreads, smem_bytes, s>>>(b);
+        switch (b.filt & (S | C)) {
+        case 0: gen_kernel<kModeEmit, 0><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        case S: gen_kernel<kModeEmit, S><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        case C: gen_kernel<kModeEmit, C><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        default: gen_kernel<kModeEmit, S | C><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+        }
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -2380,12 +2481,13 @@ cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm)
 {
     const int g = gen_smem_max();
     cudaError_t e;
-    const void *gens[] = {(const void *)gen_kernel<kModeClassCount, true>,
-                          (const void *)gen_kernel<kModeBetaCount, true>,
-                          (const void *)gen_kernel<kModeTileCount, false>,
-                          (const void *)gen_kernel<kModeTileCount, true>,
-                          (const void *)gen_kernel<kModeEmit, false>,
-                          (const void *)gen_kernel<kModeEmit, true>,
+    constexpr int S = kFiltSym, C = kFiltCut;
+    const void *gens[] = {(const void *)gen_kernel<kModeClassCount, S>, (const void *)gen_kernel<kModeClassCount, S | C>,
+                          (const void *)gen_kernel<kModeBetaCount, S>,  (const void *)gen_kernel<kModeBetaCount, S | C>,
+                          (const void *)gen_kernel<kModeTileCount, 0>,  (const void *)gen_kernel<kModeTileCount, S>,
+                          (const void *)gen_kernel<kModeTileCount, C>,  (const void *)gen_kernel<kModeTileCount, S | C>,
+                          (const void *)gen_kernel<kModeEmit, 0>,       (const void *)gen_kernel<kModeEmit, S>,
+                          (const void *)gen_kernel<kModeEmit, C>,       (const void *)gen_kernel<kModeEmit, S | C>,
                           (const void *)gen_kernel_one<kModeDetTerms>};
     for (const void *f : gens)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;

@@ -47,7 +47,7 @@ class Pt2Error(RuntimeError):
 class pt2_opts(ctypes.Structure):
     _fields_ = [("constraint_mod", ctypes.c_uint64), ("constraint_rem", ctypes.c_uint64),
                 ("pass_budget_bytes", ctypes.c_uint64), ("tile_target", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("numerator_cutoff", ctypes.c_double)]
 
 
 class pt2_result(ctypes.Structure):
@@ -121,13 +121,14 @@ def _check(ctx, rc):
 
 
 def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False,
-              spin_symmetric=False) -> pt2_opts:
+              spin_symmetric=False, cutoff=0.0) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
     o.tile_target = int(tile_target)
     o.flags = ((PT2_FLAG_PROFILE if profile else 0) | (PT2_FLAG_AUTOTUNE if autotune else 0) |
                (PT2_FLAG_SPIN_SYMMETRIC if spin_symmetric else 0))
+    o.numerator_cutoff = float(cutoff)
     return o
 
 

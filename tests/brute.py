@@ -88,16 +88,26 @@ def rank(d1, d2) -> int:
     return (bin(d1[0] ^ d2[0]).count("1") + bin(d1[1] ^ d2[1]).count("1")) // 2
 
 
-def pt2(h, eri, dets, H, ref_idx, coef, e0):
-    """E2, the connected external set (sorted keys) and its numerators and diagonals."""
+def pt2(h, eri, dets, H, ref_idx, coef, e0, cutoff=0.0):
+    """E2, the connected external set (sorted keys) and its numerators and diagonals.
+
+    With a cutoff, a contribution H_ai c_i of a connected reference
+    determinant counts only if |H_ai c_i| >= cutoff, and a determinant
+    belongs to the set only if one of its contributions counts."""
     ref_idx = list(ref_idx)
     refset = set(ref_idx)
-    hc = H[:, ref_idx] @ np.asarray(coef)
+    coef = np.asarray(coef)
+    hc = H[:, ref_idx] @ coef
+    contrib = H[:, ref_idx] * coef[None, :]
     ext = []
     for k, d in enumerate(dets):
         if k in refset:
             continue
-        if any(rank(d, dets[i]) in (1, 2) for i in ref_idx):
+        conn = [j for j, i in enumerate(ref_idx) if rank(d, dets[i]) in (1, 2)]
+        if cutoff > 0:
+            conn = [j for j in conn if abs(contrib[k, j]) >= cutoff]
+            hc[k] = sum(contrib[k, j] for j in conn)
+        if conn:
             ext.append(k)
     ext.sort(key=lambda k: (dets[k][0], dets[k][1]))
     e2 = sum(hc[k] ** 2 / (e0 - H[k, k]) for k in ext)

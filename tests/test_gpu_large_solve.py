@@ -65,3 +65,21 @@ def test_sampled_constraint_class_matches_oracle(large, cls):
     assert (got["digest_sum"], got["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
     assert got["n_pos_denom"] == ref["n_pos_denom"]
     assert abs(got["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
+
+
+def test_paper_cutoff_at_full_size(large):
+    # the paper's 1e-8 cutoff on the full workload: fewer kept contributions,
+    # and a sampled constraint class against the oracle with the same cutoff
+    c, s, r, e0, rid = large["c"], large["s"], large["r"], large["e0"], large["rid"]
+    cut = 1e-8
+    exact = c.run(rid)
+    got = c.run(rid, cutoff=cut)
+    assert got["n_terms"] < exact["n_terms"]
+    assert got["n_unique"] == got["n_in_ref"] + got["n_external"]
+    assert c.run(rid, cutoff=cut)["e2"] == got["e2"]
+    cls = (49999, 7)
+    gc = c.run(rid, constraint=cls, cutoff=cut)
+    ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, constraint=cls, cutoff=cut)
+    for k in ("n_terms", "n_external", "n_in_ref", "digest_sum", "digest_xor", "n_pos_denom"):
+        assert gc[k] == ref[k], k
+    assert abs(gc["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))

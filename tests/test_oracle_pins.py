@@ -101,6 +101,31 @@ def test_oracle_matches_brute_force(brute_cases):
         assert abs(res["e2"] - bf["e2"]) <= 1e-12 * max(1.0, abs(bf["e2"]))
 
 
+def test_numerator_cutoff_matches_brute_force(brute_cases):
+    # the cutoff of the Results section: contributions |c_i H_ai| below it are
+    # ignored; with the cutoff at the median contribution about half go, and
+    # whole determinants leave the set when all of theirs do
+    for c in brute_cases:
+        keys = keys_of(c["ref"])
+        ref_idx = c["ref_idx"]
+        contrib = np.abs(c["H"][:, ref_idx] * c["coef"][None, :])
+        conn = np.array([[brute.rank(d, c["dets"][i]) in (1, 2) for i in ref_idx] for d in c["dets"]])
+        cut = float(np.median(contrib[conn]))
+        bf = brute.pt2(c["h"], c["eri"], c["dets"], c["H"], ref_idx, c["coef"], c["e0"], cutoff=cut)
+        full = brute.pt2(c["h"], c["eri"], c["dets"], c["H"], ref_idx, c["coef"], c["e0"])
+        k, num, haa, res = oracle.dump_external(c["h"], c["eri"], keys, c["coef"], c["e0"], cutoff=cut)
+        assert np.array_equal(k, bf["keys"])
+        np.testing.assert_allclose(num, bf["num"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(haa, bf["haa"], rtol=0, atol=1e-12)
+        assert abs(res["e2"] - bf["e2"]) <= 1e-12 * max(1.0, abs(bf["e2"]))
+        assert len(bf["keys"]) <= len(full["keys"]) and bf["e2"] != full["e2"]
+        # kept contributions: the connected pairs at or above the cutoff (terms
+        # landing on reference determinants included)
+        assert res["n_terms"] == int((contrib[conn] >= cut).sum())
+        assert oracle.pt2(c["h"], c["eri"], keys, c["coef"], c["e0"], cutoff=0.0) == \
+            oracle.pt2(c["h"], c["eri"], keys, c["coef"], c["e0"])
+
+
 def test_oracle_diagonal_matches_brute_force(brute_cases):
     for c in brute_cases:
         keys = keys_of(c["dets"])
