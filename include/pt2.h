@@ -134,6 +134,15 @@ typedef struct {
  * min_abs_denom and n_pos_denom then describe the kept half (alpha' >= beta').
  * PT2_ERR_INVALID if the reference is not symmetric. */
 #define PT2_FLAG_SPIN_SYMMETRIC 4u
+/* Duplicate subtraction (the section on removing duplicate contributions):
+ * instead of filtering the reference determinants out of the external set,
+ * keep them in the sum and subtract sum_i c_i^2 (E0 - H_ii) over the reference
+ * determinants of the constraint class.  Equal to the filtered E2 when c is an
+ * eigenvector of H in the reference space with eigenvalue E0 (the E0 given to
+ * pt2_load_reference); otherwise it differs by the eigenvector residual.
+ * n_in_ref is then 0 and n_external, the digest, min_abs_denom and
+ * n_pos_denom cover every generated key, reference keys included. */
+#define PT2_FLAG_SUBTRACT_REF 8u
 
 typedef struct {
     double e2;                /* the PT2 energy, Hartree */

@@ -149,6 +149,7 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.heavy_class = 0;
     p.sym = 0;
     p.cutoff = 0.0;
+    p.subtract = 0;
     p.cons_mod = 1;
     p.err = (uint32_t *)c->err_word.ptr;
     return p;

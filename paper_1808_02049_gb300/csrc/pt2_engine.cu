@@ -80,6 +80,7 @@ int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)
     if (!(j.o.numerator_cutoff >= 0.0) || std::isinf(j.o.numerator_cutoff))
         return fail(c, PT2_ERR_INVALID, "numerator_cutoff must be finite and non-negative");
     j.gp.cutoff = j.o.numerator_cutoff;
+    j.gp.subtract = (j.o.flags & PT2_FLAG_SUBTRACT_REF) ? 1u : 0u;
     return PT2_OK;
 }
 
@@ -106,6 +107,18 @@ cudaError_t gen_launch(pt2_ctx *c, GenMode mode, GenBatch b, uint64_t n_ctas, in
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Duplicate subtraction of a job (none unless requested): after its
+// accumulator is initialised, subtract its reference determinants' c_i^2 (E0 - H_ii).
+cudaError_t job_subtract(pt2_ctx *c, const Job &j, RunAcc *acc, cudaStream_t st)
+{
+    if (!j.gp.subtract) return cudaSuccess;
+    c->launches++;
+    return launch_ref_subtract(reinterpret_cast<const uint64_t *>(j.r->keys.ptr),
+                               reinterpret_cast<const double *>(j.r->coef.ptr),
+                               reinterpret_cast<const double *>(j.r->hii.ptr), j.r->n_det, j.r->e0, j.gp.cons_mod,
+                               j.gp.cons_rem, acc, reinterpret_cast<uint32_t *>(c->err_word.ptr), st);
 }
 
 // Checks a job's generator launches need (kFiltSym | kFiltCut).
@@ -523,6 +536,7 @@ int run_single(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, pt2_result *ou
     if ((rc = upload_steps(c, steps, c->steps))) return rc;
     CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, st), "memset");
     CK(launch_acc_init(j.acc, 1, st), "acc init");
+    CK(job_subtract(c, j, j.acc, st), "duplicate subtraction");
     StepDev *d = reinterpret_cast<StepDev *>(c->steps.ptr);
     for (size_t k = 0; k < steps.size(); ++k)
         if ((rc = enqueue_step(c, steps[k], d + k, dump, prof))) return rc;
@@ -588,6 +602,8 @@ int capture_batch(pt2_ctx *c, Batch &b)
     int n = (int)b.jobs.size();
     cudaError_t e = cudaMemsetAsync(c->err_word.ptr, 0, 4, st);
     if (e == cudaSuccess) e = launch_acc_init(reinterpret_cast<RunAcc *>(b.acc.ptr), n, st);
+    for (int i = 0; e == cudaSuccess && i < n; ++i)
+        e = job_subtract(c, *b.jobs[i], reinterpret_cast<RunAcc *>(b.acc.ptr) + i, st);
     StepDev *d = reinterpret_cast<StepDev *>(b.tables.ptr);
     for (size_t k = 0; e == cudaSuccess && k < b.steps.size(); ++k)
         if (enqueue_step(c, b.steps[k], d + k, nullptr, false) != PT2_OK) e = cudaErrorUnknown;
@@ -672,7 +688,9 @@ void server_iteration(pt2_ctx *c)
         for (Job *j : admit) j->t_admit = now_s();
         if (rc == PT2_OK)
             for (Job *j : admit)
-                if (launch_acc_init(j->acc, 1, c->stream) != cudaSuccess) rc = PT2_ERR_CUDA;
+                if (launch_acc_init(j->acc, 1, c->stream) != cudaSuccess ||
+                    job_subtract(c, *j, j->acc, c->stream) != cudaSuccess)
+                    rc = PT2_ERR_CUDA;
         std::lock_guard<std::mutex> lk(S.mu);
         if (rc != PT2_OK) {
             server_fail_jobs(c, admit, rc);
@@ -884,6 +902,8 @@ int pt2_batch_run(pt2_ctx *c, uint32_t batch_id, pt2_result *results)
         c->launches = 0;
         CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, st), "memset");
         CK(launch_acc_init(reinterpret_cast<RunAcc *>(b.acc.ptr), (int)n, st), "acc init");
+        for (size_t i = 0; i < n; ++i)
+            CK(job_subtract(c, *b.jobs[i], reinterpret_cast<RunAcc *>(b.acc.ptr) + i, st), "duplicate subtraction");
         StepDev *d = reinterpret_cast<StepDev *>(b.tables.ptr);
         for (size_t k = 0; k < b.steps.size(); ++k)
             if ((rc = enqueue_step(c, b.steps[k], d + k, nullptr, true))) return rc;

@@ -109,6 +109,7 @@ struct GenParams {
     uint32_t heavy_class;         // beta-count mode: the alpha class whose beta classes are counted
     uint32_t sym;                 // spin-flip symmetric run: only terms with alpha' >= beta'
     double cutoff;                // numerator cutoff: contributions |c_i H_ai| below it are dropped (0: none)
+    uint32_t subtract;            // duplicate subtraction: reference keys stay in the sum (no reference slices)
     uint64_t cons_mod, cons_rem;  // alpha % mod == rem (mod <= 1: none)
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance
@@ -219,6 +220,9 @@ cudaError_t launch_pass_finish(const unsigned long long *tile_off, const unsigne
                                const unsigned long long *expected, RunAcc *const *acc, unsigned int *n_big,
                                uint32_t *err, cudaStream_t s);
 cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s);
+// acc.E2 -= sum over the reference determinants of the constraint class of c_i^2 (E0 - H_ii), exactly
+cudaError_t launch_ref_subtract(const uint64_t *keys, const double *coef, const double *hii, uint64_t n, double e0,
+                                uint64_t cons_mod, uint64_t cons_rem, RunAcc *acc, uint32_t *err, cudaStream_t s);
 cudaError_t launch_acc_finalize(RunAcc *acc, int n, cudaStream_t s);
 cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm);  // once per process and device, before any capture
 size_t tile_smem_bytes();

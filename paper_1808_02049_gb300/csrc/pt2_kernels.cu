@@ -1370,7 +1370,8 @@ __global__ void ref_tile_kernel(const RefPartParams p)
     }
     const uint32_t cl = class_of(zc), bc = bclass_of(zcb);
     uint32_t t = 0xFFFFFFFFu;
-    if (cl >= q.class_lo && cl < q.class_hi && bc >= q.bclass_lo && bc < q.bclass_hi &&
+    // a run with duplicate subtraction keeps the reference keys in the sum
+    if (!q.subtract && cl >= q.class_lo && cl < q.class_hi && bc >= q.bclass_lo && bc < q.bclass_hi &&
         cons_ok(q.cons_mod, q.cons_rem, A)) {
         t = (uint32_t)(q.tile_base + __umul64hi(zt, q.n_tiles));
         atomicAdd(&p.ref_count[t], 1u);
@@ -2385,6 +2386,66 @@ __global__ void acc_init_kernel(RunAcc *acc, int n)
 cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s)
 {
     acc_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(acc, n);
+    return cudaGetLastError();
+}
+
+// Duplicate subtraction (the section on removing duplicate contributions):
+// when the reference keys are left in the sum, a reference determinant i of
+// the constraint class receives the numerator (H c)_i - H_ii c_i, which is
+// c_i (E0 - H_ii) if c is an eigenvector of H in the reference space with
+// eigenvalue E0, so its PT2-like term is c_i^2 (E0 - H_ii).  That amount is
+// subtracted here in the same exact fixed point as the sum.
+__global__ void __launch_bounds__(256) ref_subtract_kernel(const uint64_t *__restrict__ keys,
+                                                           const double *__restrict__ coef,
+                                                           const double *__restrict__ hii, uint64_t n, double e0,
+                                                           uint64_t cons_mod, uint64_t cons_rem, RunAcc *acc,
+                                                           uint32_t *err)
+{
+    uint64_t lo = 0;
+    int64_t hi = 0;
+    uint32_t er = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!cons_ok(cons_mod, cons_rem, keys[2 * i])) continue;
+        const double c = coef[i];
+        fx_add_double(lo, hi, -((c * c) * (e0 - hii[i])), er);
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+        const int64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+        fx_add_fx(lo, hi, olo, ohi);
+        er |= __shfl_down_sync(0xffffffffu, er, off);
+    }
+    __shared__ unsigned long long red[2][8];
+    __shared__ uint32_t rer[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = lo;
+        red[1][warp] = (unsigned long long)hi;
+        rer[warp] = er;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t blo = 0;
+        int64_t bhi = 0;
+        uint32_t ber = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            fx_add_fx(blo, bhi, red[0][w], (int64_t)red[1][w]);
+            ber |= rer[w];
+        }
+        const unsigned long long old = atomicAdd(&acc->e2_lo, (unsigned long long)blo);
+        const unsigned long long carry = (old + blo) < old ? 1ull : 0ull;
+        atomicAdd((unsigned long long *)&acc->e2_hi, (unsigned long long)bhi + carry);
+        if (ber) atomicOr(err, ber);
+    }
+}
+
+cudaError_t launch_ref_subtract(const uint64_t *keys, const double *coef, const double *hii, uint64_t n, double e0,
+                                uint64_t cons_mod, uint64_t cons_rem, RunAcc *acc, uint32_t *err, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216;
+    ref_subtract_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, coef, hii, n, e0, cons_mod, cons_rem, acc, err);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ PT2_ERR_UNSUPPORTED = -7
 PT2_FLAG_PROFILE = 1
 PT2_FLAG_AUTOTUNE = 2
 PT2_FLAG_SPIN_SYMMETRIC = 4
+PT2_FLAG_SUBTRACT_REF = 8
 
 EXPORTS = ["pt2_create", "pt2_destroy", "pt2_last_error", "pt2_load_system", "pt2_load_reference",
            "pt2_unload", "pt2_diagonal", "pt2_run", "pt2_dump_external", "pt2_batch_create", "pt2_batch_run",
@@ -121,13 +122,14 @@ def _check(ctx, rc):
 
 
 def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False,
-              spin_symmetric=False, cutoff=0.0) -> pt2_opts:
+              spin_symmetric=False, cutoff=0.0, subtract_ref=False) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
     o.tile_target = int(tile_target)
     o.flags = ((PT2_FLAG_PROFILE if profile else 0) | (PT2_FLAG_AUTOTUNE if autotune else 0) |
-               (PT2_FLAG_SPIN_SYMMETRIC if spin_symmetric else 0))
+               (PT2_FLAG_SPIN_SYMMETRIC if spin_symmetric else 0) |
+               (PT2_FLAG_SUBTRACT_REF if subtract_ref else 0))
     o.numerator_cutoff = float(cutoff)
     return o
 
