@@ -161,7 +161,10 @@ def bench_cutoff(ctx, rid, cut=1e-8, reps=2):
             best = dt if best is None or dt < best else best
         out[name] = (res, best)
     (ex, te), (ct, tc) = out["exact"], out["cutoff"]
+    ctx.run(rid, cutoff=cut, profile=True)
+    ph, _ = ctx.phase_times()
     return {"cutoff": cut, "ms_exact": te * 1e3, "ms_cutoff": tc * 1e3, "speedup": te / tc,
+            "phase_ms_cutoff": {k: round(v, 3) for k, v in ph.items()},
             "terms_exact": ex["n_terms"], "terms_kept": ct["n_terms"], "kept_fraction": ct["n_terms"] / ex["n_terms"],
             "external_exact": ex["n_external"], "external_kept": ct["n_external"],
             "e2_exact": ex["e2"], "e2_cutoff": ct["e2"], "delta_e2": ct["e2"] - ex["e2"]}
@@ -319,10 +322,10 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 began a1350b82
-    "kernels_sha256": "b7ffa4cd94fd8ded7c0b90a68e9148e5815518f1dd33dee07447b216da946d0d",
-    "tile_kernel": (4.134259e9 + 4.805376e6) / 129_750_000,        # 31.90 B per term
-    "gen_kernel<Emit>": (0.16580736e9 + 4.10613e9) / 129_750_000,  # 32.92 B per term
+    # code hash (kernel_code_sha256) of the captured source; its file sha256 began ecffd826
+    "kernels_sha256": "d62cf165b13840a8982943793b43bbfd265443393b954df1d762b4e602830719",
+    "tile_kernel": (4.13362e9 + 5.024256e6) / 129_750_000,        # 31.90 B per term
+    "gen_kernel<Emit>": (0.165389312e9 + 4.105932e9) / 129_750_000,  # 32.92 B per term
 }
 
 

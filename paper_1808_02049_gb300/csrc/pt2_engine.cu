@@ -121,6 +121,13 @@ cudaError_t job_subtract(pt2_ctx *c, const Job &j, RunAcc *acc, cudaStream_t st)
                                j.gp.cons_rem, acc, reinterpret_cast<uint32_t *>(c->err_word.ptr), st);
 }
 
+// Whether a job generated the terms its plan counted: exactly, or at most
+// the plan's count for a run with a numerator cutoff (planned from all terms).
+bool terms_as_planned(const Job &j, uint64_t n_terms)
+{
+    return j.gp.cutoff > 0.0 ? n_terms <= j.total : n_terms == j.total;
+}
+
 // Checks a job's generator launches need (kFiltSym | kFiltCut).
 int job_filt(const Job &j) { return (j.gp.sym ? kFiltSym : 0) | (j.gp.cutoff > 0.0 ? kFiltCut : 0); }
 
@@ -359,7 +366,7 @@ void fill_step(pt2_ctx *c, const StepPlan &sp, StepDev &h)
         h.tile_base[i] = tb;
         h.e0[i] = j.r->e0;
         h.sym[i] = j.gp.sym;
-        h.expected[i] = P.records;
+        h.expected[i] = P.records | (j.gp.cutoff > 0.0 ? kExpectAtMost : 0ull);
         h.acc[i] = j.acc;
         h.n_big[i] = 0;
         cta += j.r->n_det;
@@ -553,7 +560,7 @@ int run_single(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, pt2_result *ou
     if ((rc = status_of_err(c, err | h.err))) return rc;
     result_of(h, j, out);
     out->seconds = ms * 1e-3;
-    if (h.n_terms != j.total)
+    if (!terms_as_planned(j, h.n_terms))
         return fail(c, PT2_ERR_CUDA, "generated %llu terms, planned %llu", (unsigned long long)h.n_terms,
                     (unsigned long long)j.total);
     if (dump) {
@@ -754,7 +761,7 @@ void server_iteration(pt2_ctx *c)
         result_of(h[i], *j, &j->result);
         j->t_done = t;
         j->result.seconds = t - j->t_submit;
-        j->status = h[i].n_terms == j->total ? PT2_OK : PT2_ERR_CUDA;
+        j->status = terms_as_planned(*j, h[i].n_terms) ? PT2_OK : PT2_ERR_CUDA;
         j->r->busy--;
         S.free_slots.push_back((int)(j->acc - reinterpret_cast<RunAcc *>(S.acc_pool.ptr)));
         S.active.erase(std::find(S.active.begin(), S.active.end(), j));
@@ -921,7 +928,7 @@ int pt2_batch_run(pt2_ctx *c, uint32_t batch_id, pt2_result *results)
     for (size_t i = 0; i < n; ++i) {
         result_of(h[i], *b.jobs[i], &results[i]);
         results[i].seconds = ms * 1e-3;  // the whole batch
-        if (h[i].n_terms != b.jobs[i]->total)
+        if (!terms_as_planned(*b.jobs[i], h[i].n_terms))
             return fail(c, PT2_ERR_CUDA, "instance %zu generated %llu terms, planned %llu", i,
                         (unsigned long long)h[i].n_terms, (unsigned long long)b.jobs[i]->total);
     }
