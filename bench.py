@@ -322,7 +322,7 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 began ecffd826
+    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began ecffd826
     "kernels_sha256": "d62cf165b13840a8982943793b43bbfd265443393b954df1d762b4e602830719",
     "tile_kernel": (4.13362e9 + 5.024256e6) / 129_750_000,        # 31.90 B per term
     "gen_kernel<Emit>": (0.165389312e9 + 4.105932e9) / 129_750_000,  # 32.92 B per term

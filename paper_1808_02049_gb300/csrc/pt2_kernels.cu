@@ -22,6 +22,14 @@
 //     big tile        tiles larger than shared memory, in chunks reduced to
 //                     exact partials
 //
+// Run options, as template variants launched only where a step needs them
+// (ordinary runs keep their registers): a spin-flip symmetric run keeps only
+// terms with alpha' >= beta' and counts alpha' > beta' twice (the Z2
+// subsection); the numerator cutoff drops contributions |c_i H_ai| below it in
+// the tile count and the emission (the matrix-element cutoff subsection);
+// duplicate subtraction leaves the reference keys in the sum and subtracts
+// c_i^2 (E0 - H_ii) per reference determinant (ref_subtract_kernel).
+//
 // FP64 is the scarce unit on this GPU, so every quantity with a natural exact
 // integer form is kept as one: the diagonal difference (int64, 2^-48 Ha), the
 // per-key numerator sum and the energy sum (int128, 2^-90).  FP64 is used for
