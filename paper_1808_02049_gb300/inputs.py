@@ -147,6 +147,8 @@ def make_reference(n_orb: int, n_elec_per_spin: int, n_det: int, max_level: int,
     n = int(n_elec_per_spin)
     if not (0 < n < n_orb <= 64):
         raise ValueError("need 0 < n_elec_per_spin < n_orb <= 64")
+    if n_det > _count_within(n_orb, n, max_level):
+        raise ValueError("n_det exceeds the determinants within max_level of HF")
     rng = np.random.Generator(np.random.PCG64(seed))
     hf = np.uint64((1 << n) - 1)
     alphas = [np.array([hf], dtype=np.uint64)]
@@ -201,6 +203,10 @@ def make_symmetric_reference(n_orb: int, n_elec_per_spin: int, n_det: int, max_l
     n = int(n_elec_per_spin)
     if not (0 < n < n_orb <= 64):
         raise ValueError("need 0 < n_elec_per_spin < n_orb <= 64")
+    if n_det > _count_within(n_orb, n, max_level):
+        raise ValueError("n_det exceeds the determinants within max_level of HF")
+    if n_det % 2 == 0 and max_level < 2:
+        raise ValueError("an even n_det needs a second self-mirrored determinant (max_level >= 2)")
     rng = np.random.Generator(np.random.PCG64(seed))
     hf = (1 << n) - 1
     pairs = [(hf, hf)]

@@ -52,3 +52,26 @@ def test_create_without_gpu_reports_an_error(lib):
         pt2.pt2_create(0)
     assert e.value.code in (pt2.PT2_ERR_CUDA, pt2.PT2_ERR_INVALID)
     assert pt2.pt2_last_error(None)
+
+
+@pytest.mark.parametrize("struct", [pt2.pt2_opts, pt2.pt2_result])
+def test_binding_structs_match_the_header_layout(struct, tmp_path):
+    # the C compiler's size and field offsets of each struct the binding
+    # mirrors, against ctypes' (a field added on one side only fails here)
+    name = struct.__name__
+    fields = [f for f, _ in struct._fields_]
+    src = tmp_path / "layout.c"
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pt2.h"', "int main(void) {",
+             f'    printf("size %zu\\n", sizeof({name}));']
+    lines += [f'    printf("{f} %zu\\n", offsetof({name}, {f}));' for f in fields]
+    lines += ["    return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                     check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(struct)
+    for f in fields:
+        assert int(out[f]) == getattr(struct, f).offset, f
