@@ -6,7 +6,9 @@
   determinant (all singles and doubles, structural);
 * the duplicate-removal identity of the paper (subtracting c_i^2 (E - H_ii)
   from the unfiltered sum gives the filtered one when c is an eigenvector of
-  H in the reference space);
+  H in the reference space), for the whole sum and per constraint class;
+* the numerator cutoff against brute force (contributions filtered column by
+  column in the dense H), and its constraint classes partitioning the sum;
 * invariants: c -> 2c scales E2 by exactly 4; swapping alpha and beta words of
   every determinant leaves E2 unchanged; reordering the reference leaves E2
   unchanged; the constraint classes alpha % m = r partition the sum
@@ -205,6 +207,46 @@ def test_subtraction_identity_eigenvector_reference():
         sub_reached = sub - float(np.sum(c[unreached] ** 2 * (e0 - hii[unreached])))
         unfiltered = res["e2"] + res["e2_ref_like"]
         assert abs((unfiltered - sub_reached) - res["e2"]) < 1e-11
+
+
+def test_subtraction_identity_per_constraint_class():
+    # the identity holds key by key, so it holds in every constraint class:
+    # the class's unfiltered sum minus c_i^2 (E0 - H_ii) over the reference
+    # determinants of the class equals the class's filtered E2
+    for seed, (n_orb, n, n_ref) in enumerate([(6, 2, 14), (6, 3, 12)]):
+        h, eri = strong_integrals(n_orb, 60 + seed)
+        dets = brute.basis(n_orb, n, n)
+        rng = np.random.default_rng(70 + seed)
+        ref = [dets[i] for i in sorted(rng.choice(len(dets), n_ref, replace=False))]
+        keys = keys_of(ref)
+        H = brute.hamiltonian(h, eri, dets)
+        idx = {d: k for k, d in enumerate(dets)}
+        ri = [idx[d] for d in ref]
+        w, V = np.linalg.eigh(H[np.ix_(ri, ri)])
+        c, e0 = V[:, 0], w[0]
+        hii = oracle.diagonals(h, eri, keys)
+        reached = set()
+        for d in ref:
+            kk, _, _ = oracle.det_terms(h, eri, d[0], d[1], 1.0)
+            reached |= {(a, b) for a, b in kk.tolist()}
+        for m, r in [(3, 0), (3, 1), (3, 2)]:
+            res = oracle.pt2(h, eri, keys, c, e0, constraint=(m, r), include_ref=True)
+            sub = sum(c[i] ** 2 * (e0 - hii[i]) for i, d in enumerate(ref) if d[0] % m == r and d in reached)
+            assert abs(res["e2"] + res["e2_ref_like"] - sub - res["e2"]) < 1e-11
+
+
+def test_cutoff_constraint_classes_partition_the_sum():
+    s = inputs.make_integrals(12, inputs.workload_seed(8))
+    r = inputs.make_reference(12, 3, 200, 3, inputs.workload_seed(8) + 1)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    cut = 1e-4
+    full = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, cutoff=cut)
+    exact = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
+    assert full["n_terms"] < exact["n_terms"]
+    parts = [oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, cutoff=cut, constraint=(4, k)) for k in range(4)]
+    assert sum(p["n_terms"] for p in parts) == full["n_terms"]
+    assert sum(p["n_external"] for p in parts) == full["n_external"]
+    assert abs(sum(p["e2"] for p in parts) - full["e2"]) < 1e-12 * abs(full["e2"])
 
 
 def test_scaling_swap_permutation_invariants():
