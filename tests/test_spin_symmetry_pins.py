@@ -97,3 +97,20 @@ def test_symmetric_reference_generator_and_oracle_mirrors():
     w2 = mirror_check(k2, num2, haa2)
     assert w2 is None or w2 > 1e-6
     assert abs(halves(k2, num2, haa2, e0) - res2["e2"]) > 1e-9 * abs(res2["e2"])
+
+
+def test_reference_generators_are_seeded_and_refuse_impossible_sizes():
+    import pytest
+
+    a = inputs.make_symmetric_reference(12, 3, 101, 3, 5)
+    b = inputs.make_symmetric_reference(12, 3, 101, 3, 5)
+    assert np.array_equal(a.keys, b.keys) and np.array_equal(a.coef, b.coef)
+    # an even size needs one self-mirrored determinant besides Hartree-Fock
+    c = inputs.make_symmetric_reference(12, 3, 100, 3, 5)
+    assert int(np.sum(c.keys[0::2] == c.keys[1::2])) == 2
+    with pytest.raises(ValueError):
+        inputs.make_reference(6, 2, 10 ** 6, 2, 1)
+    with pytest.raises(ValueError):
+        inputs.make_symmetric_reference(6, 2, 10 ** 6, 2, 1)
+    with pytest.raises(ValueError):
+        inputs.make_symmetric_reference(12, 3, 100, 1, 1)
