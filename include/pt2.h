@@ -120,6 +120,8 @@ typedef struct {
                                    the external set.  n_terms counts the kept
                                    contributions.  PT2_ERR_INVALID if negative
                                    or not finite. */
+    uint32_t debug_flags;       /* PT2_DEBUG_* test aids below; 0 in normal use */
+    uint32_t reserved;          /* must be 0 */
 } pt2_opts;
 
 #define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times); a batch created
@@ -144,6 +146,21 @@ typedef struct {
  * n_pos_denom cover every generated key, reference keys included. */
 #define PT2_FLAG_SUBTRACT_REF 8u
 
+/* Test aids (pt2_opts.debug_flags).  They exercise paths that ordinary inputs
+ * reach only rarely; neither changes a result.
+ * PT2_DEBUG_NARROW_SORT_HASH: the 32-bit hash that orders the records of a
+ *   tile keeps only 4 bits, so most keys of a tile share their hash and their
+ *   bucket: the grouping tells them apart by the full 128-bit comparison and
+ *   hands long buckets to its warp path.  Slower; E2, counts and the external
+ *   set are those of an ordinary run (pt2_result.n_hash_collisions counts the
+ *   comparisons that met different keys with equal hashes).
+ * PT2_DEBUG_SHORT_COPY_WAIT: the tile kernels give up waiting for a tile's
+ *   bulk copy after 64 SM cycles instead of about a second.  The copy still
+ *   lands (a second bounded wait), the CTA stops, and the run returns
+ *   PT2_ERR_TIMEOUT; the context stays usable. */
+#define PT2_DEBUG_NARROW_SORT_HASH 1u
+#define PT2_DEBUG_SHORT_COPY_WAIT 2u
+
 typedef struct {
     double e2;                /* the PT2 energy, Hartree */
     uint64_t n_terms;         /* generated (key, H_ai c_i) pairs */
@@ -157,7 +174,8 @@ typedef struct {
     uint32_t n_passes;        /* memory-bounded passes used */
     uint32_t n_tiles;         /* hash tiles over all passes */
     uint32_t n_oversize;      /* tiles handled by the chunked path */
-    uint32_t reserved;
+    uint32_t n_hash_collisions; /* comparisons inside a tile that met two different keys with
+                                   the same 32-bit sort hash (saturates at 2^32 - 1) */
     double seconds;           /* device time of the run (CUDA events) */
 } pt2_result;
 
@@ -259,9 +277,25 @@ int pt2_det_terms(pt2_ctx *ctx, uint32_t ref_id, uint64_t det_index, uint64_t *k
  * array's device address; make that first call before any stream capture.
  * All calls share the array and clear its counter when they start, so calls
  * whose GPU work overlaps (several threads or contexts) race and must be
- * serialised by the caller.  Blocking: returns after the terms are written. */
+ * serialised by the caller.  The call writes keys, val and haa on the
+ * context's stream (pt2_stream): work the caller has queued on its own
+ * streams that reads or writes these buffers must be finished, or ordered
+ * before the call (for example by synchronising), when the call is made.
+ * A device error of the generation is reported like pt2_run's (the
+ * context's error word is cleared first and read after).
+ * Blocking: returns after the terms are written. */
 int pt2_det_terms_noalloc(pt2_ctx *ctx, uint32_t ref_id, uint64_t det_index, uint64_t *keys, double *val,
                           double *haa, uint64_t cap, uint64_t *n_out);
+
+/* The per-key term of Eq. 3, num^2 / (E0 - H_aa), evaluated with the device
+ * arithmetic of the tile kernels: the denominator rounded to the library's
+ * fixed point (multiples of 2^-48 Ha), its reciprocal taken from the
+ * single-precision hardware estimate refined by one Newton-Raphson step in
+ * FP64 (relative error below 2^-44), FP64 products.  num and denom (E0 - H_aa
+ * in Hartree) are n host doubles each, term receives n doubles.  Every entry
+ * must be finite with 0 < |denom| < 2^15 Ha after rounding (PT2_ERR_INVALID
+ * otherwise).  Parity aid: tests bound this arithmetic against exact values. */
+int pt2_eval_terms(pt2_ctx *ctx, uint64_t n, const double *num, const double *denom, double *term);
 
 /* Per-phase device milliseconds of the last run made with PT2_FLAG_PROFILE:
  * out[0] class count, [1] tile count, [2] scan, [3] generate/emit,

@@ -402,9 +402,11 @@ int pt2_load_reference(pt2_ctx *c, uint32_t system_id, uint64_t n_det, const uin
     CK(cudaMemcpyAsync(r->coef.ptr, coef, n_det * 8, cudaMemcpyHostToDevice, c->stream), "copy coef");
     CK(launch_diag(sys_dev(s), (const uint64_t *)r->keys.ptr, n_det, (double *)r->hii.ptr, c->stream),
        "diagonal kernel");
-    CK(launch_ref_d0((const double *)r->hii.ptr, n_det, e0, (int64_t *)r->d0.ptr, c->stream), "denominator kernel");
     CK(launch_ref_g(sys_dev(s), (const uint64_t *)r->keys.ptr, n_det, (int64_t *)r->g.ptr, c->stream),
        "orbital energy kernel");
+    CK(launch_ref_d0(sys_dev(s), (const uint64_t *)r->keys.ptr, (const int64_t *)r->g.ptr, n_det, e0,
+                     (int64_t *)r->d0.ptr, c->stream),
+       "denominator kernel");
     {
         // E0 - H_ii must lie inside the fixed-point range of the diagonal
         std::vector<double> hii(n_det);
@@ -483,13 +485,14 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
                   uint64_t cap, uint64_t *n_out)
 {
     if (!c) return PT2_ERR_INVALID;
+    // the lock comes first: pt2_unload frees references and systems under it
+    std::lock_guard<std::recursive_mutex> lock(c->exec);
     auto it = c->refs.find(ref_id);
     if (it == c->refs.end()) return fail(c, PT2_ERR_NOT_FOUND, "unknown reference id %u", ref_id);
     if (!n_out || (cap && (!keys || !val || !haa))) return fail(c, PT2_ERR_INVALID, "bad arguments");
     RefRes &r = *it->second;
     if (det_index >= r.n_det) return fail(c, PT2_ERR_INVALID, "determinant index out of range");
     SystemRes &s = *c->systems.at(r.system);
-    std::lock_guard<std::recursive_mutex> lock(c->exec);
     cudaSetDevice(c->device);
     const uint64_t T = terms_per_det(s.n, r.na, r.nb);
     int rc;
@@ -506,8 +509,11 @@ int pt2_det_terms(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint64_t *key
     CK(cudaMemsetAsync(c->cursor.ptr, 0, 4, c->stream), "memset");
     CK(launch_gen_single(kModeDetTerms, p, nullptr, nullptr, c->stream), "generator");
     unsigned int n32 = 0;
+    uint32_t err = 0;
     CK(cudaMemcpyAsync(&n32, c->cursor.ptr, 4, cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaMemcpyAsync(&err, c->err_word.ptr, 4, cudaMemcpyDeviceToHost, c->stream), "copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
+    if ((rc = status_of_err(c, err))) return rc;
     const unsigned long long n = n32;
     *n_out = n;
     if (n > cap) return fail(c, PT2_ERR_OOM, "determinant has %llu terms, above cap %llu", n, (unsigned long long)cap);
@@ -528,6 +534,8 @@ int pt2_det_terms_noalloc(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint6
                           double *haa, uint64_t cap, uint64_t *n_out)
 {
     if (!c) return PT2_ERR_INVALID;
+    // the lock comes first: pt2_unload frees references and systems under it
+    std::lock_guard<std::recursive_mutex> lock(c->exec);
     auto it = c->refs.find(ref_id);
     if (it == c->refs.end()) return fail(c, PT2_ERR_NOT_FOUND, "unknown reference id %u", ref_id);
     if (!n_out || (cap && (!keys || !val || !haa))) return fail(c, PT2_ERR_INVALID, "bad arguments");
@@ -539,14 +547,55 @@ int pt2_det_terms_noalloc(pt2_ctx *c, uint32_t ref_id, uint64_t det_index, uint6
         return fail(c, PT2_ERR_OOM,
                     "a determinant of this system has %llu terms, above the %llu the fixed device scratch holds",
                     (unsigned long long)T, (unsigned long long)kNoAllocMaxTerms);
-    std::lock_guard<std::recursive_mutex> lock(c->exec);
     cudaSetDevice(c->device);
     GenParams p = gen_params(c, s, r);
     p.det_begin = det_index;
     unsigned long long n = 0;
+    // the error word is context memory allocated at creation; clear it so
+    // that neither this call nor the next run sees a stale bit
+    CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, c->stream), "memset");
     CK(launch_det_terms_noalloc(c->device, p, cap, keys, val, haa, &n, c->stream), "allocation-free generation");
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&err, c->err_word.ptr, 4, cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    int rc;
+    if ((rc = status_of_err(c, err))) return rc;
     *n_out = n;
     if (n > cap) return fail(c, PT2_ERR_OOM, "determinant has %llu terms, above cap %llu", n, (unsigned long long)cap);
+    return PT2_OK;
+}
+
+int pt2_eval_terms(pt2_ctx *c, uint64_t n, const double *num, const double *denom, double *term)
+{
+    if (!c) return PT2_ERR_INVALID;
+    if (n == 0) return PT2_OK;
+    if (!num || !denom || !term) return fail(c, PT2_ERR_INVALID, "bad arguments");
+    for (uint64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(num[i]) || !std::isfinite(denom[i]) || !(std::fabs(denom[i]) < 32768.0) ||
+            std::llrint(denom[i] * kDenScale) == 0)
+            return fail(c, PT2_ERR_INVALID, "entry %llu: numerator or denominator out of range",
+                        (unsigned long long)i);
+    }
+    std::lock_guard<std::recursive_mutex> lock(c->exec);
+    cudaSetDevice(c->device);
+    DevBuf dn, dd, dt;
+    int rc;
+    if ((rc = dev_alloc(c, dn, n * 8, "numerators"))) return rc;
+    if ((rc = dev_alloc(c, dd, n * 8, "denominators")) || (rc = dev_alloc(c, dt, n * 8, "terms"))) {
+        dev_free(c, dn);
+        dev_free(c, dd);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(dn.ptr, num, n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd.ptr, denom, n * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_eval_terms((const double *)dn.ptr, (const double *)dd.ptr, n, (double *)dt.ptr, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(term, dt.ptr, n * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, dn);
+    dev_free(c, dd);
+    dev_free(c, dt);
+    if (e != cudaSuccess) return cuda_fail(c, e, "term evaluation");
     return PT2_OK;
 }
 

@@ -131,6 +131,13 @@ bool terms_as_planned(const Job &j, uint64_t n_terms)
 // Checks a job's generator launches need (kFiltSym | kFiltCut).
 int job_filt(const Job &j) { return (j.gp.sym ? kFiltSym : 0) | (j.gp.cutoff > 0.0 ? kFiltCut : 0); }
 
+// Options of a job's instance in the tile kernels.
+uint32_t job_iflags(const Job &j)
+{
+    return (j.gp.sym ? kInstSym : 0u) | ((j.o.debug_flags & PT2_DEBUG_NARROW_SORT_HASH) ? kInstNarrow : 0u) |
+           ((j.o.debug_flags & PT2_DEBUG_SHORT_COPY_WAIT) ? kInstShortWait : 0u);
+}
+
 // Terms per beta class among the terms of alpha class k of a job (one
 // beta-count launch over the job's determinants).
 int beta_counts(pt2_ctx *c, const Job &j, uint32_t k, std::vector<unsigned long long> &out)
@@ -365,7 +372,7 @@ void fill_step(pt2_ctx *c, const StepPlan &sp, StepDev &h)
         h.det_base[i] = cta;
         h.tile_base[i] = tb;
         h.e0[i] = j.r->e0;
-        h.sym[i] = j.gp.sym;
+        h.iflags[i] = job_iflags(j);
         h.expected[i] = P.records | (j.gp.cutoff > 0.0 ? kExpectAtMost : 0ull);
         h.acc[i] = j.acc;
         h.n_big[i] = 0;
@@ -439,7 +446,7 @@ int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *d
     tp.n_tiles = sp.n_tiles;
     tp.tile_base = d->tile_base;
     tp.e0 = d->e0;
-    tp.sym = d->sym;
+    tp.iflags = d->iflags;
     tp.sym_any = (gb.filt & kFiltSym) != 0;
     tp.acc = d->acc;
     tp.n_big = d->n_big;
@@ -491,6 +498,7 @@ void result_of(const RunAcc &h, const Job &j, pt2_result *out)
     for (const auto &p : j.passes) tiles += p.n_tiles;
     out->n_tiles = (uint32_t)std::min<uint64_t>(tiles, 0xFFFFFFFFull);
     out->n_oversize = h.n_big;
+    out->n_hash_collisions = (uint32_t)std::min<unsigned long long>(h.n_coll, 0xFFFFFFFFull);
 }
 
 // Upload the device tables of a list of steps (one pinned staging copy).

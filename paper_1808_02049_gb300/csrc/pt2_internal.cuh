@@ -13,9 +13,8 @@ constexpr int kClassBits = 12;               // alpha-hash classes used to form 
 constexpr int kNumClasses = 1 << kClassBits;
 constexpr int kGenThreads = 256;             // generator CTA
 constexpr int kGenBatch = 8;                 // terms whose slots a lane requests before storing any
-constexpr int kTileThreads = 256;            // tile sort-reduce CTA (1024 / kTileThreads per SM)
-constexpr int kTileCap = 1024;                // records a tile CTA sorts in shared memory
-constexpr int kSortCap = 1024;               // records one in-shared-memory sort handles
+constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per SM)
+constexpr int kTileCap = 1024;               // records a tile CTA sorts in shared memory
 constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)
 constexpr uint64_t kMaxTilesPerPass = 6400000;  // keeps the tile cursors (4 B each) resident in L2
 constexpr uint64_t kMaxPassBytes = 96ull << 30;  // bound on one pass's term records
@@ -29,8 +28,8 @@ constexpr uint64_t kTermsPerDetPass = 10000;
 constexpr uint64_t kMaxStepRecords = (1ull << 32) - 1;  // record slots of a step are 32-bit
 static_assert(kMaxPassBytes / 32 <= kMaxStepRecords, "record slots of a pass must fit 32-bit tile cursors");
 constexpr int kBigThreads = 256;
-constexpr int kBigChunk = 768;              // records of an oversize tile sorted per chunk
-constexpr int kBigCap = 640;                // partial records finished per sort (oversize path)
+constexpr int kBigChunk = 1024;             // records of an oversize tile grouped per chunk
+constexpr int kBigCap = 640;                // partial records finished per grouping (oversize path)
 constexpr uint64_t kBigScratch = 16384;      // partial records per buffer of one oversize CTA
 constexpr int kBigBuckets = 256;             // most hash buckets the partials of one oversize tile split into
 static_assert(kBigBuckets * kBigCap >= 2 * kBigScratch, "the hash split can always make buckets fit a chunk");
@@ -52,6 +51,11 @@ constexpr uint32_t kErrWaitTimeout = 2u;     // a bounded mbarrier wait ran out
 constexpr uint32_t kErrScratch = 4u;         // oversize tile larger than its scratch
 constexpr uint32_t kErrNoProgress = 8u;      // the partials of an oversize tile could not be split to fit a chunk
 constexpr uint32_t kErrCount = 16u;          // emitted terms differ from the plan
+
+// Per-instance run options the tile kernels read (TileParams::iflags).
+constexpr uint32_t kInstSym = 1u;        // spin-flip symmetric run
+constexpr uint32_t kInstNarrow = 2u;     // narrowed sort hash (test aid: most keys of a tile share hash and bucket)
+constexpr uint32_t kInstShortWait = 4u;  // bulk-copy waits give up almost at once (test aid: exercises the timeout)
 
 // One generated term: the excited determinant, its numerator H_ai c_i and
 // its denominator E0 - H_aa in units of 2^-48 Ha (from the parent's diagonal
@@ -97,7 +101,7 @@ struct GenParams {
     const HashTables *hash;
     const uint64_t *keys;  // 2 * n_det
     const double *coef;
-    const int64_t *d0;     // (E0 - H_ii) * 2^48 per determinant
+    const int64_t *d0;     // (E0 - H_ii) * 2^48 per determinant, exact from the integer tables
     const int64_t *g;      // per determinant, 2 n values: (h_xx + p(x)) * 2^48, alpha x then beta x
     double e0;
     uint64_t n_det;
@@ -157,7 +161,7 @@ struct RunAcc {
     double min_abs_den;
     unsigned int err;
     unsigned int n_big;          // oversize tiles over all passes
-    unsigned long long big_max;  // unused
+    unsigned long long n_coll;   // times two different keys of a tile shared their sort hash
 };
 
 // Tiles of a step cover several instances: tile t belongs to the instance
@@ -170,7 +174,8 @@ struct TileParams {
     uint64_t n_tiles;                    // over all instances
     const unsigned long long *tile_base; // n_inst + 1
     const double *e0;                    // per instance
-    const uint32_t *sym;                 // per instance: spin-flip symmetric run (keys with alpha > beta count twice)
+    const uint32_t *iflags;              // per instance: options of the tile kernels (kInst* bits: spin-flip
+                                         // symmetric run, narrowed sort hash, short copy waits)
     RunAcc *const *acc;                  // per instance
     unsigned int *n_big;                 // per instance: oversize tiles of the pass
     unsigned long long *big_max;         // largest oversize tile (diagnostic)
@@ -209,7 +214,9 @@ cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int sme
 cudaError_t launch_gen_single(GenMode mode, const GenParams &p, GenParams *d_params, unsigned long long *d_base,
                               cudaStream_t s);  // one determinant (parity aid); d_* are 1- and 2-entry scratch
 cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, double *out, cudaStream_t s);
-cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s);
+// (E0 - H_ii) 2^48 exactly from the integer tables (needs the g tables of launch_ref_g)
+cudaError_t launch_ref_d0(const SysDev &sys, const uint64_t *keys, const int64_t *g, uint64_t n, double e0,
+                          int64_t *d0, cudaStream_t s);
 cudaError_t launch_ref_g(const SysDev &sys, const uint64_t *keys, uint64_t n, int64_t *g, cudaStream_t s);
 cudaError_t launch_scan_u32_to_u64(const uint32_t *in, unsigned long long *out, uint32_t *out32, uint64_t n,
                                    unsigned long long *tmp, cudaStream_t s);
@@ -227,6 +234,8 @@ cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s);
 cudaError_t launch_ref_subtract(const uint64_t *keys, const double *coef, const double *hii, uint64_t n, double e0,
                                 uint64_t cons_mod, uint64_t cons_rem, RunAcc *acc, uint32_t *err, cudaStream_t s);
 cudaError_t launch_acc_finalize(RunAcc *acc, int n, cudaStream_t s);
+// num^2 / den with the tile kernels' arithmetic (den in Hartree, rounded to 2^-48)
+cudaError_t launch_eval_terms(const double *num, const double *den, uint64_t n, double *out, cudaStream_t s);
 cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm);  // once per process and device, before any capture
 size_t tile_smem_bytes();
 size_t big_smem_bytes();

@@ -98,19 +98,21 @@ __device__ __forceinline__ bool key_less(uint64_t a0, uint64_t b0, uint64_t a1, 
 
 // ---------------------------------------------------- exact fixed point
 
-// Add value * 2^90 (rounded half away from zero) to the 128-bit integer
-// (lo, hi).  |value| must stay below 2^36, else the range bit is set.
-__device__ __forceinline__ void fx_add_double(uint64_t &lo, int64_t &hi, double v, uint32_t &err)
+// Add value * 2^shift (rounded half away from zero) to the 128-bit integer
+// (lo, hi).  |value| * 2^shift must stay below 2^126, else the range bit is
+// set.  Numerators use shift 90 (|value| < 2^36); energy terms, whose
+// denominator is a 2^-48 fixed-point integer, fold that power of two in.
+__device__ __forceinline__ void fx_add_double(uint64_t &lo, int64_t &hi, double v, uint32_t &err, int shift = kFxShift)
 {
     uint64_t bits = (uint64_t)__double_as_longlong(v);
     int e = (int)((bits >> 52) & 0x7FF);
     if (e == 0) return;  // zero / subnormal: below the resolution
-    if (e >= 1023 + 36) {
+    if (e >= 1023 + 126 - shift) {
         err |= kErrFixedRange;
         return;
     }
     uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    int sh = e - 1075 + kFxShift;  // value = m * 2^(e - 1075)
+    int sh = e - 1075 + shift;  // value * 2^shift = m * 2^sh
     uint64_t ml, mh;
     if (sh >= 0) {
         if (sh == 0) {
@@ -199,23 +201,33 @@ __device__ __forceinline__ double fx_to_double(uint64_t lo, int64_t hi)
 __device__ __forceinline__ double den_to_double(int64_t d) { return __ll2double_rn((long long)d) * 0x1p-48; }
 static_assert(kDenShift == 48, "den_to_double scales by 2^-48");
 
-// Reciprocal of d: a single-precision hardware estimate refined by one
-// Newton-Raphson step, x1 = x0 (2 - d x0) (relative error about 2^-46).
-__device__ __forceinline__ double recip(double d, int64_t dfx)
+// 1 / dfx for a nonzero fixed-point denominator dfx (E0 - H_aa = dfx 2^-48):
+// the single-precision hardware estimate x0 of rcp.approx.ftz.f32 (at most
+// 1 ulp) of dfx rounded to float (half an ulp), together within 2^-22.4
+// relative, refined by one Newton-Raphson step x1 = x0 + x0 (1 - dfx x0) in
+// FP64, whose relative error is the square of x0's plus FP64 rounding:
+// below 2^-44.  Every nonzero int64 has a reciprocal that is a normal
+// float (between 2^-63 and 1), so x0's bits map onto a double directly
+// (sign, exponent rebiased by 1023 - 127, mantissa widened).  dfx = 0 maps to
+// a huge finite value (the float's infinity rebiased), so a term with a
+// nonzero numerator overflows the fixed-point range and is reported.
+__device__ __forceinline__ double recip_fx(int64_t dfx)
 {
-    float f = __ll2float_rn((long long)dfx) * 0x1p-48f;
+    const double d = __ll2double_rn((long long)dfx);
+    const float f = __ll2float_rn((long long)dfx);
     float rf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
-    uint32_t fb = __float_as_uint(rf);
-    uint32_t fe = (fb >> 23) & 0xFF;
-    uint64_t db;
-    if (fe == 0) db = (uint64_t)(fb >> 31) << 63;
-    else if (fe == 0xFF) db = ((uint64_t)(fb >> 31) << 63) | (0x7FFull << 52) | ((uint64_t)(fb & 0x7FFFFF) << 29);
-    else db = ((uint64_t)(fb >> 31) << 63) | ((uint64_t)(fe + 896) << 52) | ((uint64_t)(fb & 0x7FFFFF) << 29);
-    double x = __longlong_as_double((long long)db);
-    double e = __fma_rn(-d, x, 1.0);
+    const uint32_t fb = __float_as_uint(rf);
+    const uint64_t db = ((uint64_t)(fb >> 31) << 63) | ((uint64_t)(((fb >> 23) & 0xFFu) + 896u) << 52) |
+                        ((uint64_t)(fb & 0x7FFFFFu) << 29);
+    const double x = __longlong_as_double((long long)db);
+    const double e = __fma_rn(-d, x, 1.0);
     return __fma_rn(x, e, x);
 }
+
+// The Epstein-Nesbet term num^2 / (E0 - H_aa) of Eq. 3 in units of 2^-48 Ha
+// (the fixed-point addition of the energy applies the factor 2^48).
+__device__ __forceinline__ double term_fx48(double num, int64_t dfx) { return (num * num) * recip_fx(dfx); }
 
 // ------------------------------------------------- mbarrier + TMA bulk copy
 
@@ -263,14 +275,32 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for the phase with the given parity, giving up after ~2^31 SM cycles
-// (about a second).  On a timeout the error bit is set and a second bounded
-// wait gives the copy in flight the chance to land before the CTA moves on.
-__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *err)
+// Non-blocking probe of the phase (try_wait may suspend the thread for a
+// hardware time window before it answers; test_wait answers at once).
+__device__ __forceinline__ bool mbar_probe(uint64_t *bar, uint32_t parity)
 {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity, giving up after `limit` SM
+// cycles (2^31, about a second, in normal runs; a limit below 2^12 cycles
+// polls with the non-blocking probe so that it can expire before a copy
+// lands).  On a timeout the error bit is set and a second bounded wait (2^31
+// cycles) gives the copy in flight the chance to land before the CTA stops.
+__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *err, long long limit)
+{
+    const bool quick = limit < (1ll << 12);
     long long t0 = clock64();
-    while (!mbar_test(bar, parity)) {
-        if (clock64() - t0 > (1ll << 31)) {
+    while (!(quick ? mbar_probe(bar, parity) : mbar_test(bar, parity))) {
+        if (clock64() - t0 > limit) {
             atomicOr(err, kErrWaitTimeout);
             long long t1 = clock64();
             while (!mbar_test(bar, parity) && clock64() - t1 < (1ll << 31)) {
@@ -359,6 +389,7 @@ struct GenFixed {
     uint16_t blk_g[2 * kVbkBitsMax];
     uint8_t blk_k[2 * kVbkBitsMax];
     int n_blk;
+    unsigned int n_list;  // listed alpha-alpha doubles of the current round
 };
 
 // beta class of a beta-string hash (splits the heavy alpha classes)
@@ -437,42 +468,56 @@ __device__ __forceinline__ void store_rec32(Rec32 *dst, uint64_t a, uint64_t b, 
 // the hot loops hold them in registers whether the parameters live in the
 // constant bank or in global memory.
 struct EmitOut {
-    uint32_t *counts;      // TileCount: terms per tile
-    unsigned int *cursor;  // Emit / DetTerms: next slot per tile
+    unsigned int *ctr;      // TileCount: terms per tile; Emit / DetTerms: next slot per tile
     Rec32 *recs;
-    uint64_t n_tiles;
-    unsigned long long rec_cap;
+    uint32_t n_tiles;       // tiles of the instance in the pass (< 2^32)
+    uint32_t rec_cap;       // record slots of the step (< 2^32)
     uint32_t *err;
-    double e0;
+    double e0;              // DetTerms only
 };
 
-template <int MODE, class KeyFn, class ValFn>
+// Tile of a term from the high word of its tile hash: floor(zt_hi n_tiles / 2^32)
+// (the reference partition uses the same map).
+__device__ __forceinline__ uint32_t tile_of(uint64_t zt, uint32_t n_tiles)
+{
+    return __umulhi((uint32_t)(zt >> 32), n_tiles);
+}
+
+template <int MODE, int NB = kGenBatch, class KeyFn, class ValFn>
 __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, int n, KeyFn key, ValFn val)
 {
-    uint32_t slot[kGenBatch];
-    bool ok[kGenBatch];
-    double el[kGenBatch];
+    // The lanes of a warp hold consecutive items (i0 - lane is the warp's
+    // first), so the steps in which some lane has an item are known to the
+    // whole warp and the others are skipped.
+    const int wbase = i0 - (int)(threadIdx.x & 31);
+    const int nst = wbase >= n ? 0 : min(NB, (n - wbase + step - 1) / step);
+    uint32_t slot[NB];
+    uint32_t ok = 0;  // bit u: item of step u is a term of the pass
+    double el[NB];
 #pragma unroll
-    for (int u = 0; u < kGenBatch; ++u) {
-        const int i = i0 + u * step;
-        uint64_t zt = 0;
-        el[u] = 0.0;
-        ok[u] = i < n && key(i, zt, el[u]);
+    for (int u = 0; u < NB; ++u) {
         slot[u] = 0;
-        if (ok[u]) {
-            if constexpr (MODE == kModeTileCount) {
-                red_add_global(&p.counts[__umul64hi(zt, p.n_tiles)], 1u);
-            } else if constexpr (MODE == kModeEmit) {
-                slot[u] = atom_add_global(&p.cursor[__umul64hi(zt, p.n_tiles)], 1u);
-            } else {
-                slot[u] = atom_add_global(&p.cursor[0], 1u);
+        el[u] = 0.0;
+        if (u < nst) {
+            const int i = i0 + u * step;
+            uint64_t zt = 0;
+            if (i < n && key(i, zt, el[u])) {
+                ok |= 1u << u;
+                if constexpr (MODE == kModeTileCount) {
+                    red_add_global(&p.ctr[tile_of(zt, p.n_tiles)], 1u);
+                } else if constexpr (MODE == kModeEmit) {
+                    slot[u] = atom_add_global(&p.ctr[tile_of(zt, p.n_tiles)], 1u);
+                } else {
+                    slot[u] = atom_add_global(&p.ctr[0], 1u);
+                }
             }
         }
     }
     if constexpr (MODE == kModeEmit || MODE == kModeDetTerms) {
 #pragma unroll
-        for (int u = 0; u < kGenBatch; ++u) {
-            if (!ok[u]) continue;
+        for (int u = 0; u < NB; ++u) {
+            if (u >= nst) break;
+            if (!((ok >> u) & 1u)) continue;
             if (slot[u] >= p.rec_cap) {  // emission disagrees with the counts
                 if constexpr (MODE == kModeEmit) atomicOr(p.err, kErrCount);
                 continue;
@@ -792,15 +837,15 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     } else {
         const uint64_t ZtaA = F.ZtaA, ZtbB = F.ZtbB;
         EmitOut out;
-        out.counts = MODE == kModeTileCount ? p.tile_counts + p.tile_base : nullptr;
-        out.cursor = MODE == kModeEmit ? p.cursor + p.tile_base : p.cursor;
+        out.ctr = MODE == kModeTileCount ? p.tile_counts + p.tile_base
+                  : MODE == kModeEmit    ? p.cursor + p.tile_base
+                                         : p.cursor;
         out.recs = p.recs;
-        out.n_tiles = p.n_tiles;
-        out.rec_cap = p.rec_cap;
+        out.n_tiles = (uint32_t)p.n_tiles;
+        out.rec_cap = (uint32_t)min(p.rec_cap, (unsigned long long)0xFFFFFFFFull);
         out.err = p.err;
         out.e0 = p.e0;
         const uint32_t class_lo = p.class_lo, class_hi = p.class_hi;
-        const uint64_t cons_mod = p.cons_mod, cons_rem = p.cons_rem;
         // beta singles of the pass: all of them, or the compacted list
         const int n_sb = bfull ? p.n_sb : F.n_sb_pass;
         auto sb_at = [&](int k) { return bfull ? k : (int)sb_pass[k]; };
@@ -810,7 +855,6 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         uint32_t *vb_cnt = reinterpret_cast<uint32_t *>(smem + p.smem_hist);
         uint16_t *vb_off = reinterpret_cast<uint16_t *>(vb_cnt + kVbkBuckets);
         uint16_t *vb_list = vb_off + kVbkBuckets + 1;
-        uint16_t *vb_warp = vb_list + kMaxVirPairs;
         if (b_in) {  // uniform across the CTA
             if (tid == 0) {
                 constexpr int gs = kClassBits - kVbkBits;
@@ -918,175 +962,300 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                         num = flip_sign(c * v, info >> 16);
                         den = d0 - sb_delta[s];
                     });
-        // ---- alpha-beta doubles: one alpha single per warp, beta singles over lanes
-        for (int k = warp; k < n_sa_pass; k += nw) {
-            const int s = sa_pass[k];
-            const uint32_t info = sa_info[s];
-            const int rA = info & 0xFF, aA = (info >> 8) & 0xFF;
-            const uint64_t a2 = A ^ (1ull << rA) ^ (1ull << aA);
-            const uint64_t ztA = sa_zt[s];
-            int64_t baseD = 0;
-            double cA = 0.0;
-            // (aA rA|aB rB) = (rA aA|rB aB): lanes take consecutive beta
-            // singles (same rB, ascending aB), so this layout is contiguous
-            const double *slice = eri + ((size_t)rA * N + aA) * N * N;
-            if constexpr (kVal) {
-                // u[q] = J(aA, q) - J(rA, q): the alpha-beta cross terms of H_aa
-                for (int q = lane; q < N; q += 32) vec[q] = Jx[aA * N + q] - Jx[rA * N + q];
-                __syncwarp();
-                baseD = d0 - sa_delta[s];
-                cA = flip_sign(c, info >> 16);
+        // ---- alpha-beta doubles: every (alpha single of the pass, beta single)
+        // item over the whole CTA, in groups of up to kAbGroup alpha singles (a
+        // pass holding few classes has few alpha singles, and one per warp
+        // would leave most warps idle).  Items of one alpha single are
+        // consecutive, so lanes take consecutive beta singles (same rB,
+        // ascending aB) and the integral (aA rA|aB rB) = (rA aA|rB aB) is read
+        // contiguously.  Row j of vec holds u[q] = J(aA, q) - J(rA, q) for the
+        // group's alpha single j: the alpha-beta cross terms of H_aa.
+        {
+            constexpr int kAbGroup = kGenThreads / 32;  // rows of vec
+            const uint32_t nsb = (uint32_t)n_sb;
+            // i / nsb = umulhi(i, ceil(2^32 / nsb)) exactly while i * nsb < 2^32
+            const uint32_t magic = nsb ? (uint32_t)((0x100000000ull + nsb - 1) / nsb) : 0u;
+            for (int g0 = 0; g0 < n_sa_pass; g0 += kAbGroup) {  // uniform across the CTA
+                const int ng = min(kAbGroup, n_sa_pass - g0);
+                __syncthreads();  // vec rows free
+                if constexpr (kVal) {
+                    for (int j = warp; j < ng; j += nw) {
+                        const uint32_t ia = sa_info[sa_pass[g0 + j]];
+                        const int rA = ia & 0xFF, aA = (ia >> 8) & 0xFF;
+                        for (int q = lane; q < N; q += 32) vec_all[j * kMaxOrb + q] = Jx[aA * N + q] - Jx[rA * N + q];
+                    }
+                }
+                __syncthreads();
+                const int nitems = ng * n_sb;
+                for (int i0 = tid; i0 < nitems; i0 += kGenThreads * kGenBatch)
+                    emit_batch<MODE>(
+                        out, i0, kGenThreads, nitems,
+                        [&](int i, uint64_t &zt, double &el) {
+                            const int j = (int)__umulhi((uint32_t)i, magic), k = i - j * n_sb;
+                            const int s = sa_pass[g0 + j], sb = sb_at(k);
+                            const uint32_t ia = sa_info[s];
+                            if (sym && single_word(B, sb_info[sb]) > single_word(A, ia)) return false;
+                            if (cutting) {
+                                const uint32_t bi = sb_info[sb];
+                                el = __ldg(eri + (((size_t)(ia & 0xFF) * N + ((ia >> 8) & 0xFF)) * N + (bi & 0xFF)) * N +
+                                           ((bi >> 8) & 0xFF));
+                                if (!above_cut(c, el, cut)) return false;
+                            }
+                            zt = sa_zt[s] ^ sb_zt[sb];
+                            return true;
+                        },
+                        [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
+                            const int j = (int)__umulhi((uint32_t)i, magic), k = i - j * n_sb;
+                            const int s = sa_pass[g0 + j], sb = sb_at(k);
+                            const uint32_t ia = sa_info[s], bi = sb_info[sb];
+                            const int rA = ia & 0xFF, aA = (ia >> 8) & 0xFF, rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
+                            ka = A ^ (1ull << rA) ^ (1ull << aA);
+                            kb = B ^ (1ull << rB) ^ (1ull << aB);
+                            const double v =
+                                cutting ? el : __ldg(eri + (((size_t)rA * N + aA) * N + rB) * N + aB);
+                            num = flip_sign(c * v, (ia >> 16) ^ (bi >> 16));
+                            const int64_t *u = vec_all + j * kMaxOrb;
+                            den = d0 - sa_delta[s] - sb_delta[sb] - (u[aB] - u[rB]);
+                        });
             }
-            for (int sb0 = lane; sb0 < n_sb; sb0 += 32 * kGenBatch)
-                emit_batch<MODE>(
-                    out, sb0, 32, n_sb,
-                    [&](int k, uint64_t &zt, double &el) {
-                        const int sb = sb_at(k);
-                        if (sym && single_word(B, sb_info[sb]) > a2) return false;
-                        if (cutting) {
-                            const uint32_t bi = sb_info[sb];
-                            el = __ldg(slice + (bi & 0xFF) * N + ((bi >> 8) & 0xFF));
-                            if (!above_cut(c, el, cut)) return false;
-                        }
-                        zt = ztA ^ sb_zt[sb];
-                        return true;
-                    },
-                    [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
-                        const int sb = sb_at(k);
-                        const uint32_t bi = sb_info[sb];
-                        const int rB = bi & 0xFF, aB = (bi >> 8) & 0xFF;
-                        ka = a2;
-                        kb = B ^ (1ull << rB) ^ (1ull << aB);
-                        num = flip_sign(cA * (cutting ? el : __ldg(slice + rB * N + aB)), bi >> 16);
-                        den = baseD - sb_delta[sb] - (vec[aB] - vec[rB]);
-                    });
-            __syncwarp();
         }
-        // ---- same-spin doubles: one occupied pair per warp, virtual pairs over lanes
-        for (int spin = 0; spin < 2; ++spin) {
-            if (spin == 0 && !b_in) continue;  // alpha-alpha doubles keep beta string B
-            if (spin == 1 && !a_in) break;
-            const int npo = spin ? n_occ_pairs_b : n_occ_pairs_a;
-            const int npv = spin ? n_vir_pairs_b : n_vir_pairs_a;
-            const int *occ = spin ? F.occB : F.occA;
-            const int *vir = spin ? F.virB : F.virA;
-            const int nv = spin ? nvb : nva;
-            const int64_t *g = spin ? F.gB : F.gA;
-            const uint64_t W = spin ? B : A;
+        // ---- alpha-alpha doubles (beta string B).  The candidates of an
+        // occupied pair are the virtual pairs of the bucket ranges the pass's
+        // class blocks map to (block xor the top bits of the occupied part's
+        // class hash).  A pass holding few classes leaves each occupied pair
+        // few candidates, so they are enumerated over the whole CTA: the
+        // candidate count of every occupied pair, a block scan, one thread per
+        // candidate checking its class and listing it, and the list emitted
+        // with every lane busy, in rounds of at most kListCap candidates.
+        if (b_in) {  // uniform across the CTA
+            uint32_t *poff = vb_cnt;                                  // candidate offsets of the occupied pairs
+            uint32_t *clist = reinterpret_cast<uint32_t *>(vec_all);  // (occupied pair << 16) | virtual pair
+            constexpr int kPairGroup = kVbkBuckets - 1;
+            constexpr uint32_t kListCap = (uint32_t)(kGenThreads / 32 * kMaxOrb * 8 / 4);
+            constexpr int kAaBatch = 4;  // terms whose slots a lane requests together here (fewer live registers)
+            const int npo = n_occ_pairs_a;
+            const uint32_t lt = (1u << lane) - 1u;
+            auto key_aa = [&](int k, uint64_t &zt, double &el) {
+                const uint32_t e = clist[k];
+                const int pr = pairs[e >> 16], pv = pairs[e & 0xFFFFu];
+                const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+                const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
+                if (cutting) {
+                    el = same_double_value(eri, N, r1, r2, a1, a2);
+                    if (!above_cut(c, el, cut)) return false;
+                }
+                zt = ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2] ^ F.zta[a1] ^ F.zta[a2];
+                return true;
+            };
+            auto val_aa = [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
+                const uint32_t e = clist[k];
+                const int pr = pairs[e >> 16], pv = pairs[e & 0xFFFFu];
+                const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+                const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
+                const uint64_t w1 = A ^ (1ull << r1) ^ (1ull << a1);
+                ka = w1 ^ (1ull << r2) ^ (1ull << a2);
+                kb = B;
+                const uint32_t par = __popcll(A & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                const double v = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
+                num = flip_sign(c * v, par);
+                // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
+                // v(x) = g(x) - W(r1,x) - W(r2,x)
+                den = d0 + F.gA[r1] + F.gA[r2] - __ldg(WSx + r1 * N + r2) -
+                      (F.gA[a1] - __ldg(WSx + r1 * N + a1) - __ldg(WSx + r2 * N + a1)) -
+                      (F.gA[a2] - __ldg(WSx + r1 * N + a2) - __ldg(WSx + r2 * N + a2)) - __ldg(WSx + a1 * N + a2);
+            };
+            __syncthreads();  // the alpha-beta warps are done with vec
+            for (int p0 = 0; p0 < npo; p0 += kPairGroup) {
+                const int np = min(kPairGroup, npo - p0);
+                for (int t = tid; t <= np; t += kGenThreads) {
+                    uint32_t n = 0;
+                    if (t < np) {
+                        const int pr = pairs[p0 + t];
+                        const uint32_t u = vb_bucket(F.ZcA ^ F.zc[F.occA[pr & 0xFF]] ^ F.zc[F.occA[pr >> 8]]);
+                        for (int q = 0; q < F.n_blk; ++q) {
+                            const uint32_t k = F.blk_k[q];
+                            const uint32_t bb = (F.blk_g[q] ^ u) & ~((1u << k) - 1u);
+                            n += (uint32_t)vb_off[bb + (1u << k)] - vb_off[bb];
+                        }
+                    }
+                    poff[t] = n;
+                }
+                __syncthreads();
+                block_scan_excl_u32(poff, np + 1, F.wsum);
+                const uint32_t total = poff[np];
+                for (uint32_t c0 = 0; c0 < total; c0 += kListCap) {
+                    if (tid == 0) F.n_list = 0;
+                    __syncthreads();
+                    const uint32_t c1 = min(total, c0 + kListCap);
+                    for (uint32_t cb = c0; cb < c1; cb += kGenThreads) {
+                        const uint32_t ci = cb + tid;
+                        bool keep = false;
+                        uint32_t item = 0;
+                        if (ci < c1) {
+                            int lo = 0, hi = np;  // the occupied pair: last t with poff[t] <= ci
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (poff[mid] <= ci) lo = mid;
+                                else hi = mid;
+                            }
+                            const int pr = pairs[p0 + lo];
+                            const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+                            const uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
+                            const uint32_t u = vb_bucket(zc12);
+                            uint32_t i = ci - poff[lo];
+                            int vp = 0;
+                            for (int q = 0; q < F.n_blk; ++q) {
+                                const uint32_t k = F.blk_k[q];
+                                const uint32_t bb = (F.blk_g[q] ^ u) & ~((1u << k) - 1u);
+                                const uint32_t st = vb_off[bb], sz = (uint32_t)vb_off[bb + (1u << k)] - st;
+                                if (i < sz) {
+                                    vp = vb_list[st + i];
+                                    break;
+                                }
+                                i -= sz;
+                            }
+                            const int pv = pairs[vp];
+                            const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
+                            const uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
+                            const uint64_t w2 = A ^ (1ull << r1) ^ (1ull << r2) ^ (1ull << a1) ^ (1ull << a2);
+                            keep = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, w2) &&
+                                   !(sym && w2 < B);
+                            item = ((uint32_t)(p0 + lo) << 16) | (uint32_t)vp;
+                        }
+                        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+                        if (m) {
+                            const int leader = __ffs(m) - 1;
+                            uint32_t base = 0;
+                            if (lane == leader) base = atomicAdd(&F.n_list, (unsigned)__popc(m));
+                            base = __shfl_sync(0xffffffffu, base, leader);
+                            if (keep) clist[base + __popc(m & lt)] = item;
+                        }
+                    }
+                    __syncthreads();
+                    const int nl = (int)F.n_list;
+                    for (int k0 = tid; k0 < nl; k0 += kGenThreads * kAaBatch)
+                        emit_batch<MODE, kAaBatch>(out, k0, kGenThreads, nl, key_aa, val_aa);
+                    __syncthreads();  // the list area is reused
+                }
+            }
+        }
+        // ---- beta-beta doubles (alpha string A): one occupied pair per warp,
+        // virtual pairs over lanes.  In an ordinary pass every virtual pair
+        // gives a term of the pass and the terms are emitted straight away.
+        // Where an item needs a check (the beta class in a pass over part of
+        // a heavy alpha class, the spin-flip rule) the warp first lists the
+        // items that pass it, gathering several occupied pairs, and emits the
+        // list with every lane busy.
+        if (a_in) {  // uniform across the CTA
+            uint32_t *wl = reinterpret_cast<uint32_t *>(vec);  // the warp's item list (its row of vec)
+            constexpr int kWarpList = kMaxOrb * 8 / 4;
+            const uint32_t lt = (1u << lane) - 1u;
+            const int npo = n_occ_pairs_b, npv = n_vir_pairs_b;
+            const bool listed = !bfull || sym;
+            int nl = 0;
+            // emit the listed items, each (occupied pair << 16) | virtual pair
+            auto flush = [&]() {
+                __syncwarp();
+                for (int k0 = lane; k0 < nl; k0 += 32 * kGenBatch)
+                    emit_batch<MODE>(
+                        out, k0, 32, nl,
+                        [&](int k, uint64_t &zt, double &el) {
+                            const uint32_t e = wl[k];
+                            const int pr = pairs[e >> 16], pv = pairs[e & 0xFFFFu];
+                            const int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
+                            const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
+                            if (cutting) {
+                                el = same_double_value(eri, N, r1, r2, a1, a2);
+                                if (!above_cut(c, el, cut)) return false;
+                            }
+                            zt = ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2] ^ F.ztb[a1] ^ F.ztb[a2];
+                            return true;
+                        },
+                        [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
+                            const uint32_t e = wl[k];
+                            const int pr = pairs[e >> 16], pv = pairs[e & 0xFFFFu];
+                            const int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
+                            const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
+                            const uint64_t w1 = B ^ (1ull << r1) ^ (1ull << a1);
+                            ka = A;
+                            kb = w1 ^ (1ull << r2) ^ (1ull << a2);
+                            const uint32_t par =
+                                __popcll(B & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                            const double v = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
+                            num = flip_sign(c * v, par);
+                            den = d0 + F.gB[r1] + F.gB[r2] - __ldg(WSx + r1 * N + r2) -
+                                  (F.gB[a1] - __ldg(WSx + r1 * N + a1) - __ldg(WSx + r2 * N + a1)) -
+                                  (F.gB[a2] - __ldg(WSx + r1 * N + a2) - __ldg(WSx + r2 * N + a2)) -
+                                  __ldg(WSx + a1 * N + a2);
+                        });
+                __syncwarp();
+                nl = 0;
+            };
             for (int pi = warp; pi < npo; pi += nw) {
                 const int pr = pairs[pi];
-                const int r1 = occ[pr & 0xFF], r2 = occ[pr >> 8];
-                const uint64_t w12 = W ^ (1ull << r1) ^ (1ull << r2);
-                const uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
-                const uint64_t zcb12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
-                const uint64_t zt12 =
-                    spin ? (ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2]) : (ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2]);
-                // items: every virtual beta pair, or the alpha pairs of the bucket
-                // ranges the pass's blocks map to (block xor top bits of zc12)
-                const bool nar = spin == 0;
-                int nitems = npv, nq = 0;
-                uint16_t *ws = vb_warp + warp * 64;  // [0, 32): slice starts, [32, 64): item offsets
-                if (nar) {
-                    const uint32_t u = vb_bucket(zc12);
-                    nq = F.n_blk;
-                    uint32_t start = 0, sz = 0;
-                    if (lane < nq) {
-                        const uint32_t k = F.blk_k[lane];
-                        const uint32_t b = (F.blk_g[lane] ^ u) & ~((1u << k) - 1u);
-                        start = vb_off[b];
-                        sz = (uint32_t)vb_off[b + (1u << k)] - start;
+                const int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
+                const uint64_t w12 = B ^ (1ull << r1) ^ (1ull << r2);
+                if (!listed) {
+                    // every virtual pair is a term of the pass
+                    int64_t base = 0;
+                    if constexpr (kVal) {
+                        for (int j = lane; j < nvb; j += 32) {
+                            const int x = F.virB[j];
+                            vec[j] = F.gB[x] - WSx[r1 * N + x] - WSx[r2 * N + x];
+                        }
+                        __syncwarp();
+                        base = d0 + F.gB[r1] + F.gB[r2] - WSx[r1 * N + r2];
                     }
-                    uint32_t incl = sz;
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-                        if (lane >= off) incl += v;
-                    }
-                    if (lane < nq) {
-                        ws[lane] = (uint16_t)start;
-                        ws[32 + lane] = (uint16_t)(incl - sz);
-                    }
-                    nitems = (int)__shfl_sync(0xffffffffu, incl, 31);
-                    __syncwarp();
-                }
-                if (nitems == 0) continue;  // uniform across the warp
-                int64_t base = 0;
-                if constexpr (kVal) {
-                    // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
-                    // v(x) = g(x) - W(r1,x) - W(r2,x)
-                    for (int j = lane; j < nv; j += 32) {
-                        int x = vir[j];
-                        vec[j] = g[x] - WSx[r1 * N + x] - WSx[r2 * N + x];
-                    }
-                    __syncwarp();
-                    base = d0 + g[r1] + g[r2] - WSx[r1 * N + r2];
-                }
-                // the same emission over items mapped to virtual pairs by `pair_at`
-                // (instantiated separately for the direct and the bucketed case)
-                auto emit_pairs = [&](int n_items, auto pair_at) {
-                    for (int t0 = lane; t0 < n_items; t0 += 32 * kGenBatch)
+                    const uint64_t zt12 = ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2];
+                    for (int t0 = lane; t0 < npv; t0 += 32 * kGenBatch)
                         emit_batch<MODE>(
-                            out, t0, 32, n_items,
-                            [&](int i, uint64_t &zt, double &el) {
-                                const int t = pair_at(i);
+                            out, t0, 32, npv,
+                            [&](int t, uint64_t &zt, double &el) {
                                 const int pv = pairs[t];
-                                const int a1 = vir[pv & 0xFF], a2 = vir[pv >> 8];
-                                if (spin == 0) {
-                                    uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
-                                    if (cl < class_lo || cl >= class_hi) return false;
-                                    const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
-                                    if (!cons_ok(cons_mod, cons_rem, w2)) return false;
-                                    if (sym && w2 < B) return false;
-                                    if (cutting) {
-                                        el = same_double_value(eri, N, r1, r2, a1, a2);
-                                        if (!above_cut(c, el, cut)) return false;
-                                    }
-                                    zt = zt12 ^ F.zta[a1] ^ F.zta[a2];
-                                } else {
-                                    if (!bfull) {
-                                        const uint32_t bc = bclass_of(zcb12 ^ F.zcb[a1] ^ F.zcb[a2]);
-                                        if (bc < blo || bc >= bhi) return false;
-                                    }
-                                    if (sym && (w12 ^ (1ull << a1) ^ (1ull << a2)) > A) return false;
-                                    if (cutting) {
-                                        el = same_double_value(eri, N, r1, r2, a1, a2);
-                                        if (!above_cut(c, el, cut)) return false;
-                                    }
-                                    zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
+                                const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
+                                if (cutting) {
+                                    el = same_double_value(eri, N, r1, r2, a1, a2);
+                                    if (!above_cut(c, el, cut)) return false;
                                 }
+                                zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
                                 return true;
                             },
-                            [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
-                                const int t = pair_at(i);
+                            [&](int t, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
                                 const int pv = pairs[t];
                                 const int j1 = pv & 0xFF, j2 = pv >> 8;
-                                const int a1 = vir[j1], a2 = vir[j2];
-                                const uint64_t w2 = w12 ^ (1ull << a1) ^ (1ull << a2);
-                                ka = spin ? A : w2;
-                                kb = spin ? w2 : B;
-                                const uint64_t w1 = W ^ (1ull << r1) ^ (1ull << a1);
+                                const int a1 = F.virB[j1], a2 = F.virB[j2];
+                                const uint64_t w1 = B ^ (1ull << r1) ^ (1ull << a1);
+                                ka = A;
+                                kb = w12 ^ (1ull << a1) ^ (1ull << a2);
                                 const uint32_t par =
-                                    __popcll(W & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
+                                    __popcll(B & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
                                 // a1 is the fastest-varying index across lanes
-                                const double e = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
-                                num = flip_sign(c * e, par);
+                                const double v = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
+                                num = flip_sign(c * v, par);
                                 den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
                             });
-                };
-                if (nar)
-                    emit_pairs(nitems, [&](int i) -> int {
-                        int lo = 0, hi = nq;  // last slice whose offset is at most i
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if ((int)ws[32 + mid] <= i) lo = mid;
-                            else hi = mid;
-                        }
-                        return vb_list[ws[lo] + (i - (int)ws[32 + lo])];
-                    });
-                else
-                    emit_pairs(npv, [](int i) -> int { return i; });
-                __syncwarp();
+                    __syncwarp();
+                    continue;
+                }
+                const uint64_t zcb12 = F.ZcbB ^ F.zcb[r1] ^ F.zcb[r2];
+                for (int c0 = 0; c0 < npv; c0 += 32) {
+                    const int t = c0 + lane;
+                    bool keep = false;
+                    if (t < npv) {
+                        const int pv = pairs[t];
+                        const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
+                        const uint32_t bc = bclass_of(zcb12 ^ F.zcb[a1] ^ F.zcb[a2]);
+                        keep = (bfull || (bc >= p.bclass_lo && bc < p.bclass_hi)) &&
+                               !(sym && (w12 ^ (1ull << a1) ^ (1ull << a2)) > A);
+                    }
+                    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+                    if (nl + __popc(m) > kWarpList) flush();  // uniform across the warp
+                    if (keep) wl[nl + __popc(m & lt)] = ((uint32_t)pi << 16) | (uint32_t)t;
+                    nl += __popc(m);
+                }
+                if (nl > kWarpList - 32) flush();
             }
+            flush();
         }
     }
 }
@@ -1154,11 +1323,29 @@ __global__ void diag_kernel(const SysDev sys, const uint64_t *__restrict__ keys,
     out[i] = e;
 }
 
-__global__ void ref_d0_kernel(const double *__restrict__ hii, uint64_t n, double e0, int64_t *__restrict__ d0)
+// d0 = (E0 - H_ii) 2^48 of every reference determinant, exactly from the
+// integer tables: sum over the occupied spin-orbitals x of (h_xx + g(x))
+// counts each one-electron energy twice and each pair energy <xj||xj> twice,
+// so it is 2 H_ii (2^-48 Ha).  A term's E0 - H_aa, assembled from its parent's
+// d0 and integer increments, is then the same integer whichever reference
+// determinant generated it.
+__global__ void ref_d0_kernel(const SysDev sys, const uint64_t *__restrict__ keys, const int64_t *__restrict__ g,
+                              uint64_t n, int64_t e0x, int64_t *__restrict__ d0)
 {
-    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    d0[i] = __double2ll_rn((e0 - hii[i]) * kDenScale);
+    const int N = sys.n;
+    const int64_t *gi = g + i * 2 * N;
+    int64_t s = 0;
+    for (uint64_t m = keys[2 * i]; m; m &= m - 1) {
+        const int x = __ffsll((long long)m) - 1;
+        s += sys.hdx[x] + gi[x];
+    }
+    for (uint64_t m = keys[2 * i + 1]; m; m &= m - 1) {
+        const int x = __ffsll((long long)m) - 1;
+        s += sys.hdx[x] + gi[N + x];
+    }
+    d0[i] = e0x - (s >> 1);
 }
 
 // g(x) = h_xx + p(x) of every reference determinant, p(x) = sum over its
@@ -1197,10 +1384,11 @@ cudaError_t launch_ref_g(const SysDev &sys, const uint64_t *keys, uint64_t n, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_ref_d0(const double *hii, uint64_t n, double e0, int64_t *d0, cudaStream_t s)
+cudaError_t launch_ref_d0(const SysDev &sys, const uint64_t *keys, const int64_t *g, uint64_t n, double e0,
+                          int64_t *d0, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    ref_d0_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(hii, n, e0, d0);
+    ref_d0_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys, keys, g, n, (int64_t)std::llrint(e0 * kDenScale), d0);
     return cudaGetLastError();
 }
 
@@ -1348,7 +1536,7 @@ __global__ void ref_tile_kernel(const RefPartParams p)
     // a run with duplicate subtraction keeps the reference keys in the sum
     if (!q.subtract && cl >= q.class_lo && cl < q.class_hi && bc >= q.bclass_lo && bc < q.bclass_hi &&
         cons_ok(q.cons_mod, q.cons_rem, A)) {
-        t = (uint32_t)(q.tile_base + __umul64hi(zt, q.n_tiles));
+        t = (uint32_t)(q.tile_base + tile_of(zt, (uint32_t)q.n_tiles));
         atomicAdd(&p.ref_count[t], 1u);
     }
     p.ref_tile[g] = t;
@@ -1412,7 +1600,7 @@ struct KeyStats {
     uint64_t e2_lo;
     int64_t e2_hi;
     uint64_t dsum, dxor, min_den;
-    uint32_t n_unique, n_in_ref, n_ext, n_pos;
+    uint32_t n_in_ref, n_ext, n_pos, n_coll;  // distinct keys = n_in_ref + n_ext
     uint32_t err;
     __device__ void clear()
     {
@@ -1420,108 +1608,10 @@ struct KeyStats {
         e2_hi = 0;
         dsum = dxor = 0;
         min_den = ~0ull;
-        n_unique = n_in_ref = n_ext = n_pos = 0;
+        n_in_ref = n_ext = n_pos = n_coll = 0;
         err = 0;
     }
 };
-
-// Group `cnt` keys held in shared memory so that equal keys are adjacent:
-// counting sort by a key hash into B buckets (B a power of two, about cnt/2),
-// then within each bucket equal keys are gathered: small buckets by an
-// insertion sort on the 128-bit key (alpha word most significant), large ones
-// (a key with many duplicates) by repeated warp-wide partitions.  On return
-// perm[0..cnt) lists record indices bucket by bucket with equal keys
-// contiguous.  hist must be zero on entry and is left zero.
-template <class KeyAt>
-__device__ void group_keys(int cnt, int max_buckets, KeyAt key, uint16_t *perm, uint16_t *rnk, uint16_t *bkt,
-                           uint32_t *hist, uint32_t *warp_tot, unsigned int *nbig)
-{
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    int B = 32;
-    while (2 * B < cnt && B < max_buckets) B <<= 1;
-    if (tid == 0) *nbig = 0;
-    for (int i = tid; i < cnt; i += nt) {
-        uint64_t a, b;
-        key(i, a, b);
-        const uint32_t bb = bucket_hash(a, b) & (uint32_t)(B - 1);
-        bkt[i] = (uint16_t)bb;
-        rnk[i] = (uint16_t)atomicAdd(&hist[bb], 1u);
-    }
-    __syncthreads();
-    block_scan_excl_u32(hist, B, warp_tot);
-    for (int i = tid; i < cnt; i += nt) perm[hist[bkt[i]] + rnk[i]] = (uint16_t)i;
-    __syncthreads();
-    // small buckets: one thread each; large ones are queued for a warp (bkt is free now)
-    for (int bb = tid; bb < B; bb += nt) {
-        const int s = (int)hist[bb];
-        const int e = bb + 1 < B ? (int)hist[bb + 1] : cnt;
-        if (e - s <= 1) continue;
-        if (e - s > 24) {
-            bkt[atomicAdd(nbig, 1u)] = (uint16_t)bb;
-            continue;
-        }
-        uint64_t la, lb;  // last key of the sorted prefix
-        key(perm[s], la, lb);
-        for (int i = s + 1; i < e; ++i) {
-            const uint16_t x = perm[i];
-            uint64_t a, b;
-            key(x, a, b);
-            if (!key_less(a, b, la, lb)) {
-                la = a;
-                lb = b;
-                continue;
-            }
-            int j = i;
-            while (j > s) {
-                uint64_t pa, pb;
-                key(perm[j - 1], pa, pb);
-                if (!key_less(a, b, pa, pb)) break;
-                perm[j] = perm[j - 1];
-                --j;
-            }
-            perm[j] = x;
-        }
-    }
-    __syncthreads();
-    const int nb = (int)*nbig;
-    for (int q = warp; q < nb; q += nw) {
-        const int bb = bkt[q];
-        const int s = (int)hist[bb];
-        const int e = bb + 1 < B ? (int)hist[bb + 1] : cnt;
-        int pos = s;
-        while (pos < e) {
-            uint64_t ka, kb;
-            key(perm[pos], ka, kb);
-            int n_eq = 0, n_ne = 0;
-            for (int base = pos; base < e; base += 32) {
-                const int j = base + lane;
-                uint16_t x = 0;
-                bool eq = false;
-                if (j < e) {
-                    x = perm[j];
-                    uint64_t a, b;
-                    key(x, a, b);
-                    eq = a == ka && b == kb;
-                }
-                const unsigned m_eq = __ballot_sync(0xffffffffu, j < e && eq);
-                const unsigned m_ne = __ballot_sync(0xffffffffu, j < e && !eq);
-                const unsigned lt = (1u << lane) - 1u;
-                if (j < e) {
-                    if (eq) rnk[pos + n_eq + __popc(m_eq & lt)] = x;
-                    else rnk[e - 1 - (n_ne + __popc(m_ne & lt))] = x;
-                }
-                n_eq += __popc(m_eq);
-                n_ne += __popc(m_ne);
-            }
-            __syncwarp();
-            for (int j = pos + lane; j < e; j += 32) perm[j] = rnk[j];
-            __syncwarp();
-            pos += n_eq;
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < B; i += nt) hist[i] = 0;  // ready for the next call
-}
 
 __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long n, uint64_t a, uint64_t b)
 {
@@ -1536,25 +1626,23 @@ __device__ __forceinline__ bool in_slice(const uint64_t *rk, unsigned long long 
     return false;
 }
 
-// One unique key: explicit filter against the reference slice, then the
+// One distinct key: explicit filter against the reference slice, then the
 // Epstein-Nesbet term num^2 / (E0 - H_aa) of Eq. 3, added exactly.
 // In a spin-flip symmetric run (sym) a key with a > b stands for itself and
-// its mirror (b, a), whose term is the same, so it counts twice.
+// its mirror (b, a), whose term is the same, so it counts twice (one more
+// power of two in the fixed-point addition).
 __device__ __forceinline__ void finish_key(const TileParams &p, double e0, bool sym, const uint64_t *rk,
                                            unsigned long long nrk, uint64_t a, uint64_t b, double num, int64_t den,
                                            KeyStats &st)
 {
-    st.n_unique++;
-    if (in_slice(rk, nrk, a, b)) {
+    if (nrk && in_slice(rk, nrk, a, b)) {
         st.n_in_ref++;
         return;
     }
-    double d = den_to_double(den);
-    double term = (num * num) * recip(d, den);
-    if (sym && a != b) term += term;
-    fx_add_double(st.e2_lo, st.e2_hi, term, st.err);
+    fx_add_double(st.e2_lo, st.e2_hi, term_fx48(num, den), st.err,
+                  kFxShift + kDenShift + ((sym && a != b) ? 1 : 0));
     st.n_ext++;
-    uint64_t ad = den < 0 ? (uint64_t)(-den) : (uint64_t)den;
+    const uint64_t ad = den < 0 ? (uint64_t)(-den) : (uint64_t)den;
     st.min_den = ad < st.min_den ? ad : st.min_den;
     st.n_pos += den > 0;
     st.dsum += digest1(a, b);
@@ -1565,7 +1653,7 @@ __device__ __forceinline__ void finish_key(const TileParams &p, double e0, bool 
             p.dump_keys[2 * slot] = a;
             p.dump_keys[2 * slot + 1] = b;
             p.dump_num[slot] = num;
-            p.dump_haa[slot] = e0 - d;
+            p.dump_haa[slot] = e0 - den_to_double(den);
         }
     }
 }
@@ -1583,10 +1671,10 @@ __device__ void flush_stats(const TileParams &p, RunAcc *acc, KeyStats st, unsig
         st.dxor ^= __shfl_down_sync(0xffffffffu, st.dxor, off);
         uint64_t om = __shfl_down_sync(0xffffffffu, st.min_den, off);
         st.min_den = om < st.min_den ? om : st.min_den;
-        st.n_unique += __shfl_down_sync(0xffffffffu, st.n_unique, off);
         st.n_in_ref += __shfl_down_sync(0xffffffffu, st.n_in_ref, off);
         st.n_ext += __shfl_down_sync(0xffffffffu, st.n_ext, off);
         st.n_pos += __shfl_down_sync(0xffffffffu, st.n_pos, off);
+        st.n_coll += __shfl_down_sync(0xffffffffu, st.n_coll, off);
         st.err |= __shfl_down_sync(0xffffffffu, st.err, off);
     }
     if (lane == 0) {
@@ -1595,26 +1683,26 @@ __device__ void flush_stats(const TileParams &p, RunAcc *acc, KeyStats st, unsig
         red[2][warp] = st.dsum;
         red[3][warp] = st.dxor;
         red[4][warp] = st.min_den;
-        red[5][warp] = st.n_unique;
         red[6][warp] = st.n_in_ref;
         red[7][warp] = st.n_ext;
         red[8][warp] = st.n_pos;
         red[9][warp] = st.err;
+        red[10][warp] = st.n_coll;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint64_t lo = 0, dsum = 0, dxor = 0, mind = ~0ull, nu = 0, nr = 0, ne = 0, np = 0, er = 0;
+        uint64_t lo = 0, dsum = 0, dxor = 0, mind = ~0ull, nr = 0, ne = 0, np = 0, er = 0, nc = 0;
         int64_t hi = 0;
         for (int w = 0; w < nw; ++w) {
             fx_add_fx(lo, hi, red[0][w], (int64_t)red[1][w]);
             dsum += red[2][w];
             dxor ^= red[3][w];
             mind = red[4][w] < mind ? red[4][w] : mind;
-            nu += red[5][w];
             nr += red[6][w];
             ne += red[7][w];
             np += red[8][w];
             er |= red[9][w];
+            nc += red[10][w];
         }
         unsigned long long old = atomicAdd(&acc->e2_lo, (unsigned long long)lo);
         unsigned long long carry = (old + lo) < old ? 1ull : 0ull;
@@ -1622,10 +1710,11 @@ __device__ void flush_stats(const TileParams &p, RunAcc *acc, KeyStats st, unsig
         atomicAdd(&acc->dsum, dsum);
         atomicXor(&acc->dxor, dxor);
         atomicMin(&acc->min_den, mind);
-        atomicAdd(&acc->n_unique, nu);
+        atomicAdd(&acc->n_unique, nr + ne);
         atomicAdd(&acc->n_in_ref, nr);
         atomicAdd(&acc->n_ext, ne);
         atomicAdd(&acc->n_pos, np);
+        if (nc) atomicAdd(&acc->n_coll, nc);
         if (er) atomicOr(p.err, (unsigned)er);
     }
 }
@@ -1642,379 +1731,317 @@ __device__ const uint64_t *load_ref_slice(const TileParams &p, uint64_t t, uint6
     return p.ref_keys + 2 * s;
 }
 
-// ------------------------------------------- in-tile LSD radix sort + reduce
+constexpr uint32_t kNarrowMask = 0x03C00000u;  // 4 hash bits, all inside the bucket digit
+constexpr long long kWaitCycles = 1ll << 31;    // about a second
+constexpr long long kShortWaitCycles = 64;      // shorter than any global-memory copy
+
+// ------------------------------------------ in-tile bucket sort + reduce
 //
-// A tile (or a chunk of an oversize tile) of at most kSortCap records sits in
-// shared memory.  Each key is compressed to a 32-bit hash (the paper's
-// compression of keys by hash functions) carried in a 64-bit word with the
-// record's index, and the words are sorted with a stable LSD radix sort staged
-// through shared memory: three 8-bit digit passes over the low 24 hash bits
-// (a fourth over the top 8 bits only when two different keys share those 24),
-// each ranking items within a warp with __match_any_sync, scanning the
-// per-(digit, warp, item) counts into offsets and scattering.  Equal keys then
-// form contiguous runs; every run is verified against the full 128-bit key (a
-// remaining hash collision sends the chunk to an exact path) and reduced by
-// key.
+// A tile (or a chunk of an oversize tile) of at most kGrpCap records sits in
+// shared memory.  Its records are sorted so that equal keys share a bucket
+// and every key is reduced once (the sort and the single pass of
+// Algorithm 1):
+//   1. one counting-sort pass on the top 10 bits of a 32-bit hash of the key
+//      (1024 buckets): a record's rank inside its bucket from a
+//      shared-memory atomic, bucket starts from a block scan, one scatter;
+//   2. one lane per record: it heads its key if no earlier record of its
+//      bucket has the same (hash, alpha word, beta word).  Keys that share
+//      the 32-bit hash are told apart by the full 128-bit comparison, so the
+//      grouping is exact whatever the hash does;
+//   3. one lane per distinct key: the head adds up the records of its key
+//      that follow it in the bucket and finishes the key; a head with a long
+//      tail (a key with many duplicates) is summed by a warp.
+// A key's numerator is the exact fixed-point sum of its contributions (a
+// single contribution is rounded to the same 2^-90 grid), so the result does
+// not depend on the order in which records meet, on the tiling or on which
+// path summed the key.  E0 - H_aa is the same exact integer in every record of
+// a key (it is assembled from integer tables), so the head record supplies it.
 
-constexpr int kSortThreads = kTileThreads;
-constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = kSortCap / kSortThreads;  // items per thread
-constexpr int kWarpSpan = kSortCap / kSortWarps;     // positions a warp ranks in a digit pass
-constexpr int kSortCtasPerSm = 1024 / kSortThreads;  // sorting CTAs per SM the registers are sized for
-constexpr int kLongRun = 8;                          // longer runs are summed by a warp
-static_assert(kSortItems * kSortThreads == kSortCap, "the sort holds whole items per thread");
-static_assert(kWarpSpan == 32 * kSortItems, "a warp ranks whole rows of 32 positions");
-static_assert(kSortThreads % 256 == 0, "the first 256 threads take one digit each in the offset scan");
-static_assert(kBigThreads == kSortThreads, "every sorting CTA has the sort's width");
-static_assert(kBigChunk <= kSortCap && kBigCap <= kSortCap && kTileCap <= kSortCap, "chunks fit one sort");
+constexpr int kGrpThreads = kTileThreads;
+constexpr int kGrpWarps = kGrpThreads / 32;
+constexpr int kGrpCap = kTileCap;
+constexpr int kGrpBuckets = 1024;
+constexpr int kGrpItems = kGrpCap / kGrpThreads;  // records per thread
+constexpr int kGrpBktShift = 22;                  // bucket = top 10 bits of the hash
+constexpr int kLongTail = 16;                     // heads with more records after them are summed by a warp
+constexpr int kTileCtasPerSm = 4;                 // resident tile CTAs the registers are sized for
+static_assert(kGrpBuckets == 4 * kGrpThreads, "each thread clears four buckets");
+static_assert(kGrpBuckets == (1 << (32 - kGrpBktShift)), "the bucket digit is the top bits of the hash");
+static_assert(kGrpCap <= 1024 && kGrpItems * kGrpThreads == kGrpCap, "record indices take 10 bits");
+static_assert(kBigThreads == kGrpThreads, "every grouping CTA has the grouping's width");
+static_assert(kBigChunk <= kGrpCap && kBigCap <= kGrpCap, "chunks fit one grouping");
+static_assert(kGrpCap / (kLongTail + 1) <= kGrpThreads, "long heads fit their list");
 
-struct SortSmem {
-    uint64_t words[2][kSortCap];  // (hash << 16) | record index
-    union {
-        uint16_t cnt[kSortWarps][256];  // digit pass: per-warp digit counts, then offsets
-        struct {
-            uint16_t heads[kSortCap], longq[kSortCap];  // after the passes: run heads, long runs
-        } h;
-        unsigned long long red[10][32];  // final statistics reduction
-    } u;
-    uint16_t dbase[256];
-    uint32_t warp_tot[33];
-    unsigned int nheads, nlong, collision;
+struct GrpSmem {
+    uint64_t ent[kGrpCap];      // (hash << 32) | record index, bucket by bucket
+    uint32_t cnt[kGrpBuckets];  // bucket sizes, then bucket starts; zero between groupings
+    uint16_t uniq[kGrpCap];     // position (in ent) of the head of each distinct key
+    uint16_t lng[kGrpThreads];  // heads with a long tail
+    uint32_t warp_tot[kGrpWarps];
+    unsigned int nuniq, nlong;
 };
 
-__device__ __forceinline__ uint32_t key_hash32(uint64_t a, uint64_t b)
+// Distinct keys listed by the last grouping (its heads, then its long heads).
+__device__ __forceinline__ int group_keys(const GrpSmem &G) { return (int)(G.nuniq + G.nlong); }
+
+// 32-bit hash that orders the records of a tile.  The keys of a tile share
+// its tile hash (a Zobrist hash of the key), so this one mixes the two words
+// with unrelated multipliers.
+__device__ __forceinline__ uint32_t sort_hash(uint64_t a, uint64_t b)
 {
-    uint64_t h = (a ^ 0x2545F4914F6CDD1Dull) * 0x9E3779B97F4A7C15ull;
-    h ^= b;
-    h *= 0xBF58476D1CE4E5B9ull;
-    h ^= h >> 31;
-    h *= 0x94D049BB133111EBull;
+    uint64_t h = (a * 0x9E3779B97F4A7C15ull) ^ b;
+    h ^= h >> 32;
+    h *= 0xD6E8FEB86659FD93ull;
     return (uint32_t)(h >> 32);
 }
 
-// One stable counting-sort pass on the 8-bit digit at `shift` of the hash.
-// Warp w ranks positions [w * kWarpSpan, (w + 1) * kWarpSpan) row by row (32
-// positions per row, in order): __match_any_sync gives each item its rank
-// among equal digits of the row, added to the warp's running count of that
-// digit, which the row's lowest such lane then advances.  The counts live in
-// a per-warp table, so it is cleared with a warp barrier only.  Thread d then
-// turns digit d's per-warp counts into offsets and a block scan gives the
-// digit bases; every item lands at base + warp offset + rank.
-__device__ __forceinline__ void lsd_pass(const uint64_t *src, uint64_t *dst, int cnt, int shift, SortSmem &S)
+// A single contribution as the exact fixed-point sum gives it: values from
+// 2^-38 up are on the 2^-90 grid already, smaller ones are rounded to it,
+// values of 2^36 and more are out of range.
+__device__ __forceinline__ double canon_num(double v, uint32_t &err)
+{
+    const int e = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+    if (e >= 1023 - 38 && e < 1023 + 36) return v;
+    uint64_t lo = 0;
+    int64_t hi = 0;
+    fx_add_double(lo, hi, v, err);
+    return fx_to_double(lo, hi);
+}
+
+// Record access for the grouping: the key, and adding a record's numerator
+// to an exact fixed-point sum.
+struct R32 {
+    using Rec = Rec32;
+    static __device__ __forceinline__ void key(const Rec32 *r, int i, uint64_t &a, uint64_t &b)
+    {
+        const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(r + i);
+        a = k.x;
+        b = k.y;
+    }
+    static __device__ __forceinline__ void add(const Rec32 *r, int i, uint64_t &fl, int64_t &fh, uint32_t &err)
+    {
+        fx_add_double(fl, fh, r[i].num, err);
+    }
+};
+struct R48 {
+    using Rec = Rec48;
+    static __device__ __forceinline__ void key(const Rec48 *r, int i, uint64_t &a, uint64_t &b)
+    {
+        const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(r + i);
+        a = k.x;
+        b = k.y;
+    }
+    static __device__ __forceinline__ void add(const Rec48 *r, int i, uint64_t &fl, int64_t &fh, uint32_t &)
+    {
+        fx_add_fx(fl, fh, r[i].fx_lo, r[i].fx_hi);
+    }
+};
+
+// Group the cnt <= kGrpCap records of `recs` (shared memory) by key.  Every
+// distinct key is handed to run(head, exact, fl, fh), once, by one thread:
+// head is the index of one of its records; if exact, (fl, fh) is the exact
+// numerator sum of all its records, otherwise head is its only record.  On
+// return G.uniq[0, group_keys(G)) lists the head record of every distinct key
+// (for a dense finish by the caller).  hmask narrows the hash (a test aid
+// that makes most keys of a tile share their hash and bucket).  Returns how
+// often this thread met two different keys with the same hash.  Every thread
+// of the CTA must call it; it starts after and ends with a barrier.
+template <class R, class Run>
+__device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t hmask, GrpSmem &G, uint32_t &err,
+                                  Run &&run)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint16_t *wc = S.u.cnt[warp];
-    reinterpret_cast<uint4 *>(wc)[lane] = make_uint4(0, 0, 0, 0);  // 32 lanes x 16 B = 256 counts
-    __syncwarp();
-    uint64_t w[kSortItems];
-    uint32_t dig[kSortItems], rank[kSortItems];
     const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = warp * kWarpSpan + it * 32 + lane;
-        const bool valid = pos < cnt;
-        w[it] = valid ? src[pos] : 0ull;
-        const uint32_t d = (uint32_t)(w[it] >> (16 + shift)) & 0xFFu;
-        // past-the-end lanes get a value no real digit has, so they match nobody
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 256u + lane);
-        dig[it] = d;
-        const uint32_t before = valid ? wc[d] : 0u;
-        rank[it] = before + __popc(peers & lt);
-        __syncwarp();
-        if (valid && (peers & lt) == 0) wc[d] = (uint16_t)(before + __popc(peers));
-        __syncwarp();
+    if (tid == 0) {
+        G.nuniq = 0;
+        G.nlong = 0;
     }
-    __syncthreads();
-    // thread d < 256: offsets of digit d within each warp's share, and its total
-    uint32_t total_d = 0;
-    if (tid < 256) {
-        const int d = tid;
+    // 1. hash and rank within the bucket
+    uint32_t hh[kGrpItems], rk[kGrpItems];
 #pragma unroll
-        for (int k = 0; k < kSortWarps; ++k) {
-            const uint32_t c = S.u.cnt[k][d];
-            S.u.cnt[k][d] = (uint16_t)total_d;
-            total_d += c;
+    for (int k = 0; k < kGrpItems; ++k) {
+        const int i = tid + k * kGrpThreads;
+        hh[k] = 0;
+        rk[k] = 0;
+        if (i < cnt) {
+            uint64_t a, b;
+            R::key(recs, i, a, b);
+            hh[k] = sort_hash(a, b) & hmask;
+            rk[k] = atomicAdd(&G.cnt[hh[k] >> kGrpBktShift], 1u);
         }
     }
-    // exclusive scan of the digit totals over warps 0..7: the digit bases
+    __syncthreads();
+    // bucket starts (thread t scans buckets 4t .. 4t + 3)
     {
-        uint32_t incl = total_d;
+        const uint4 c4 = reinterpret_cast<const uint4 *>(G.cnt)[tid];
+        const uint32_t sz = c4.x + c4.y + c4.z + c4.w;
+        uint32_t incl = sz;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += t;
         }
-        if (lane == 31 && warp < 8) S.warp_tot[warp] = incl;
+        if (lane == 31) G.warp_tot[warp] = incl;
         __syncthreads();
-        if (tid < 256) {
-            uint32_t base = 0;
+        uint32_t lo = incl - sz;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) base += k < warp ? S.warp_tot[k] : 0u;
-            S.dbase[tid] = (uint16_t)(base + incl - total_d);
-        }
+        for (int w = 0; w < kGrpWarps; ++w) lo += w < warp ? G.warp_tot[w] : 0u;
+        reinterpret_cast<uint4 *>(G.cnt)[tid] = make_uint4(lo, lo + c4.x, lo + c4.x + c4.y, lo + c4.x + c4.y + c4.z);
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = warp * kWarpSpan + it * 32 + lane;
-        if (pos < cnt) dst[S.dbase[dig[it]] + S.u.cnt[warp][dig[it]] + rank[it]] = w[it];
+    for (int k = 0; k < kGrpItems; ++k) {
+        const int i = tid + k * kGrpThreads;
+        if (i < cnt) G.ent[G.cnt[hh[k] >> kGrpBktShift] + rk[k]] = ((uint64_t)hh[k] << 32) | (uint32_t)i;
     }
     __syncthreads();
-}
-
-// Value of one unique key handed to a consumer: the numerator either as the
-// FP64 value of a single record or as an exact fixed-point sum.
-struct KeyVal {
-    uint64_t a, b;
-    bool fixed;
-    double num;
-    uint64_t fl;
-    int64_t fh;
-    int64_t den;
-};
-
-template <class Rec>
-__device__ __forceinline__ void rec_value(const Rec &r, bool &fixed, double &num, uint64_t &fl, int64_t &fh);
-template <>
-__device__ __forceinline__ void rec_value<Rec32>(const Rec32 &r, bool &fixed, double &num, uint64_t &fl, int64_t &fh)
-{
-    fixed = false;
-    num = r.num;
-    fl = 0;
-    fh = 0;
-}
-template <>
-__device__ __forceinline__ void rec_value<Rec48>(const Rec48 &r, bool &fixed, double &num, uint64_t &fl, int64_t &fh)
-{
-    fixed = true;
-    num = 0.0;
-    fl = r.fx_lo;
-    fh = r.fx_hi;
-}
-__device__ __forceinline__ void rec_add(const Rec32 &r, uint64_t &fl, int64_t &fh, uint32_t &err)
-{
-    fx_add_double(fl, fh, r.num, err);
-}
-__device__ __forceinline__ void rec_add(const Rec48 &r, uint64_t &fl, int64_t &fh, uint32_t &)
-{
-    fx_add_fx(fl, fh, r.fx_lo, r.fx_hi);
-}
-
-// Sort the chunk and hand every unique key to `emit` (any order; every thread
-// may call it).  Returns false, for all threads, if two different keys share
-// a hash; then nothing was emitted and the caller must use the exact path.
-template <class Rec, class Emit>
-__device__ bool sort_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_t &err, Emit &&emit)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint64_t *A = S.words[0], *B = S.words[1];
-    if (tid == 0) {
-        S.nheads = 0;
-        S.nlong = 0;
-        S.collision = 0;
-    }
+    // 2. one lane per record: does an earlier record of its bucket have its key?
+    uint32_t coll = 0;
 #pragma unroll
-    for (int it = 0; it < kSortItems; ++it) {
-        const int pos = it * kSortThreads + tid;
-        if (pos < cnt) A[pos] = ((uint64_t)key_hash32(recs[pos].a, recs[pos].b) << 16) | (uint64_t)pos;
-    }
-    __syncthreads();
-    // three digit passes order the words by the low 24 hash bits; a fourth
-    // (the top 8 bits) runs only if two different keys share those 24 bits
-    lsd_pass(A, B, cnt, 0, S);
-    lsd_pass(B, A, cnt, 8, S);
-    lsd_pass(A, B, cnt, 16, S);
-    uint64_t hmask = 0xFFFFFFull << 16;
-    A = S.words[1];
-    for (int round = 0; round < 2; ++round) {
-        // heads of equal-hash runs; a run must also hold a single 128-bit key
-#pragma unroll
-        for (int it = 0; it < kSortItems; ++it) {
-            const int pos = it * kSortThreads + tid;
-            bool head = false;
-            if (pos < cnt) {
-                const uint64_t wv = A[pos];
-                head = pos == 0 || (A[pos - 1] & hmask) != (wv & hmask);
-                if (!head) {
-                    const Rec &r0 = recs[wv & 0xFFFF], &rp = recs[A[pos - 1] & 0xFFFF];
-                    if (r0.a != rp.a || r0.b != rp.b) S.collision = 1;
+    for (int k = 0; k < kGrpItems; ++k) {
+        const int pos = tid + k * kGrpThreads;
+        bool head = false, longh = false;
+        if (pos < cnt) {
+            const uint64_t e = G.ent[pos];
+            const uint32_t h = (uint32_t)(e >> 32);
+            const uint32_t bk = h >> kGrpBktShift;
+            const int bs = (int)G.cnt[bk];
+            head = true;
+            if (bs < pos) {
+                uint64_t a, b;
+                R::key(recs, (int)(e & 0x3FFu), a, b);
+                for (int j = bs; j < pos; ++j) {
+                    const uint64_t ej = G.ent[j];
+                    if ((uint32_t)(ej >> 32) != h) continue;
+                    uint64_t a2, b2;
+                    R::key(recs, (int)(ej & 0x3FFu), a2, b2);
+                    if (a2 == a && b2 == b) {
+                        head = false;
+                        break;
+                    }
+                    ++coll;
                 }
             }
-            const uint32_t m = __ballot_sync(0xffffffffu, head);
+            if (head) {
+                const int be = bk + 1 < (uint32_t)kGrpBuckets ? (int)G.cnt[bk + 1] : cnt;
+                longh = be - pos - 1 > kLongTail;
+            }
+        }
+        const bool shorth = head && !longh;
+        const uint32_t m = __ballot_sync(0xffffffffu, shorth);
+        if (m) {
+            const int leader = __ffs(m) - 1;
             uint32_t base = 0;
-            if (lane == 0 && m) base = atomicAdd(&S.nheads, (unsigned)__popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (head) S.u.h.heads[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pos;
+            if (lane == leader) base = atomicAdd(&G.nuniq, (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (shorth) G.uniq[base + __popc(m & lt)] = (uint16_t)pos;
         }
-        __syncthreads();
-        if (!S.collision) break;
-        if (round == 1) return false;
-        __syncthreads();
-        if (tid == 0) {
-            S.nheads = 0;
-            S.collision = 0;
-        }
-        lsd_pass(S.words[1], S.words[0], cnt, 24, S);
-        A = S.words[0];
-        hmask = 0xFFFFFFFFull << 16;
-    }
-    const int nh = (int)S.nheads;
-    for (int h = tid; h < nh; h += kSortThreads) {
-        const int j = S.u.h.heads[h];
-        const uint64_t hj = A[j] & hmask;
-        const Rec &r0 = recs[A[j] & 0xFFFF];
-        KeyVal v;
-        v.a = r0.a;
-        v.b = r0.b;
-        v.den = r0.den;
-        rec_value(r0, v.fixed, v.num, v.fl, v.fh);
-        if (j + 1 < cnt && (A[j + 1] & hmask) == hj) {
-            if (j + kLongRun < cnt && (A[j + kLongRun] & hmask) == hj) {
-                S.u.h.longq[atomicAdd(&S.nlong, 1u)] = (uint16_t)j;
-                continue;
-            }
-            uint64_t fl = 0;
-            int64_t fh = 0;
-            rec_add(r0, fl, fh, err);
-            for (int k = j + 1; k < cnt && (A[k] & hmask) == hj; ++k) {
-                const Rec &r2 = recs[A[k] & 0xFFFF];
-                rec_add(r2, fl, fh, err);
-                v.den = r2.den < v.den ? r2.den : v.den;
-            }
-            v.fixed = true;
-            v.fl = fl;
-            v.fh = fh;
-        }
-        emit(v);
+        if (longh) G.lng[atomicAdd(&G.nlong, 1u)] = (uint16_t)pos;
     }
     __syncthreads();
-    const int nl = (int)S.nlong;
-    for (int q = warp; q < nl; q += kSortThreads / 32) {
-        const int j = S.u.h.longq[q];
-        const uint64_t hj = A[j] & hmask;
+    // 3. one lane per distinct key: its records follow its head in the bucket
+    const int nu = (int)G.nuniq;
+    for (int u = tid; u < nu; u += kGrpThreads) {
+        const int pos = G.uniq[u];
+        const uint64_t e = G.ent[pos];
+        const uint32_t h = (uint32_t)(e >> 32);
+        const int idx = (int)(e & 0x3FFu);
+        const uint32_t bk = h >> kGrpBktShift;
+        const int be = bk + 1 < (uint32_t)kGrpBuckets ? (int)G.cnt[bk + 1] : cnt;
+        bool multi = false;
         uint64_t fl = 0;
         int64_t fh = 0;
-        int64_t den = recs[A[j] & 0xFFFF].den;
-        for (int base = j; base < cnt; base += 32) {
-            const int k = base + lane;
-            const bool same = k < cnt && (A[k] & hmask) == hj;
-            if (same) {
-                const Rec &r = recs[A[k] & 0xFFFF];
-                rec_add(r, fl, fh, err);
-                den = r.den < den ? r.den : den;
+        if (pos + 1 < be) {
+            uint64_t a, b;
+            R::key(recs, idx, a, b);
+            for (int q = pos + 1; q < be; ++q) {
+                const uint64_t eq = G.ent[q];
+                if ((uint32_t)(eq >> 32) != h) continue;
+                const int iq = (int)(eq & 0x3FFu);
+                uint64_t a2, b2;
+                R::key(recs, iq, a2, b2);
+                if (a2 != a || b2 != b) continue;
+                if (!multi) R::add(recs, idx, fl, fh, err);
+                multi = true;
+                R::add(recs, iq, fl, fh, err);
             }
-            if (__ballot_sync(0xffffffffu, same) != 0xffffffffu) break;
+        }
+        run(idx, multi, fl, fh);
+        G.uniq[u] = (uint16_t)idx;
+    }
+    // heads with a long tail, a warp each
+    const int nlg = (int)G.nlong;
+    for (int q0 = warp; q0 < nlg; q0 += kGrpWarps) {
+        const int pos = G.lng[q0];
+        const uint64_t e = G.ent[pos];
+        const uint32_t h = (uint32_t)(e >> 32);
+        const int idx = (int)(e & 0x3FFu);
+        const uint32_t bk = h >> kGrpBktShift;
+        const int be = bk + 1 < (uint32_t)kGrpBuckets ? (int)G.cnt[bk + 1] : cnt;
+        uint64_t a, b;
+        R::key(recs, idx, a, b);
+        uint64_t fl = 0;
+        int64_t fh = 0;
+        for (int base = pos; base < be; base += 32) {
+            const int q = base + lane;
+            if (q < be) {
+                const uint64_t eq = G.ent[q];
+                if ((uint32_t)(eq >> 32) == h) {
+                    const int iq = (int)(eq & 0x3FFu);
+                    uint64_t a2, b2;
+                    R::key(recs, iq, a2, b2);
+                    if (a2 == a && b2 == b) R::add(recs, iq, fl, fh, err);
+                }
+            }
         }
 #pragma unroll
         for (int off = 16; off; off >>= 1) {
-            const uint64_t olo = __shfl_down_sync(0xffffffffu, fl, off);
-            const int64_t ohi = __shfl_down_sync(0xffffffffu, fh, off);
-            const int64_t od = __shfl_down_sync(0xffffffffu, den, off);
-            fx_add_fx(fl, fh, olo, ohi);
-            den = od < den ? od : den;
+            const uint64_t ol = __shfl_down_sync(0xffffffffu, fl, off);
+            const int64_t oh = __shfl_down_sync(0xffffffffu, fh, off);
+            fx_add_fx(fl, fh, ol, oh);
         }
         if (lane == 0) {
-            const Rec &r0 = recs[A[j] & 0xFFFF];
-            KeyVal v;
-            v.a = r0.a;
-            v.b = r0.b;
-            v.fixed = true;
-            v.num = 0.0;
-            v.fl = fl;
-            v.fh = fh;
-            v.den = den;
-            emit(v);
+            run(idx, true, fl, fh);
+            G.uniq[nu + q0] = (uint16_t)idx;
         }
     }
+    __syncthreads();  // every reader of the bucket starts is done
+    reinterpret_cast<uint4 *>(G.cnt)[tid] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    return true;
-}
-
-// Exact fallback for a chunk whose hash compression collided: bucket the keys
-// by a second hash and insertion-sort each bucket by the full key (slow, and
-// only reached with probability ~cnt^2 / 2^33 per chunk).
-template <class Rec, class Emit>
-__device__ void exact_reduce_chunk(const Rec *recs, int cnt, SortSmem &S, uint32_t &err, Emit &&emit)
-{
-    uint16_t *perm = reinterpret_cast<uint16_t *>(S.words[0]);
-    uint16_t *rnk = reinterpret_cast<uint16_t *>(S.words[0]) + kSortCap;
-    uint16_t *bkt = reinterpret_cast<uint16_t *>(S.words[0]) + 2 * kSortCap;
-    uint32_t *hist = reinterpret_cast<uint32_t *>(S.words[1]);
-    for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    auto key = [&](int i, uint64_t &a, uint64_t &b) {
-        a = recs[i].a;
-        b = recs[i].b;
-    };
-    group_keys(cnt, kSortCap, key, perm, rnk, bkt, hist, S.warp_tot, &S.nlong);
-    const int nt = blockDim.x;
-    const int chunk = (cnt + nt - 1) / nt;
-    const int s = threadIdx.x * chunk, e = min(cnt, s + chunk);
-    for (int j = s; j < e; ++j) {
-        const Rec &r0 = recs[perm[j]];
-        if (j > 0) {
-            const Rec &rp = recs[perm[j - 1]];
-            if (rp.a == r0.a && rp.b == r0.b) continue;
-        }
-        KeyVal v;
-        v.a = r0.a;
-        v.b = r0.b;
-        v.fixed = true;
-        v.num = 0.0;
-        v.fl = 0;
-        v.fh = 0;
-        v.den = r0.den;
-        for (int k = j; k < cnt; ++k) {
-            const Rec &r2 = recs[perm[k]];
-            if (k > j && (r2.a != r0.a || r2.b != r0.b)) break;
-            rec_add(r2, v.fl, v.fh, err);
-            v.den = r2.den < v.den ? r2.den : v.den;
-        }
-        emit(v);
-    }
-    __syncthreads();
-}
-
-// One unique key into the statistics (filter + Eq. 3 term).
-__device__ __forceinline__ void finish_keyval(const TileParams &p, double e0, bool sym, const uint64_t *rk,
-                                              unsigned long long nrk, const KeyVal &v, KeyStats &st)
-{
-    finish_key(p, e0, sym, rk, nrk, v.a, v.b, v.fixed ? fx_to_double(v.fl, v.fh) : v.num, v.den, st);
+    return coll;
 }
 
 // Shared memory of the main tile kernel (several CTAs share an SM, so one CTA's
 // tile load and barriers overlap the others' work).
 struct MainSmem {
     Rec32 recs[kTileCap];
-    SortSmem S;
+    GrpSmem G;
     uint64_t rk[2 * kRefSliceSmem];
     unsigned long long meta[4];  // current tile: offset, count, reference offset, reference count
+    unsigned long long next[4];  // the same for the CTA's next tile (thread 0 reads it one tile ahead)
     uint64_t bar[2];
 };
+static_assert(sizeof(GrpSmem::ent) >= 11 * 32 * sizeof(unsigned long long), "statistics reduce in the entry area");  // rows 0-4, 6-10
 
 size_t tile_smem_bytes() { return sizeof(MainSmem); }
 
-struct TileMeta {
-    unsigned long long off, cnt, roff, rcnt;
-};
-
-__device__ __forceinline__ TileMeta tile_meta(const TileParams &p, uint64_t t)
+__device__ __forceinline__ void tile_meta(const TileParams &p, uint64_t t, unsigned long long *m)
 {
-    TileMeta m{0, 0, 0, 0};
+    m[0] = m[1] = m[2] = m[3] = 0;
     if (t < p.n_tiles) {
-        m.off = p.tile_off[t];
-        m.cnt = p.tile_off[t + 1] - m.off;
-        m.roff = p.ref_off[t];
-        m.rcnt = p.ref_off[t + 1] - m.roff;
+        m[0] = p.tile_off[t];
+        m[1] = p.tile_off[t + 1] - m[0];
+        m[2] = p.ref_off[t];
+        m[3] = p.ref_off[t + 1] - m[2];
     }
-    return m;
 }
 
-__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, const TileMeta &m)
+// Thread 0: start the bulk copy of the tile described by m (if it fits).
+__device__ __forceinline__ void issue_tile(const TileParams &p, MainSmem &M, const unsigned long long *m)
 {
-    if (m.cnt == 0 || m.cnt > (unsigned long long)kTileCap) return;
+    if (m[1] == 0 || m[1] > (unsigned long long)kTileCap) return;
     fence_proxy_async_smem();
-    bulk_load(M.recs, p.recs + m.off, (uint32_t)(m.cnt * sizeof(Rec32)), &M.bar[0]);
+    bulk_load(M.recs, p.recs + m[0], (uint32_t)(m[1] * sizeof(Rec32)), &M.bar[0]);
 }
 
 __device__ __forceinline__ void push_oversize(const TileParams &p, int inst, uint64_t t, unsigned long long cnt)
@@ -2036,50 +2063,57 @@ __device__ __forceinline__ int tile_instance(const unsigned long long *__restric
     return lo;
 }
 
+// Statistics reduction area (the grouping's entries, free between tiles).
+__device__ __forceinline__ unsigned long long (*red_area(GrpSmem &G))[32]
+{
+    return reinterpret_cast<unsigned long long (*)[32]>(G.ent);
+}
+
 // Persistent: CTA g handles tiles g, g + G, g + 2G, ...  Thread 0 keeps the
 // tile metadata one tile ahead, so each tile's TMA load starts at once.
 // Tiles of one instance are consecutive, so a CTA's statistics are flushed
 // to an instance's accumulator when its tiles move on to the next instance.
+// A bulk copy that does not complete within the wait limit stops the CTA
+// (the run then reports the timeout).
 template <bool SYM>
-__global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(const TileParams p)
+__global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MainSmem &M = *reinterpret_cast<MainSmem *>(smem_raw);
     const uint64_t G = gridDim.x;
     KeyStats st;
     st.clear();
-    TileMeta nx{0, 0, 0, 0};
     if (threadIdx.x == 0) {
         mbar_init(&M.bar[0], 1);
-        nx = tile_meta(p, blockIdx.x);
+        tile_meta(p, blockIdx.x, M.next);
     }
+    for (int i = threadIdx.x; i < kGrpBuckets; i += blockDim.x) M.G.cnt[i] = 0;
     __syncthreads();
-    // current instance, the first tile past it and its E0, kept in registers
-    // (a CTA's tiles increase, so they only change at instance boundaries)
+    // current instance, the first tile past it and its options, kept in
+    // registers (a CTA's tiles increase, so they only change at instance boundaries)
     int cur = tile_instance(p.tile_base, p.n_inst, blockIdx.x);
     unsigned long long cur_end = p.tile_base[cur + 1];
     double e0 = p.e0[cur];
-    bool sym = SYM && p.sym[cur] != 0;
+    uint32_t fl = p.iflags[cur];
     bool dirty = false;
     uint32_t phase = 0;
     for (uint64_t t = blockIdx.x; t < p.n_tiles; t += G) {
         if (t >= cur_end) {  // uniform across the CTA
-            if (dirty) flush_stats(p, p.acc[cur], st, M.S.u.red);
+            if (dirty) flush_stats(p, p.acc[cur], st, red_area(M.G));
             st.clear();
             dirty = false;
             cur = tile_instance(p.tile_base, p.n_inst, t);
             cur_end = p.tile_base[cur + 1];
             e0 = p.e0[cur];
-            sym = SYM && p.sym[cur] != 0;
+            fl = p.iflags[cur];
         }
+        const bool sym = SYM && (fl & kInstSym);
+        const uint32_t hmask = (fl & kInstNarrow) ? kNarrowMask : 0xFFFFFFFFu;
         const int inst = cur;
         if (threadIdx.x == 0) {
-            issue_tile(p, M, nx);
-            M.meta[0] = nx.off;
-            M.meta[1] = nx.cnt;
-            M.meta[2] = nx.roff;
-            M.meta[3] = nx.rcnt;
-            nx = tile_meta(p, t + G);  // consumed next iteration
+            issue_tile(p, M, M.next);
+            for (int k = 0; k < 4; ++k) M.meta[k] = M.next[k];
+            tile_meta(p, t + G, M.next);  // consumed next iteration
         }
         __syncthreads();
         const unsigned long long cntl = M.meta[1];
@@ -2095,16 +2129,28 @@ __global__ void __launch_bounds__(kTileThreads, kSortCtasPerSm) tile_kernel(cons
             } else {
                 rk = p.ref_keys + 2 * roff;
             }
-            mbar_wait_bounded(&M.bar[0], phase, p.err);
+            const bool ok =
+                mbar_wait_bounded(&M.bar[0], phase, p.err, (fl & kInstShortWait) ? kShortWaitCycles : kWaitCycles);
             phase ^= 1u;
-            const bool ok = sort_reduce_chunk(M.recs, cnt, M.S, st.err,
-                                              [&](const KeyVal &v) { finish_keyval(p, e0, sym, rk, rcnt, v, st); });
-            if (!ok && threadIdx.x == 0) push_oversize(p, inst, t, cntl);  // exact path for a hash collision
+            if (__syncthreads_or(!ok)) break;
+            Rec32 *recs = M.recs;
+            // the head record of each key takes the key's numerator ...
+            st.n_coll += group_records<R32>(recs, cnt, hmask, M.G, st.err,
+                                            [&](int head, bool exact, uint64_t sl, int64_t sh) {
+                                                recs[head].num =
+                                                    exact ? fx_to_double(sl, sh) : canon_num(recs[head].num, st.err);
+                                            });
+            // ... and every lane finishes one key at a time
+            const int nk = group_keys(M.G);
+            for (int u = threadIdx.x; u < nk; u += kTileThreads) {
+                const Rec32 r = recs[M.G.uniq[u]];
+                finish_key(p, e0, sym, rk, rcnt, r.a, r.b, r.num, r.den, st);
+            }
             dirty = true;
         }
-        __syncthreads();  // records, slice and metadata free for the next tile
+        __syncthreads();  // records, slice, entries and metadata free for the next tile
     }
-    if (dirty) flush_stats(p, p.acc[cur], st, M.S.u.red);
+    if (dirty) flush_stats(p, p.acc[cur], st, red_area(M.G));
     __syncthreads();
     if (threadIdx.x == 0) mbar_inval(&M.bar[0]);
 }
@@ -2121,17 +2167,17 @@ cudaError_t launch_tiles(const TileParams &p, int n_ctas, cudaStream_t s)
 
 // ------------------------------------------------------ oversize tiles
 
-// Tiles above shared-memory capacity (keys with many duplicates, or a tile
-// whose hash compression collided): each chunk is sorted and reduced to
-// (key, exact fixed-point numerator, min denominator) records; the reduced
-// list is processed again until it fits one chunk, then finished like a
-// normal tile.  Exact sums make the result independent of the chunking.
+// Tiles above shared-memory capacity (keys with many duplicates): each chunk
+// is grouped and reduced to (key, exact fixed-point numerator, denominator)
+// partials; the partial list is grouped again until it fits one chunk, then
+// finished like a normal tile.  Exact sums make the result independent of
+// the chunking.
 struct BigSmem {
     union {
         Rec32 r32[kBigChunk];
         Rec48 r48[kBigCap];
     } u;
-    SortSmem S;
+    GrpSmem G;
     uint64_t rk[2 * kRefSliceSmem];
     uint64_t bar;
     unsigned int out_count;
@@ -2142,28 +2188,25 @@ struct BigSmem {
 
 size_t big_smem_bytes() { return sizeof(BigSmem); }
 
-template <class Rec>
-__device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst, uint32_t &err)
+// One chunk of records -> exact partials appended to dst (out_count of them).
+__device__ uint32_t chunk_to_partials(Rec32 *recs, int m, BigSmem &M, Rec48 *dst, uint32_t hmask, uint32_t &err)
 {
-    auto put = [&](const KeyVal &v) {
+    return group_records<R32>(recs, m, hmask, M.G, err, [&](int head, bool exact, uint64_t sl, int64_t sh) {
+        const Rec32 &r = recs[head];
         Rec48 o;
-        o.a = v.a;
-        o.b = v.b;
-        if (v.fixed) {
-            o.fx_lo = v.fl;
-            o.fx_hi = v.fh;
-        } else {
-            uint64_t fl = 0;
-            int64_t fh = 0;
-            fx_add_double(fl, fh, v.num, err);
-            o.fx_lo = fl;
-            o.fx_hi = fh;
+        o.a = r.a;
+        o.b = r.b;
+        if (!exact) {
+            sl = 0;
+            sh = 0;
+            fx_add_double(sl, sh, r.num, err);
         }
-        o.den = v.den;
+        o.fx_lo = sl;
+        o.fx_hi = sh;
+        o.den = r.den;
         o.pad = 0;
         dst[atomicAdd(&M.out_count, 1u)] = o;
-    };
-    if (!sort_reduce_chunk(recs, m, M.S, err, put)) exact_reduce_chunk(recs, m, M.S, err, put);
+    });
 }
 
 // Persistent over the oversize tiles of all instances, numbered in one index
@@ -2174,7 +2217,7 @@ __device__ void chunk_to_partials(const Rec *recs, int m, BigSmem &M, Rec48 *dst
 // two buffers of scratch_cap records; a tile whose partials outgrow it sets
 // kErrScratch.
 template <bool SYM>
-__global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(const TileParams p)
+__global__ void __launch_bounds__(kBigThreads, kTileCtasPerSm) big_tile_kernel(const TileParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BigSmem &M = *reinterpret_cast<BigSmem *>(smem_raw);
@@ -2182,6 +2225,7 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
     Rec48 *bufB = bufA + p.scratch_cap;
     uint32_t phase = 0;
     if (threadIdx.x == 0) mbar_init(&M.bar, 1);
+    for (int i = threadIdx.x; i < kGrpBuckets; i += blockDim.x) M.G.cnt[i] = 0;
     __syncthreads();
     const int nt = blockDim.x;
     if (threadIdx.x == 0) {
@@ -2196,114 +2240,133 @@ __global__ void __launch_bounds__(kBigThreads, kSortCtasPerSm) big_tile_kernel(c
     const unsigned int total = M.big_pre[p.n_inst];
     int inst = -1;
     double e0 = 0.0;
-    bool sym = false;
+    uint32_t fl = 0;
     KeyStats st;
     st.clear();
-    {
-        for (unsigned int idx = blockIdx.x; idx < total; idx += gridDim.x) {
-            if (inst < 0 || idx >= M.big_pre[inst + 1]) {  // uniform across the CTA
-                if (inst >= 0) {
-                    flush_stats(p, p.acc[inst], st, M.S.u.red);
-                    __syncthreads();
-                }
-                st.clear();
-                int lo = 0, hi = p.n_inst;  // last instance whose range starts at or before idx
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (M.big_pre[mid] <= idx) lo = mid;
-                    else hi = mid;
-                }
-                inst = lo;
-                e0 = p.e0[inst];
-                sym = SYM && p.sym[inst] != 0;
-            }
-            const uint64_t t = p.big_list[p.tile_base[inst] + (idx - M.big_pre[inst])];
-            const unsigned long long off = p.tile_off[t];
-            const unsigned long long cnt = p.tile_off[t + 1] - off;
-            bool bad = false;
-            // chunks of records -> exact partials (Rec48) in bufA
-            unsigned long long u = 0;
-            for (unsigned long long cs = 0; !bad && cs < cnt; cs += kBigChunk) {
-                const int m = (int)min((unsigned long long)kBigChunk, cnt - cs);
-                if (u + (unsigned long long)m > p.scratch_cap) {  // uniform
-                    if (threadIdx.x == 0) atomicOr(p.err, kErrScratch);
-                    bad = true;
-                    break;
-                }
-                if (threadIdx.x == 0) {
-                    fence_proxy_async_smem();
-                    bulk_load(M.u.r32, p.recs + off + cs, (uint32_t)(m * sizeof(Rec32)), &M.bar);
-                    M.out_count = 0;
-                }
-                mbar_wait_bounded(&M.bar, phase, p.err);
-                phase ^= 1;
-                __syncthreads();
-                chunk_to_partials(M.u.r32, m, M, bufA + u, st.err);
-                u += M.out_count;
+    bool stop = false;
+    for (unsigned int idx = blockIdx.x; idx < total && !stop; idx += gridDim.x) {
+        if (inst < 0 || idx >= M.big_pre[inst + 1]) {  // uniform across the CTA
+            if (inst >= 0) {
+                flush_stats(p, p.acc[inst], st, red_area(M.G));
                 __syncthreads();
             }
-            // Partials of different chunks may share a key.  If they fit one
-            // chunk they are sorted and reduced together; otherwise they are
-            // first split by a hash of the key into buckets that each fit a
-            // chunk (equal keys share a bucket) and every bucket is finished
-            // on its own.  Exact sums make the result independent of the split.
-            unsigned long long nrk;
-            const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
-            auto fin = [&](const KeyVal &v) { finish_keyval(p, e0, sym, rk, nrk, v, st); };
-            auto finish_list = [&](const Rec48 *src, int m) {
-                for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
-                __syncthreads();
-                if (!sort_reduce_chunk(M.u.r48, m, M.S, st.err, fin)) exact_reduce_chunk(M.u.r48, m, M.S, st.err, fin);
-                __syncthreads();
-            };
-            if (!bad && u <= (unsigned long long)kBigCap) {
-                finish_list(bufA, (int)u);
-            } else if (!bad) {
-                int nbk = 2;
-                while ((unsigned long long)nbk * (kBigCap / 2) < u && nbk < kBigBuckets) nbk *= 2;
-                for (;;) {  // uniform: every thread sees the same counts
-                    for (int i = threadIdx.x; i < nbk; i += nt) M.bk_cnt[i] = 0;
-                    __syncthreads();
-                    for (unsigned long long i = threadIdx.x; i < u; i += nt)
-                        atomicAdd(&M.bk_cnt[bucket_hash(bufA[i].a, bufA[i].b) & (nbk - 1)], 1u);
-                    __syncthreads();
-                    unsigned int mx = 0;
-                    for (int i = 0; i < nbk; ++i) mx = max(mx, M.bk_cnt[i]);
-                    if (mx <= (unsigned)kBigCap || nbk >= kBigBuckets) {
-                        if (mx > (unsigned)kBigCap) {
-                            if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
-                            bad = true;
-                        }
-                        break;
-                    }
-                    nbk *= 2;
-                    __syncthreads();
-                }
-                if (!bad) {
-                    if (threadIdx.x == 0) {
-                        unsigned int run = 0;
-                        for (int i = 0; i < nbk; ++i) {
-                            M.bk_off[i] = (unsigned short)run;
-                            run += M.bk_cnt[i];
-                            M.bk_cnt[i] = 0;  // refilled by the scatter below
-                        }
-                    }
-                    __syncthreads();
-                    for (unsigned long long i = threadIdx.x; i < u; i += nt) {
-                        const Rec48 r = bufA[i];
-                        const int k = bucket_hash(r.a, r.b) & (nbk - 1);
-                        bufB[M.bk_off[k] + atomicAdd(&M.bk_cnt[k], 1u)] = r;
-                    }
-                    __syncthreads();
-                    for (int k = 0; k < nbk; ++k)
-                        if (M.bk_cnt[k]) finish_list(bufB + M.bk_off[k], (int)M.bk_cnt[k]);
-                }
+            st.clear();
+            int lo = 0, hi = p.n_inst;  // last instance whose range starts at or before idx
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (M.big_pre[mid] <= idx) lo = mid;
+                else hi = mid;
             }
+            inst = lo;
+            e0 = p.e0[inst];
+            fl = p.iflags[inst];
+        }
+        const bool sym = SYM && (fl & kInstSym);
+        const uint32_t hmask = (fl & kInstNarrow) ? kNarrowMask : 0xFFFFFFFFu;
+        const long long wait = (fl & kInstShortWait) ? kShortWaitCycles : kWaitCycles;
+        const uint64_t t = p.big_list[p.tile_base[inst] + (idx - M.big_pre[inst])];
+        const unsigned long long off = p.tile_off[t];
+        const unsigned long long cnt = p.tile_off[t + 1] - off;
+        bool bad = false;
+        // chunks of records -> exact partials (Rec48) in bufA
+        unsigned long long u = 0;
+        for (unsigned long long cs = 0; !bad && cs < cnt; cs += kBigChunk) {
+            const int m = (int)min((unsigned long long)kBigChunk, cnt - cs);
+            if (u + (unsigned long long)m > p.scratch_cap) {  // uniform
+                if (threadIdx.x == 0) atomicOr(p.err, kErrScratch);
+                bad = true;
+                break;
+            }
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                bulk_load(M.u.r32, p.recs + off + cs, (uint32_t)(m * sizeof(Rec32)), &M.bar);
+                M.out_count = 0;
+            }
+            const bool ok = mbar_wait_bounded(&M.bar, phase, p.err, wait);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                stop = true;
+                break;
+            }
+            st.n_coll += chunk_to_partials(M.u.r32, m, M, bufA + u, hmask, st.err);
+            u += M.out_count;
             __syncthreads();
         }
-        if (inst >= 0) flush_stats(p, p.acc[inst], st, M.S.u.red);
+        // Partials of different chunks may share a key.  If they fit one
+        // chunk they are grouped and reduced together; otherwise they are
+        // first split by a hash of the key into buckets that each fit a
+        // chunk (equal keys share a bucket) and every bucket is finished
+        // on its own.  Exact sums make the result independent of the split.
+        unsigned long long nrk;
+        const uint64_t *rk = load_ref_slice(p, t, M.rk, nrk);
+        auto finish_list = [&](const Rec48 *src, int m) {
+            for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
+            __syncthreads();
+            Rec48 *r48 = M.u.r48;
+            st.n_coll += group_records<R48>(r48, m, hmask, M.G, st.err,
+                                            [&](int head, bool exact, uint64_t sl, int64_t sh) {
+                                                Rec48 &r = r48[head];
+                                                if (!exact) {
+                                                    sl = r.fx_lo;
+                                                    sh = r.fx_hi;
+                                                }
+                                                r.pad = (uint64_t)__double_as_longlong(fx_to_double(sl, sh));
+                                            });
+            const int nk = group_keys(M.G);
+            for (int q = threadIdx.x; q < nk; q += nt) {
+                const Rec48 &r = r48[M.G.uniq[q]];
+                finish_key(p, e0, sym, rk, nrk, r.a, r.b, __longlong_as_double((long long)r.pad), r.den, st);
+            }
+            __syncthreads();
+        };
+        if (!bad && u <= (unsigned long long)kBigCap) {
+            finish_list(bufA, (int)u);
+        } else if (!bad) {
+            int nbk = 2;
+            while ((unsigned long long)nbk * (kBigCap / 2) < u && nbk < kBigBuckets) nbk *= 2;
+            for (;;) {  // uniform: every thread sees the same counts
+                for (int i = threadIdx.x; i < nbk; i += nt) M.bk_cnt[i] = 0;
+                __syncthreads();
+                for (unsigned long long i = threadIdx.x; i < u; i += nt)
+                    atomicAdd(&M.bk_cnt[bucket_hash(bufA[i].a, bufA[i].b) & (nbk - 1)], 1u);
+                __syncthreads();
+                unsigned int mx = 0;
+                for (int i = 0; i < nbk; ++i) mx = max(mx, M.bk_cnt[i]);
+                if (mx <= (unsigned)kBigCap || nbk >= kBigBuckets) {
+                    if (mx > (unsigned)kBigCap) {
+                        if (threadIdx.x == 0) atomicOr(p.err, kErrNoProgress);
+                        bad = true;
+                    }
+                    break;
+                }
+                nbk *= 2;
+                __syncthreads();
+            }
+            if (!bad) {
+                if (threadIdx.x == 0) {
+                    unsigned int run = 0;
+                    for (int i = 0; i < nbk; ++i) {
+                        M.bk_off[i] = (unsigned short)run;
+                        run += M.bk_cnt[i];
+                        M.bk_cnt[i] = 0;  // refilled by the scatter below
+                    }
+                }
+                __syncthreads();
+                for (unsigned long long i = threadIdx.x; i < u; i += nt) {
+                    const Rec48 r = bufA[i];
+                    const int k = bucket_hash(r.a, r.b) & (nbk - 1);
+                    bufB[M.bk_off[k] + atomicAdd(&M.bk_cnt[k], 1u)] = r;
+                }
+                __syncthreads();
+                for (int k = 0; k < nbk; ++k)
+                    if (M.bk_cnt[k]) finish_list(bufB + M.bk_off[k], (int)M.bk_cnt[k]);
+            }
+        }
         __syncthreads();
     }
+    if (inst >= 0) flush_stats(p, p.acc[inst], st, red_area(M.G));
+    __syncthreads();
     if (threadIdx.x == 0) mbar_inval(&M.bar);
 }
 
@@ -2356,7 +2419,7 @@ __global__ void acc_init_kernel(RunAcc *acc, int n)
     a.min_abs_den = 0.0;
     a.err = 0;
     a.n_big = 0;
-    a.big_max = 0;
+    a.n_coll = 0;
     acc[i] = a;
 }
 
@@ -2544,6 +2607,24 @@ cudaError_t launch_diag(const SysDev &sys, const uint64_t *keys, uint64_t n, dou
 {
     if (n == 0) return cudaSuccess;
     diag_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sys, keys, n, out);
+    return cudaGetLastError();
+}
+
+// The tile kernels' term arithmetic on given numerators and denominators
+// (Hartree): the denominator rounded to the 2^-48 fixed point, then
+// term_fx48, scaled back to Hartree.
+__global__ void eval_terms_kernel(const double *__restrict__ num, const double *__restrict__ den, uint64_t n,
+                                  double *__restrict__ out)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = term_fx48(num[i], __double2ll_rn(den[i] * kDenScale)) * kDenScale;
+}
+
+cudaError_t launch_eval_terms(const double *num, const double *den, uint64_t n, double *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    eval_terms_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(num, den, n, out);
     return cudaGetLastError();
 }
 

@@ -78,7 +78,7 @@ struct StepDev {
     unsigned long long det_base[kMaxBatch + 1];
     unsigned long long tile_base[kMaxBatch + 1];
     double e0[kMaxBatch];
-    uint32_t sym[kMaxBatch];
+    uint32_t iflags[kMaxBatch];  // kInst* options of each instance
     unsigned long long expected[kMaxBatch];
     RunAcc *acc[kMaxBatch];
     unsigned int n_big[kMaxBatch];

@@ -28,12 +28,14 @@ PT2_FLAG_PROFILE = 1
 PT2_FLAG_AUTOTUNE = 2
 PT2_FLAG_SPIN_SYMMETRIC = 4
 PT2_FLAG_SUBTRACT_REF = 8
+PT2_DEBUG_NARROW_SORT_HASH = 1
+PT2_DEBUG_SHORT_COPY_WAIT = 2
 
 EXPORTS = ["pt2_create", "pt2_destroy", "pt2_last_error", "pt2_load_system", "pt2_load_reference",
            "pt2_unload", "pt2_diagonal", "pt2_run", "pt2_dump_external", "pt2_batch_create", "pt2_batch_run",
            "pt2_batch_info", "pt2_batch_destroy", "pt2_autotune", "pt2_submit", "pt2_poll", "pt2_wait",
-           "pt2_server_stats", "pt2_det_terms", "pt2_det_terms_noalloc", "pt2_phase_times", "pt2_memory_info",
-           "pt2_stream"]
+           "pt2_server_stats", "pt2_det_terms", "pt2_det_terms_noalloc", "pt2_eval_terms", "pt2_phase_times",
+           "pt2_memory_info", "pt2_stream"]
 
 PHASES = ["class_count", "tile_count", "scan", "emit", "ref_partition", "tile_sort_reduce",
           "oversize_tiles", "pass_reduce"]
@@ -48,7 +50,8 @@ class Pt2Error(RuntimeError):
 class pt2_opts(ctypes.Structure):
     _fields_ = [("constraint_mod", ctypes.c_uint64), ("constraint_rem", ctypes.c_uint64),
                 ("pass_budget_bytes", ctypes.c_uint64), ("tile_target", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("numerator_cutoff", ctypes.c_double)]
+                ("flags", ctypes.c_uint32), ("numerator_cutoff", ctypes.c_double),
+                ("debug_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class pt2_result(ctypes.Structure):
@@ -57,11 +60,11 @@ class pt2_result(ctypes.Structure):
                 ("digest_sum", ctypes.c_uint64), ("digest_xor", ctypes.c_uint64),
                 ("min_abs_denom", ctypes.c_double), ("n_pos_denom", ctypes.c_uint64),
                 ("n_passes", ctypes.c_uint32), ("n_tiles", ctypes.c_uint32),
-                ("n_oversize", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_oversize", ctypes.c_uint32), ("n_hash_collisions", ctypes.c_uint32),
                 ("seconds", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -98,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "pt2_wait": (i32, [P, u64, u64, ctypes.POINTER(pt2_result)]),
         "pt2_server_stats": (i32, [P, pu64, pu64, pu64]),
         "pt2_det_terms_noalloc": (i32, [P, u32, u64, P, P, P, u64, pu64]),
+        "pt2_eval_terms": (i32, [P, u64, P, P, P]),
         "pt2_phase_times": (i32, [P, P, i32, pu64]),
         "pt2_memory_info": (i32, [P, pu64, pu64, pu64]),
         "pt2_stream": (P, [P]),
@@ -122,7 +126,8 @@ def _check(ctx, rc):
 
 
 def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False,
-              spin_symmetric=False, cutoff=0.0, subtract_ref=False) -> pt2_opts:
+              spin_symmetric=False, cutoff=0.0, subtract_ref=False, narrow_sort_hash=False,
+              short_copy_wait=False) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
@@ -131,6 +136,8 @@ def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=Fal
                (PT2_FLAG_SPIN_SYMMETRIC if spin_symmetric else 0) |
                (PT2_FLAG_SUBTRACT_REF if subtract_ref else 0))
     o.numerator_cutoff = float(cutoff)
+    o.debug_flags = ((PT2_DEBUG_NARROW_SORT_HASH if narrow_sort_hash else 0) |
+                     (PT2_DEBUG_SHORT_COPY_WAIT if short_copy_wait else 0))
     return o
 
 
@@ -283,6 +290,17 @@ def pt2_det_terms_noalloc(ctx, ref_id: int, det_index: int, keys_dev: int, val_d
     return n.value
 
 
+def pt2_eval_terms(ctx, num: np.ndarray, denom: np.ndarray) -> np.ndarray:
+    """num^2 / denom (denom = E0 - H_aa in Hartree) with the tile kernels' arithmetic."""
+    num = np.ascontiguousarray(num, dtype=np.float64)
+    denom = np.ascontiguousarray(denom, dtype=np.float64)
+    if num.shape != denom.shape:
+        raise ValueError("num and denom must have the same shape")
+    out = np.zeros_like(num)
+    _check(ctx, load_library().pt2_eval_terms(ctx, num.size, _ptr(num), _ptr(denom), _ptr(out)))
+    return out
+
+
 def pt2_phase_times(ctx):
     out = np.zeros(8)
     launches = ctypes.c_uint64()
@@ -370,6 +388,9 @@ class Context:
 
     def server_stats(self):
         return pt2_server_stats(self.handle)
+
+    def eval_terms(self, num, denom):
+        return pt2_eval_terms(self.handle, num, denom)
 
     def phase_times(self):
         return pt2_phase_times(self.handle)

@@ -4,15 +4,22 @@ Callers that cannot allocate device memory when they call (a memory pool or
 arena they must not bypass, a latency path that forbids allocation) pass
 their own device buffers; the library stages the terms in a fixed device
 array it carries.  These checks call it through the C ABI and compare its
-output with the allocating pt2_det_terms, twice in a row (the shared array
-keeps the previous call's contents, so the second call must not see them),
-and check that a determinant with more terms than the array holds is
-rejected.  This file is collected last on purpose.
+output with the allocating pt2_det_terms and with the oracle's terms of the
+same determinant, twice in a row (the shared array keeps the previous call's
+contents, so the second call must not see them), and check that a
+determinant with more terms than the array holds is rejected.
+
+The file name sorts last so that pytest collects it after every other test
+file: a run that stops at its first failure (-x) has then already run the
+rest of the suite if this convenience entry point fails.  No other test
+depends on it or on its order; each test here builds its own context and
+passes alone in a fresh process as well.
 """
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1808_02049_gb300 import inputs, pt2
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +59,12 @@ def test_noalloc_terms_match_allocating_entry_point():
             assert np.array_equal(k, k_ref)
             np.testing.assert_allclose(v, v_ref, rtol=0, atol=1e-14)
             np.testing.assert_allclose(h, h_ref, rtol=0, atol=1e-11)
+            # and directly against the oracle's singles and doubles of the determinant
+            ok, ov, oh = oracle.det_terms(s.h, s.eri, r.keys[2 * det], r.keys[2 * det + 1], r.coef[det])
+            ok, ov, oh = _sorted(ok, ov, oh)
+            assert np.array_equal(k, ok)
+            np.testing.assert_allclose(v, ov, rtol=0, atol=1e-14)
+            np.testing.assert_allclose(h, oh, rtol=0, atol=1e-11)
         # a buffer that is too small is reported, not overrun
         with pytest.raises(pt2.Pt2Error) as e:
             pt2.pt2_det_terms_noalloc(ctx.handle, rid, 3, keys.data_ptr(), val.data_ptr(), haa.data_ptr(), 100)
