@@ -1,11 +1,16 @@
 """PT2 throughput benchmark (terms/s) of the GB300 path, one JSON line.
 
-Default workload: 20 electrons (10 alpha, 10 beta) in 40 orbitals, N_det =
-100,000 reference determinants up to quadruple excitations, seeded synthetic
-integrals: 1.2975e10 generated terms per step, streamed through HBM in
-memory-bounded passes.  A step is one complete PT2 solve (work list, every
-pass of generate / tile sort-reduce / filter / energy, final sum) on inputs
-already resident in device memory.
+Headline workload: PT2 at "trillions of contributions" scale, 24 electrons
+(12 alpha, 12 beta) in 60 orbitals, N_det = 1,000,000 reference determinants
+up to quadruple excitations, seeded synthetic FP64 integrals: 4.818e11
+generated terms per complete solve, streamed through HBM in memory-bounded
+passes.  The solve is split into SLICES = 20 contiguous slices of the 4096
+alpha-hash classes (non-overlapping, complete constraint classes of
+Algorithm 2); a step is the complete path (work list, every pass of generate /
+tile sort-reduce / filter / energy, final sum) over one slice, on inputs
+already resident in device memory.  Step k takes slice k mod 20, warm-up steps
+included, so any 20 consecutive steps are exactly one complete solve, whose
+E2 is the sum of their slice energies.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -13,12 +18,13 @@ With --gpus N > 1 (under torchrun) every rank solves its own replica of the
 workload ("replicas only": the path needs no exchange between GPUs); value
 is the sum of terms over ranks divided by the slowest rank's time.
 --impl reference times the CPU oracle on a bounded sample of the same
-workload on the host cores instead.
+workload on all host cores instead.
 """
 
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import os
 import subprocess
@@ -32,9 +38,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PT2 terms/sec"
 UNIT = "terms/s"
-WORKLOAD = ("plain PT2, one large solve: 20 electrons (10a,10b) in 40 orbitals, N_det=100000 "
-            "(HF + excitations up to quadruples), seeded synthetic FP64 integrals")
-SAMPLE_DETS = 100  # reference determinants in the bounded CPU sample
+WORKLOAD = ("plain PT2 at trillions-of-contributions scale: 24 electrons (12a,12b) in 60 orbitals, "
+            "N_det=1000000 (HF + excitations up to quadruples), seeded synthetic FP64 integrals")
+SLICES = 20            # alpha-class slices of one complete solve (one per step)
+E2E_SLICES = 4         # slices of the end-to-end measurement (one load, these slices, one unload)
+CPU_DETS_ALL = 200     # reference determinants of the all-cores oracle sample
+CPU_DETS_ONE = 20      # reference determinants of the single-thread oracle sample
+REF_DETS_STEP = 40     # reference determinants per step of the reference arm
 
 
 def dist_env():
@@ -44,30 +54,53 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n_det=None):
+def workload(name="million", n_det=None):
     from paper_1808_02049_gb300 import inputs
 
-    return inputs.make_workload("large", n_det=n_det or None)
+    return inputs.make_workload(name, n_det=n_det or None)
 
 
 def workload_name(n_det):
     if not n_det:
         return WORKLOAD
-    return WORKLOAD.replace("N_det=100000", f"N_det={n_det} (reduced case)")
+    return WORKLOAD.replace("N_det=1000000", f"N_det={n_det} (reduced case)")
 
 
-def cpu_baseline(s, r, e0):
-    """The oracle (single thread) on the first SAMPLE_DETS determinants."""
+def oracle_all_cores(s, r, e0, n_dets, cores):
+    """The oracle on the first n_dets reference determinants, its constraint
+    classes alpha % m == k (m prime, several per core) solved by `cores` host
+    threads (the C oracle releases the interpreter lock); the classes
+    partition the sum, so the class results add up to the sample's PT2."""
     import oracle
 
     oracle.build()
-    m = SAMPLE_DETS
+    m = 4 * cores + 1
+    while any(m % q == 0 for q in range(2, int(m ** 0.5) + 1)):
+        m += 1
+    keys, coef = r.keys[: 2 * n_dets], r.coef[:n_dets]
     t = time.perf_counter()
-    res = oracle.pt2(s.h, s.eri, r.keys[: 2 * m], r.coef[:m], e0)
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        res = list(ex.map(lambda k: oracle.pt2(s.h, s.eri, keys, coef, e0, constraint=(m, k)), range(m)))
     dt = time.perf_counter() - t
-    return {"value": res["n_terms"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"full PT2 of the first {m} reference determinants of the workload "
-                      f"({res['n_terms']} terms, {dt:.1f} s, single thread)"}
+    return sum(x["n_terms"] for x in res), sum(x["e2"] for x in res), dt, m
+
+
+def cpu_baseline(s, r, e0):
+    """The oracle as it stands on the host cores: all cores on a sample of
+    CPU_DETS_ALL determinants, one thread on CPU_DETS_ONE."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    terms_all, _, dt_all, m = oracle_all_cores(s, r, e0, CPU_DETS_ALL, cores)
+    t = time.perf_counter()
+    one = oracle.pt2(s.h, s.eri, r.keys[: 2 * CPU_DETS_ONE], r.coef[:CPU_DETS_ONE], e0)
+    dt_one = time.perf_counter() - t
+    return {"value": terms_all / dt_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": one["n_terms"] / dt_one,
+            "sample": f"PT2 of the first {CPU_DETS_ALL} reference determinants of the workload "
+                      f"({terms_all} terms, {dt_all:.1f} s on {cores} threads: constraint classes alpha % {m}); "
+                      f"single thread: the first {CPU_DETS_ONE} ({one['n_terms']} terms, {dt_one:.1f} s)"}
 
 
 class ClockSampler:
@@ -140,62 +173,87 @@ def load_fleet(ctx, n=64):
 SAME = ("e2", "n_terms", "n_unique", "n_in_ref", "n_external", "digest_sum", "digest_xor", "n_pos_denom")
 
 
-def timed_run(ctx, rid):
+def timed_run(ctx, rid, **kw):
     t = time.perf_counter()
-    res = ctx.run(rid)
+    res = ctx.run(rid, **kw)
     return res, time.perf_counter() - t
 
 
-def bench_cutoff(ctx, rid, cut=1e-8, reps=2):
-    """The paper's numerator cutoff on the one-large-solve workload: the
-    exact solve against the one that drops contributions |c_i H_ai| < cut
-    before they get a record (best of `reps` each, wall time of the call)."""
-    out = {}
-    for name, kw in (("exact", {}), ("cutoff", {"cutoff": cut})):
-        ctx.run(rid, **kw)  # warm-up
-        best = None
-        for _ in range(reps):
-            t = time.perf_counter()
-            res = ctx.run(rid, **kw)
-            dt = time.perf_counter() - t
-            best = dt if best is None or dt < best else best
-        out[name] = (res, best)
-    (ex, te), (ct, tc) = out["exact"], out["cutoff"]
-    ctx.run(rid, cutoff=cut, profile=True)
+def best_of(ctx, rid, reps, **kw):
+    ctx.run(rid, **kw)  # warm-up
+    best, res = None, None
+    for _ in range(reps):
+        res, dt = timed_run(ctx, rid, **kw)
+        best = dt if best is None or dt < best else best
+    return res, best
+
+
+def bench_large(ctx, reps=2):
+    """The one-large-solve workload (20e in 40 orbitals, N_det = 100,000,
+    1.2975e10 terms) as a complete solve per call: wall time of the blocking
+    call (best of `reps`) and the phase split of a profiled run."""
+    s, r = workload("large")
+    sid = ctx.load_system(s.h, s.eri)
+    e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
+    rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    res, dt = best_of(ctx, rid, reps)
+    ctx.run(rid, profile=True)
     ph, _ = ctx.phase_times()
-    return {"cutoff": cut, "ms_exact": te * 1e3, "ms_cutoff": tc * 1e3, "speedup": te / tc,
-            "phase_ms_cutoff": {k: round(v, 3) for k, v in ph.items()},
-            "terms_exact": ex["n_terms"], "terms_kept": ct["n_terms"], "kept_fraction": ct["n_terms"] / ex["n_terms"],
-            "external_exact": ex["n_external"], "external_kept": ct["n_external"],
-            "e2_exact": ex["e2"], "e2_cutoff": ct["e2"], "delta_e2": ct["e2"] - ex["e2"]}
+    out = {"workload": "plain PT2, one large solve: 20 electrons (10a,10b) in 40 orbitals, N_det=100000",
+           "terms": res["n_terms"], "ms_per_solve": dt * 1e3, "terms_per_s": res["n_terms"] / dt,
+           "passes": res["n_passes"], "e2": res["e2"],
+           "phase_ms": {k: round(v, 3) for k, v in ph.items()},
+           "tile_kernel_gbs": res["n_terms"] * 32 / (ph["tile_sort_reduce"] * 1e-3) / 1e9,
+           "timing": "wall time of the blocking C-ABI call, best of %d" % reps}
+    return sid, rid, res, dt, out
 
 
-def bench_subtraction(ctx, rid, reps=2):
-    """Duplicate subtraction on the one-large-solve workload against the
-    explicit filter: the cost of each (best of `reps`, wall time of the call).
-    The synthetic reference is not an eigenvector of H in its space, so the
-    two energies differ by the residual; their equality for eigenvector
-    references is a parity test, not a benchmark."""
-    out = {}
-    for name, kw in (("filtered", {}), ("subtracted", {"subtract_ref": True})):
-        ctx.run(rid, **kw)  # warm-up
-        best = None
-        for _ in range(reps):
-            t = time.perf_counter()
-            res = ctx.run(rid, **kw)
-            dt = time.perf_counter() - t
-            best = dt if best is None or dt < best else best
-        out[name] = (res, best)
-    (fr, tf), (sr, ts) = out["filtered"], out["subtracted"]
-    return {"ms_filtered": tf * 1e3, "ms_subtracted": ts * 1e3, "speedup": tf / ts,
-            "n_in_ref_filtered": fr["n_in_ref"], "n_terms": sr["n_terms"],
+def bench_cutoff(ctx, rid, exact, cut=1e-8):
+    """The paper's numerator cutoff on slices of the headline workload: the
+    slices' exact solves (timed in the measured steps) against the same
+    slices with contributions |c_i H_ai| < cut dropped before they get a
+    record (wall time of the blocking call)."""
+    ks = sorted(exact)[:2]
+    t_ex = sum(exact[k][1] for k in ks)
+    res, t_ct = [], 0.0
+    for k in ks:
+        ctx.run(rid, class_slice=(k, SLICES), cutoff=cut)  # warm-up
+        r, dt = timed_run(ctx, rid, class_slice=(k, SLICES), cutoff=cut)
+        res.append(r)
+        t_ct += dt
+    ctx.run(rid, class_slice=(ks[0], SLICES), cutoff=cut, profile=True)
+    ph, _ = ctx.phase_times()
+    ex_terms = sum(exact[k][0]["n_terms"] for k in ks)
+    ct_terms = sum(r["n_terms"] for r in res)
+    return {"cutoff": cut, "slices": [f"{k}/{SLICES}" for k in ks], "ms_exact": t_ex * 1e3, "ms_cutoff": t_ct * 1e3,
+            "speedup": t_ex / t_ct, "phase_ms_cutoff_first_slice": {k: round(v, 3) for k, v in ph.items()},
+            "terms_exact": ex_terms, "terms_kept": ct_terms, "kept_fraction": ct_terms / ex_terms,
+            "external_exact": sum(exact[k][0]["n_external"] for k in ks),
+            "external_kept": sum(r["n_external"] for r in res),
+            "delta_e2": sum(r["e2"] for r in res) - sum(exact[k][0]["e2"] for k in ks)}
+
+
+def bench_subtraction(ctx, rid, exact):
+    """Duplicate subtraction on slices of the headline workload against the
+    explicit filter (timed in the measured steps).  The synthetic reference is
+    not an eigenvector of H in its space, so the energies differ by the
+    residual; their equality for eigenvector references is a parity test."""
+    ks = sorted(exact)[:2]
+    t_f = sum(exact[k][1] for k in ks)
+    t_s = 0.0
+    for k in ks:
+        ctx.run(rid, class_slice=(k, SLICES), subtract_ref=True)
+        _, dt = timed_run(ctx, rid, class_slice=(k, SLICES), subtract_ref=True)
+        t_s += dt
+    return {"slices": [f"{k}/{SLICES}" for k in ks], "ms_filtered": t_f * 1e3, "ms_subtracted": t_s * 1e3,
+            "speedup": t_f / t_s,
             "note": "timing only: the synthetic reference is not an eigenvector, so E2 differs"}
 
 
 def bench_spin_symmetric(ctx, reps=2):
-    """The large system with a reference closed under alpha <-> beta exchange
-    (100,000 determinants with their mirrors, equal coefficients): the
-    ordinary solve against the spin-flip symmetric one, which generates,
+    """The 40-orbital system with a reference closed under alpha <-> beta
+    exchange (100,000 determinants with their mirrors, equal coefficients):
+    the ordinary solve against the spin-flip symmetric one, which generates,
     sorts and reduces only the alpha' >= beta' half (best of `reps` each)."""
     from paper_1808_02049_gb300 import inputs
 
@@ -207,20 +265,11 @@ def bench_spin_symmetric(ctx, reps=2):
     e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
     rid = ctx.load_reference(sid, r.keys, r.coef, e0)
     try:
-        out = {}
-        for name, kw in (("full", {}), ("symmetric", {"spin_symmetric": True})):
-            ctx.run(rid, **kw)  # warm-up
-            best = None
-            for _ in range(reps):
-                t = time.perf_counter()
-                res = ctx.run(rid, **kw)
-                dt = time.perf_counter() - t
-                best = dt if best is None or dt < best else best
-            out[name] = (res, best)
+        full, tf = best_of(ctx, rid, reps)
+        sym, ts = best_of(ctx, rid, reps, spin_symmetric=True)
     finally:
         ctx.unload(rid)
         ctx.unload(sid)
-    (full, tf), (sym, ts) = out["full"], out["symmetric"]
     return {"workload": "20e in 40 orbitals, symmetric reference N_det=100000 (mirrors included)",
             "ms_full": tf * 1e3, "ms_symmetric": ts * 1e3, "speedup": tf / ts,
             "terms_full": full["n_terms"], "terms_symmetric": sym["n_terms"],
@@ -231,9 +280,8 @@ def bench_spin_symmetric(ctx, reps=2):
 
 
 def bench_batched(ctx, fleet, reps):
-    """64 instances: one captured batch (autotuned tile targets) against
-    pt2_run of each instance one after the other (wall time of the blocking
-    calls in both cases)."""
+    """64 instances: one captured batch (autotuned) against pt2_run of each
+    instance one after the other (wall time of the blocking calls)."""
     for x in fleet:  # warm-up, and each instance's result alone
         x["alone"], _ = timed_run(ctx, x["rid"])
     serial = []
@@ -274,15 +322,19 @@ def bench_batched(ctx, fleet, reps):
 
 def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
     """Poisson stream of solves: 90% instances of the batched workload, 10% the
-    one-large-solve workload.  Latency = submission to completion; plain =
-    the same arrivals served first-come first-served by pt2_run alone, from
-    each request's measured pt2_run time."""
+    one-large-solve workload.  Served: every request submitted at its arrival
+    time to the continuous-batching engine (pt2_submit), latency = submission
+    to completion.  Plain: the same arrivals run first-come first-served by
+    pt2_run in one host thread (a request starts when it has arrived and the
+    previous one has finished), latency = arrival to completion."""
     rng = np.random.Generator(np.random.PCG64(seed))
     pool = [(x["rid"], x["alone"], x["alone_s"]) for x in fleet]
     reqs = [big if rng.random() < 0.1 else pool[int(rng.integers(len(pool)))] for _ in range(n_req)]
     mean_service = float(np.mean([r[2] for r in reqs]))
     rate = load / mean_service  # offered load relative to the plain path's capacity
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    arrivals -= arrivals[0]
+    # served
     tickets = []
     t0 = time.perf_counter()
     for (rid, _, _), ta in zip(reqs, arrivals):
@@ -298,23 +350,28 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
         identical &= all(got[k] == alone[k] for k in SAME)
         d_e2 = max(d_e2, abs(got["e2"] - alone["e2"]))
     terms = sum(r[1]["n_terms"] for r in reqs)
-    span = max(done) - tickets[0][1]
-    # plain: FIFO single server over the same arrivals
-    free, plat, pdone = 0.0, [], []
-    for (_, _, sv), ta in zip(reqs, arrivals):
-        start = max(free, ta)
-        free = start + sv
-        plat.append(free - ta)
-    pspan = free - arrivals[0]
+    span = max(done)
+    # plain: one host thread, pt2_run in arrival order
+    plat, pdone = [], []
+    t0 = time.perf_counter()
+    for (rid, _, _), ta in zip(reqs, arrivals):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ctx.run(rid)
+        tc = time.perf_counter() - t0
+        plat.append(tc - ta)
+        pdone.append(tc)
+    pspan = max(pdone)
     return {"workload": f"{n_req} requests, Poisson arrivals at {rate:.2f}/s "
                         f"({load:.2f}x the plain path's capacity); 90% batched-workload instances, "
                         "10% the one-large-solve workload",
             "requests": n_req, "terms": terms,
-            "served_terms_per_s": terms / span, "plain_terms_per_s": float(terms / pspan),
+            "served_terms_per_s": terms / span, "plain_terms_per_s": terms / pspan,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "plain_p50_s": float(np.percentile(plat, 50)), "plain_p99_s": float(np.percentile(plat, 99)),
             "max_abs_dE2_vs_alone": d_e2, "bit_identical_to_alone": bool(identical),
-            "plain": "first-come first-served pt2_run of the same arrivals, from measured pt2_run times"}
+            "plain": "measured: first-come first-served pt2_run of the same arrivals in one host thread"}
 
 
 # DRAM bytes per term of the two large kernels from one ncu capture
@@ -322,10 +379,10 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began ecffd826
-    "kernels_sha256": "d62cf165b13840a8982943793b43bbfd265443393b954df1d762b4e602830719",
-    "tile_kernel": (4.13362e9 + 5.024256e6) / 129_750_000,        # 31.90 B per term
-    "gen_kernel<Emit>": (0.165389312e9 + 4.105932e9) / 129_750_000,  # 32.92 B per term
+    # code hash (kernel_code_sha256) of the captured source
+    "kernels_sha256": "",
+    "tile_kernel": None,
+    "gen_kernel<Emit>": None,
 }
 
 
@@ -377,31 +434,28 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    from paper_1808_02049_gb300 import inputs  # noqa: F401
     import oracle
 
-    s, r = workload(args.n_det)
+    s, r = workload("million", args.n_det)
     oracle.build()
     e0 = oracle.e0_of(s.h, s.eri, r.keys)
-    m = SAMPLE_DETS
-    keys, coef = r.keys[: 2 * m], r.coef[:m]
+    cores = os.cpu_count() or 1
+    n = REF_DETS_STEP
     for _ in range(args.warmup):
-        oracle.pt2(s.h, s.eri, keys[:20], coef[:10], e0)
-    terms = 0
-    t0 = time.perf_counter()
+        oracle_all_cores(s, r, e0, 4, cores)
+    terms, dt = 0, 0.0
     for _ in range(args.steps):
-        res = oracle.pt2(s.h, s.eri, keys, coef, e0)
-        terms += res["n_terms"]
-    dt = time.perf_counter() - t0
+        t_, _, d_, m = oracle_all_cores(s, r, e0, n, cores)
+        terms += t_
+        dt += d_
     value = terms / dt
+    sample = (f"bounded sample per step: PT2 of the first {n} reference determinants "
+              f"({terms // args.steps} terms) on {cores} host threads (constraint classes alpha % {m})")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_name(args.n_det),
-                       "sample": f"bounded sample: PT2 of the first {m} reference determinants per step",
-                       "l2": "CPU run"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"full PT2 of the first {m} reference determinants per step"},
+            "config": {"workload": workload_name(args.n_det), "sample": sample, "l2": "CPU run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -419,7 +473,7 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     build.build_library()
-    s, r = workload(args.n_det)
+    s, r = workload("million", args.n_det)
     ctx = pt2.Context(local)
     sid = ctx.load_system(s.h, s.eri)
     e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
@@ -434,105 +488,122 @@ def run_gpu(args):
 
             dist.barrier()
 
-    for _ in range(args.warmup):
-        res = ctx.run(rid, profile=True)
-    # timed region: K solves, L2 flushed between them, CUDA events on the library stream
+    M = SLICES
+    for k in range(args.warmup):
+        ctx.run(rid, class_slice=(k % M, M), profile=True)
+    # timed region: K slices, L2 flushed between them, CUDA events on the library stream
     sampler = ClockSampler(local)
     sampler.start()
-    step_ms, phases, launches, results = [], {}, 0, []
+    step_ms, phases, launches, results, passes = [], {}, 0, [], 0
+    per_slice = {}
     barrier()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
+    for k in range(args.warmup, args.warmup + args.steps):
         flush.random_(0, 255)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        res = ctx.run(rid, profile=True)
+        res = ctx.run(rid, class_slice=(k % M, M), profile=True)
         ev1.record(stream)
         ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
+        ms = ev0.elapsed_time(ev1)
+        step_ms.append(ms)
         ph, nl = ctx.phase_times()
-        for k, v in ph.items():
-            phases[k] = phases.get(k, 0.0) + v
+        for key, v in ph.items():
+            phases[key] = phases.get(key, 0.0) + v
         launches += nl
+        passes += res["n_passes"]
         results.append(res)
+        per_slice[k % M] = (res, ms * 1e-3)
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
     total_ms = float(sum(step_ms))
     terms = sum(x["n_terms"] for x in results)
-    total_ms, terms = replica_totals(total_ms, terms, f"cuda:{local}")
-    e2s = {x["e2"] for x in results}
+    total_ms_all, terms_all = replica_totals(total_ms, terms, f"cuda:{local}")
 
-    # end to end through the C ABI with host buffers: load system and reference
-    # from host memory, solve, read the result back, unload
-    e2e_steps = max(1, min(args.steps, 2))
+    # end to end through the C ABI with host buffers: load the system and the
+    # reference from host memory, solve E2E_SLICES slices, read each result
+    # back, unload; the input bytes are copied once per E2E_SLICES steps
     h2d = s.h.nbytes + s.eri.nbytes + r.keys.nbytes + r.coef.nbytes
     d2h = 4096 * 8 + 256
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_terms = 0
-    for _ in range(e2e_steps):
-        sid2 = ctx.load_system(s.h, s.eri)
-        rid2 = ctx.load_reference(sid2, r.keys, r.coef, e0)
-        out = ctx.run(rid2)
+    sid2 = ctx.load_system(s.h, s.eri)
+    rid2 = ctx.load_reference(sid2, r.keys, r.coef, e0)
+    for k in range(E2E_SLICES):
+        out = ctx.run(rid2, class_slice=(k, M))
         e2e_terms += out["n_terms"]
-        ctx.unload(rid2)
-        ctx.unload(sid2)
+    ctx.unload(rid2)
+    ctx.unload(sid2)
     e2e_s = time.perf_counter() - t0
     barrier()
     e2e_s, e2e_terms = replica_totals(e2e_s, e2e_terms, f"cuda:{local}")
 
     extra = {}
     if rank == 0 and not args.no_batch:
+        extra["cutoff"] = bench_cutoff(ctx, rid, per_slice)
+        extra["subtraction"] = bench_subtraction(ctx, rid, per_slice)
+        lsid, lrid, lres, lsec, extra["large"] = bench_large(ctx)
+        extra["spin_symmetric"] = bench_spin_symmetric(ctx)
         fleet = load_fleet(ctx)
         extra["batched"] = bench_batched(ctx, fleet, reps=2)
         if args.served_requests > 0:
-            big_res, big_s = timed_run(ctx, rid)
-            extra["served"] = bench_served(ctx, fleet, (rid, big_res, big_s), args.served_requests,
+            extra["served"] = bench_served(ctx, fleet, (lrid, lres, lsec), args.served_requests,
                                            args.served_load)
-        extra["spin_symmetric"] = bench_spin_symmetric(ctx)
-        extra["cutoff"] = bench_cutoff(ctx, rid)
-        extra["subtraction"] = bench_subtraction(ctx, rid)
 
     if rank == 0:
-        value = terms / (total_ms * 1e-3)
+        value = terms_all / (total_ms_all * 1e-3)
         peaks = measured_peaks()
-        # dominant kernel and its roofline (algorithmic bytes per launch)
-        per_step = {k: v / args.steps for k, v in phases.items()}
-        dom = max(("emit", "tile_sort_reduce"), key=lambda k: per_step.get(k, 0.0))
-        n_pass = results[0]["n_passes"]
-        terms_step = results[0]["n_terms"]
-        bytes_per_term = 32  # one 32-byte record written (emit) or read (tile sort-reduce)
-        launch_ms = per_step[dom] / n_pass
-        achieved = (terms_step / n_pass) * bytes_per_term / (launch_ms * 1e-3) / 1e9
+        # dominant kernel and its roofline: algorithmic bytes (32 B per record
+        # written by the emission or read by the tile kernel) over the
+        # kernel's device time, summed over the passes of the timed steps
+        dom = max(("emit", "tile_sort_reduce"), key=lambda k: phases.get(k, 0.0))
+        bytes_per_term = 32
+        achieved = terms * bytes_per_term / (phases[dom] * 1e-3) / 1e9
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         kname = {"emit": "gen_kernel<Emit>", "tile_sort_reduce": "tile_kernel"}[dom]
         tpt = profiled_traffic_per_term(kname)
+        other = "tile_sort_reduce" if dom == "emit" else "emit"
         roof = {"kernel": kname,
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": None if tpt is None else tpt * terms_step / n_pass,
+                "traffic": None if tpt is None else tpt * terms / passes,
+                "traffic_note": "DRAM bytes per launch (one pass) from an ncu capture of the same kernel code, "
+                                "scaled by records; null when the kernel changed since the capture",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_term": bytes_per_term,
-                "phase_ms_per_step": {k: round(v, 3) for k, v in per_step.items()},
+                "launches": passes,
+                "phase_ms_per_step": {k: round(v / args.steps, 3) for k, v in phases.items()},
+                "second_kernel": {"kernel": {"emit": "gen_kernel<Emit>", "tile_sort_reduce": "tile_kernel"}[other],
+                                  "achieved": terms * bytes_per_term / (phases[other] * 1e-3) / 1e9,
+                                  "frac": terms * bytes_per_term / (phases[other] * 1e-3) / 1e9 / peak},
                 # the path against the floor of a global-memory sort (write 24 B,
                 # permute 48 B, read 24 B per term)
                 "path": {"bytes_per_term": 96, "achieved": value / world * 96 / 1e9,
                          "frac": value / world * 96 / 1e9 / peak}}
+        covered = sorted(per_slice) == list(range(M))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(args.n_det), "terms_per_step": terms_step, "passes": n_pass,
-                           "tiles": results[0]["n_tiles"], "oversize_tiles": results[0]["n_oversize"],
-                           "e2": results[0]["e2"], "e2_bit_identical_across_steps": len(e2s) == 1,
-                           "l2": "inputs larger than L2 (32 B x 1.3e10 terms stream through HBM per step) "
-                                 "and a 256 MB L2 flush between steps",
+                "config": {"workload": workload_name(args.n_det),
+                           "step": f"one of {M} alpha-class slices of the solve (step k: slice k mod {M}); "
+                                   f"{M} consecutive steps are one complete solve",
+                           "terms_timed": terms, "passes_timed": passes,
+                           "complete_solves_timed": round(args.steps / M, 3),
+                           "e2_complete_solve": sum(per_slice[k][0]["e2"] for k in range(M)) if covered else None,
+                           "terms_complete_solve": sum(per_slice[k][0]["n_terms"] for k in range(M)) if covered
+                           else None,
+                           "l2": "inputs larger than L2 (32-byte records, up to 96 GB per pass, stream through "
+                                 "HBM) and a 256 MB L2 flush between steps",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roof,
                 "clocks": clocks,
-                "e2e": {"value": e2e_terms / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                "e2e": {"value": e2e_terms / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // E2E_SLICES,
+                        "d2h_bytes_per_step": d2h,
+                        "note": f"one load of system and reference from host memory, {E2E_SLICES} slices solved "
+                                "and read back, one unload; input bytes per step = inputs / slices"},
                 "gpu_launches": launches}
         line.update(extra)
         if not args.no_cpu_baseline:
@@ -549,15 +620,16 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=SLICES)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the secondary measurements (cutoff, subtraction, large, spin, batched, served)")
     ap.add_argument("--n-det", type=int, default=0,
-                    help="reference size of the one-large-solve workload (0: 100000); smaller values "
-                         "give the reduced cases used for profiling")
-    ap.add_argument("--served-requests", type=int, default=200)
+                    help="reference size of the headline workload (0: 1000000); smaller values give the "
+                         "reduced cases used for profiling")
+    ap.add_argument("--served-requests", type=int, default=1000)
     ap.add_argument("--served-load", type=float, default=1.5,
                     help="offered load of the served stream relative to the plain path's capacity")
     args = ap.parse_args()

@@ -121,6 +121,18 @@ typedef struct {
                                    contributions.  PT2_ERR_INVALID if negative
                                    or not finite. */
     uint32_t debug_flags;       /* PT2_DEBUG_* test aids below; 0 in normal use */
+    uint32_t class_slices;      /* 0 or 1: every alpha class.  Otherwise only
+                                   excited determinants whose alpha-hash class
+                                   (a fixed 12-bit Zobrist hash of the alpha
+                                   string, 4096 classes) lies in slice
+                                   class_slice of class_slices contiguous
+                                   slices are summed: another non-overlapping,
+                                   complete partition of Algorithm 2, the one
+                                   the memory-bounded passes are made of, so a
+                                   slice costs about 1/class_slices of the
+                                   solve (plus its own work-list launch).  At
+                                   most 4096; combines with constraint_mod. */
+    uint32_t class_slice;
     uint32_t reserved;          /* must be 0 */
 } pt2_opts;
 

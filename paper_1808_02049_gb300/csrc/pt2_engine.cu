@@ -68,6 +68,18 @@ int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)
     if (j.o.constraint_mod > 1 && j.o.constraint_rem >= j.o.constraint_mod)
         return fail(c, PT2_ERR_INVALID, "constraint_rem must be below constraint_mod");
     if (j.o.tile_target > (uint32_t)kTileCap) return fail(c, PT2_ERR_INVALID, "tile_target above %d", kTileCap);
+    if (j.o.class_slices > (uint32_t)kNumClasses || (j.o.class_slices > 1 && j.o.class_slice >= j.o.class_slices))
+        return fail(c, PT2_ERR_INVALID, "class_slice must be below class_slices, and class_slices at most %d",
+                    kNumClasses);
+    if (j.o.reserved) return fail(c, PT2_ERR_INVALID, "pt2_opts.reserved must be 0");
+    // alpha classes [cls_lo, cls_hi) of the slice
+    if (j.o.class_slices > 1) {
+        j.cls_lo = (uint32_t)((uint64_t)j.o.class_slice * kNumClasses / j.o.class_slices);
+        j.cls_hi = (uint32_t)((uint64_t)(j.o.class_slice + 1) * kNumClasses / j.o.class_slices);
+    } else {
+        j.cls_lo = 0;
+        j.cls_hi = kNumClasses;
+    }
     j.gp = gen_params(c, *j.s, *j.r);
     j.gp.cons_mod = j.o.constraint_mod > 1 ? j.o.constraint_mod : 1;
     j.gp.cons_rem = j.o.constraint_mod > 1 ? j.o.constraint_rem : 0;
@@ -118,7 +130,8 @@ cudaError_t job_subtract(pt2_ctx *c, const Job &j, RunAcc *acc, cudaStream_t st)
     return launch_ref_subtract(reinterpret_cast<const uint64_t *>(j.r->keys.ptr),
                                reinterpret_cast<const double *>(j.r->coef.ptr),
                                reinterpret_cast<const double *>(j.r->hii.ptr), j.r->n_det, j.r->e0, j.gp.cons_mod,
-                               j.gp.cons_rem, acc, reinterpret_cast<uint32_t *>(c->err_word.ptr), st);
+                               j.gp.cons_rem, reinterpret_cast<const HashTables *>(c->hash.ptr), j.cls_lo, j.cls_hi,
+                               acc, reinterpret_cast<uint32_t *>(c->err_word.ptr), st);
 }
 
 // Whether a job generated the terms its plan counted: exactly, or at most
@@ -206,7 +219,7 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
         Job &j = *jobs[i];
         const unsigned long long *cl = cls.data() + i * kNumClasses;
         j.total = 0;
-        for (int k = 0; k < kNumClasses; ++k) j.total += cl[k];
+        for (int k = (int)j.cls_lo; k < (int)j.cls_hi; ++k) j.total += cl[k];
         uint64_t tt = j.o.tile_target;
         if (!tt) tt = c->tuned_tile[size_class(j.total)];
         if (!tt) tt = kDefaultTileTarget;
@@ -223,8 +236,8 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
         j.pass_cap = cap;
         j.passes.clear();
         Pass cur;
-        cur.c_lo = 0;
-        for (int k = 0; k < kNumClasses; ++k) {
+        cur.c_lo = j.cls_lo;
+        for (int k = (int)j.cls_lo; k < (int)j.cls_hi; ++k) {
             if (cl[k] > cap) {  // heavy alpha class: passes over its beta classes
                 if (cur.records > 0) {
                     cur.c_hi = k;
@@ -269,7 +282,7 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
             }
             cur.records += cl[k];
         }
-        cur.c_hi = kNumClasses;
+        cur.c_hi = j.cls_hi;
         if (cur.records > 0 || j.passes.empty()) j.passes.push_back(cur);
         for (auto &p : j.passes) p.n_tiles = std::max<uint64_t>(1, (p.records + tt - 1) / tt);
         j.next = 0;
@@ -665,6 +678,7 @@ struct Server {
     DevBuf acc_pool;
     std::vector<int> free_slots;
     uint64_t steps_run = 0;
+    uint64_t inflight_bytes = 0;  // pass footprint of the admitted solves
 };
 
 namespace {
@@ -676,6 +690,7 @@ void server_fail_jobs(pt2_ctx *c, std::vector<Job *> &js, int rc)
         j->status = rc;
         j->t_done = now_s();
         j->r->busy--;
+        S.inflight_bytes -= std::min(S.inflight_bytes, j->footprint);
         if (j->acc) S.free_slots.push_back((int)(j->acc - reinterpret_cast<RunAcc *>(S.acc_pool.ptr)));
     }
 }
@@ -685,10 +700,25 @@ void server_iteration(pt2_ctx *c)
 {
     Server &S = *c->server;
     std::vector<Job *> admit;
+    // Admission by HBM footprint: a solve's passes hold at most its terms or
+    // one pass budget of 32-byte records; solves are admitted in arrival order
+    // while the admitted footprint fits two steps of the context's record
+    // budget (what stays free of the HBM budget after systems, references
+    // and fixed workspace), and while slots are left.
+    const uint64_t cap_now = [&] {
+        std::lock_guard<std::recursive_mutex> lock(c->exec);
+        return records_budget(c, 2);
+    }();
     {
         std::lock_guard<std::mutex> lk(S.mu);
         while (!S.pending.empty() && S.active.size() + admit.size() < (size_t)kMaxBatch && !S.free_slots.empty()) {
             Job *j = S.pending.front();
+            const uint64_t terms = terms_per_det(j->s->n, j->r->na, j->r->nb) * j->r->n_det;
+            const uint64_t foot = std::min<uint64_t>(terms, std::max<uint64_t>(cap_now / 2, 1)) * sizeof(Rec32);
+            const bool empty = S.active.empty() && admit.empty();
+            if (!empty && S.inflight_bytes + foot > 2 * cap_now * sizeof(Rec32)) break;  // wait for room
+            j->footprint = foot;
+            S.inflight_bytes += foot;
             S.pending.pop_front();
             j->acc = reinterpret_cast<RunAcc *>(S.acc_pool.ptr) + S.free_slots.back();
             S.free_slots.pop_back();
@@ -771,6 +801,7 @@ void server_iteration(pt2_ctx *c)
         j->result.seconds = t - j->t_submit;
         j->status = terms_as_planned(*j, h[i].n_terms) ? PT2_OK : PT2_ERR_CUDA;
         j->r->busy--;
+        S.inflight_bytes -= std::min(S.inflight_bytes, j->footprint);
         S.free_slots.push_back((int)(j->acc - reinterpret_cast<RunAcc *>(S.acc_pool.ptr)));
         S.active.erase(std::find(S.active.begin(), S.active.end(), j));
     }

@@ -2438,14 +2438,22 @@ cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s)
 __global__ void __launch_bounds__(256) ref_subtract_kernel(const uint64_t *__restrict__ keys,
                                                            const double *__restrict__ coef,
                                                            const double *__restrict__ hii, uint64_t n, double e0,
-                                                           uint64_t cons_mod, uint64_t cons_rem, RunAcc *acc,
-                                                           uint32_t *err)
+                                                           uint64_t cons_mod, uint64_t cons_rem,
+                                                           const HashTables *__restrict__ hash, uint32_t cls_lo,
+                                                           uint32_t cls_hi, RunAcc *acc, uint32_t *err)
 {
     uint64_t lo = 0;
     int64_t hi = 0;
     uint32_t er = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (!cons_ok(cons_mod, cons_rem, keys[2 * i])) continue;
+        const uint64_t A = keys[2 * i];
+        if (!cons_ok(cons_mod, cons_rem, A)) continue;
+        if (cls_lo > 0 || cls_hi < (uint32_t)kNumClasses) {  // a class slice: the alpha string's class
+            uint64_t zc = 0;
+            for (uint64_t x = A; x; x &= x - 1) zc ^= hash->zc[__ffsll((long long)x) - 1];
+            const uint32_t cl = class_of(zc);
+            if (cl < cls_lo || cl >= cls_hi) continue;
+        }
         const double c = coef[i];
         fx_add_double(lo, hi, -((c * c) * (e0 - hii[i])), er);
     }
@@ -2481,11 +2489,13 @@ __global__ void __launch_bounds__(256) ref_subtract_kernel(const uint64_t *__res
 }
 
 cudaError_t launch_ref_subtract(const uint64_t *keys, const double *coef, const double *hii, uint64_t n, double e0,
-                                uint64_t cons_mod, uint64_t cons_rem, RunAcc *acc, uint32_t *err, cudaStream_t s)
+                                uint64_t cons_mod, uint64_t cons_rem, const HashTables *hash, uint32_t cls_lo,
+                                uint32_t cls_hi, RunAcc *acc, uint32_t *err, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const uint64_t blocks = (n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216;
-    ref_subtract_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, coef, hii, n, e0, cons_mod, cons_rem, acc, err);
+    ref_subtract_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, coef, hii, n, e0, cons_mod, cons_rem, hash, cls_lo,
+                                                         cls_hi, acc, err);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct Job {
     SystemRes *s = nullptr;
     pt2_opts o{};
     uint64_t tile_target = 0;
+    uint32_t cls_lo = 0, cls_hi = kNumClasses;  // alpha classes of the run (a class slice, or all)
     uint64_t pass_cap = 0;  // records one pass of this job may hold
     GenParams gp{};         // instance parameters (pass fields filled per step)
     std::vector<Pass> passes;
@@ -68,6 +69,7 @@ struct Job {
     uint64_t ticket = 0;
     uint32_t ref_id = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
+    uint64_t footprint = 0;  // bytes of records its passes may hold (server admission)
     int status = PT2_ERR_BUSY;
     pt2_result result{};
 };

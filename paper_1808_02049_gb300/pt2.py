@@ -51,7 +51,8 @@ class pt2_opts(ctypes.Structure):
     _fields_ = [("constraint_mod", ctypes.c_uint64), ("constraint_rem", ctypes.c_uint64),
                 ("pass_budget_bytes", ctypes.c_uint64), ("tile_target", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("numerator_cutoff", ctypes.c_double),
-                ("debug_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("debug_flags", ctypes.c_uint32), ("class_slices", ctypes.c_uint32),
+                ("class_slice", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class pt2_result(ctypes.Structure):
@@ -127,7 +128,7 @@ def _check(ctx, rc):
 
 def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False,
               spin_symmetric=False, cutoff=0.0, subtract_ref=False, narrow_sort_hash=False,
-              short_copy_wait=False) -> pt2_opts:
+              short_copy_wait=False, class_slice=(0, 1)) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
@@ -138,6 +139,7 @@ def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=Fal
     o.numerator_cutoff = float(cutoff)
     o.debug_flags = ((PT2_DEBUG_NARROW_SORT_HASH if narrow_sort_hash else 0) |
                      (PT2_DEBUG_SHORT_COPY_WAIT if short_copy_wait else 0))
+    o.class_slice, o.class_slices = int(class_slice[0]), int(class_slice[1])
     return o
 
 

@@ -82,3 +82,18 @@ def test_one_alpha_string_matches_oracle(million, level):
     assert abs(got["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
     # the class energy is small, so check it relatively as well
     assert abs(got["e2"] - ref["e2"]) <= 1e-10 * abs(ref["e2"])
+
+
+def test_slices_of_the_full_size_solve(million):
+    # the benchmark's steps: 20 alpha-class slices, which together are one
+    # complete solve of the 4.8e11 terms
+    c, rid = million["c"], million["rid"]
+    full = c.run(rid)
+    parts = [c.run(rid, class_slice=(k, 20)) for k in range(20)]
+    assert sum(p["n_terms"] for p in parts) == full["n_terms"] == 481_824_000_000
+    assert sum(p["n_external"] for p in parts) == full["n_external"]
+    assert sum(p["n_in_ref"] for p in parts) == full["n_in_ref"]
+    assert sum(p["digest_sum"] for p in parts) % (1 << 64) == full["digest_sum"]
+    assert abs(sum(p["e2"] for p in parts) - full["e2"]) <= 1e-14 * abs(full["e2"])
+    # no slice is far from its share (the hash classes spread the terms)
+    assert max(p["n_terms"] for p in parts) < 3 * full["n_terms"] / 20

@@ -327,3 +327,37 @@ def test_invalid_inputs_are_rejected(ctx, small):
 
 def T(n, v):
     return 2 * n * v + 2 * math.comb(n, 2) * math.comb(v, 2) + (n * v) ** 2
+
+
+def test_class_slices_partition_the_solve(ctx, small):
+    # the alpha-class slices are non-overlapping, complete constraint classes
+    # (Algorithm 2): their counts and set digests add up to the full run's
+    # exactly and their energies to its energy
+    full = ctx.run(small["rid"])
+    for m in (7, 20):
+        parts = [ctx.run(small["rid"], class_slice=(k, m)) for k in range(m)]
+        for f in ("n_terms", "n_unique", "n_in_ref", "n_external", "n_pos_denom"):
+            assert sum(p[f] for p in parts) == full[f], (m, f)
+        assert sum(p["digest_sum"] for p in parts) % (1 << 64) == full["digest_sum"]
+        x = 0
+        for p in parts:
+            x ^= p["digest_xor"]
+        assert x == full["digest_xor"]
+        assert abs(sum(p["e2"] for p in parts) - full["e2"]) <= 1e-14 * abs(full["e2"])
+        assert sum(p["n_terms"] > 0 for p in parts) > m // 2
+    assert_same_result(full, small["ref"])
+
+
+def test_class_slices_with_duplicate_subtraction_and_constraint(ctx, small):
+    # each slice subtracts the reference determinants of its own classes only
+    full = ctx.run(small["rid"], subtract_ref=True, constraint=(3, 1))
+    parts = [ctx.run(small["rid"], subtract_ref=True, constraint=(3, 1), class_slice=(k, 5)) for k in range(5)]
+    assert sum(p["n_terms"] for p in parts) == full["n_terms"]
+    assert abs(sum(p["e2"] for p in parts) - full["e2"]) <= 1e-14 * abs(full["e2"])
+
+
+def test_class_slice_options_are_validated(ctx, small):
+    for sl in ((5, 5), (0, 5000), (9, 3)):
+        with pytest.raises(pt2.Pt2Error) as e:
+            ctx.run(small["rid"], class_slice=sl)
+        assert e.value.code == pt2.PT2_ERR_INVALID
