@@ -230,7 +230,7 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
             cap = std::min<uint64_t>(cap, kMaxTilesPerPass * tt);
             cap = std::min<uint64_t>(cap, std::max<uint64_t>(kLocalPassRecords, j.r->n_det * kTermsPerDetPass));
         }
-        cap = std::min<uint64_t>(cap, kMaxPassBytes / sizeof(Rec32));  // slots are 32-bit
+        cap = std::min<uint64_t>(cap, (j.o.pass_budget_bytes ? kMaxPassBytesAsked : kMaxPassBytes) / sizeof(Rec32));
         if (split_large && !j.o.pass_budget_bytes) cap = std::min<uint64_t>(cap, std::max<uint64_t>(step_cap / 2, 1024));
         if (cap < 1024) return fail(c, PT2_ERR_OOM, "pass budget is too small (%llu records)", (unsigned long long)cap);
         j.pass_cap = cap;

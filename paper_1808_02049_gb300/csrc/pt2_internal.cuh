@@ -17,7 +17,8 @@ constexpr int kTileThreads = 256;            // tile sort-reduce CTA (four per S
 constexpr int kTileCap = 1024;               // records a tile CTA sorts in shared memory
 constexpr int kRefSliceSmem = 32;            // reference keys per tile kept in shared memory (larger slices are searched in global memory)
 constexpr uint64_t kMaxTilesPerPass = 6400000;  // keeps the tile cursors (4 B each) resident in L2
-constexpr uint64_t kMaxPassBytes = 96ull << 30;  // bound on one pass's term records
+constexpr uint64_t kMaxPassBytes = 64ull << 30;  // bound on one pass's term records unless the caller asks for more
+constexpr uint64_t kMaxPassBytesAsked = ((1ull << 32) - 1) * 32;  // an explicit pass budget: up to the 32-bit slot limit
 // Emission scatters records over the tiles of a pass; up to about 1.5e9
 // records (1.8M tiles) per pass the partly written tile lines stay in L2.  A
 // pass grows beyond that only when its determinants would otherwise emit
