@@ -239,11 +239,13 @@ int pt2_autotune(pt2_ctx *ctx, uint32_t ref_id, const pt2_opts *opts, uint32_t *
 
 /* ------------------------------------------------------------------ serving
  *
- * Continuous batching: submitted solves queue, are admitted while fewer than
- * 256 are in flight, planned (work-list launch) and then advance one pass per
- * engine step together with every other admitted solve whose next pass fits
- * the step's memory budget; finished solves leave and waiting ones join
- * between steps.  A background host thread of the context runs the engine;
+ * Continuous batching: submitted solves queue and are admitted in arrival
+ * order while fewer than 256 are in flight and their planned pass footprint
+ * (terms, at most one pass of 32-byte records each) fits two steps of the
+ * context's HBM record budget; admitted solves are planned (work-list launch)
+ * and then advance one pass per engine step together with every other
+ * admitted solve whose next pass fits the step's memory budget; finished
+ * solves leave and waiting ones join between steps.  A background host thread of the context runs the engine;
  * systems and references stay resident, and a reference with requests in
  * flight cannot be unloaded (PT2_ERR_BUSY).  Each result is bit-identical to
  * pt2_run of the same reference alone. */
