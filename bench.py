@@ -250,6 +250,38 @@ def bench_subtraction(ctx, rid, exact):
             "note": "timing only: the synthetic reference is not an eigenvector, so E2 differs"}
 
 
+def bench_triplets(ctx, reps=3):
+    """The small workload (4+4 electrons in 16 orbitals, 1,000 determinants)
+    solved as the sum of its triplet constraints, one run per triplet T (the
+    "Triplet constraints" section: every run regenerates the terms of all
+    determinants and keeps those whose three highest occupied alpha orbitals
+    are T, with Algorithm 3 for the alpha-alpha doubles), against one run whose
+    passes are ranges of alpha-hash classes (wall time of the blocking calls)."""
+    import itertools
+
+    s, r = workload("small")
+    sid = ctx.load_system(s.h, s.eri)
+    e0 = float(ctx.diagonal(sid, r.keys).min() - 0.1)
+    rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    try:
+        full, t_full = best_of(ctx, rid, reps)
+        masks = [sum(1 << q for q in o) for o in itertools.combinations(range(16), 3)]
+        for T in masks[:20]:
+            ctx.run(rid, top_alpha=T)  # warm-up
+        t0 = time.perf_counter()
+        parts = [ctx.run(rid, top_alpha=T) for T in masks]
+        t_trip = time.perf_counter() - t0
+    finally:
+        ctx.unload(rid)
+        ctx.unload(sid)
+    return {"workload": "small: 4+4 electrons in 16 orbitals, N_det=1000", "triplets": len(masks),
+            "nonempty_triplets": sum(1 for p in parts if p["n_terms"]),
+            "ms_hash_classes": t_full * 1e3, "ms_all_triplets": t_trip * 1e3, "ratio": t_trip / t_full,
+            "terms": full["n_terms"], "terms_sum_triplets": sum(p["n_terms"] for p in parts),
+            "e2_rel_diff": abs(sum(p["e2"] for p in parts) - full["e2"]) / abs(full["e2"]),
+            "note": "per-constraint regeneration: each triplet run enumerates every determinant's excitations"}
+
+
 def bench_spin_symmetric(ctx, reps=2):
     """The 40-orbital system with a reference closed under alpha <-> beta
     exchange (100,000 determinants with their mirrors, equal coefficients):
@@ -547,6 +579,7 @@ def run_gpu(args):
         extra["subtraction"] = bench_subtraction(ctx, rid, per_slice)
         lsid, lrid, lres, lsec, extra["large"] = bench_large(ctx)
         extra["spin_symmetric"] = bench_spin_symmetric(ctx)
+        extra["triplets"] = bench_triplets(ctx)
         fleet = load_fleet(ctx)
         extra["batched"] = bench_batched(ctx, fleet, reps=2)
         if args.served_requests > 0:

@@ -134,6 +134,17 @@ typedef struct {
                                    most 4096; combines with constraint_mod. */
     uint32_t class_slice;
     uint32_t reserved;          /* must be 0 */
+    uint64_t top_alpha;         /* 0: none.  Otherwise a bit mask T of k alpha
+                                   orbitals: only excited determinants whose k
+                                   highest occupied alpha orbitals are exactly
+                                   T are summed (the "Triplet constraints"
+                                   section: k = 3 a triplet, k = 4 a
+                                   quadruplet constraint; for each k the masks
+                                   T form a non-overlapping, complete
+                                   partition).  The alpha-alpha doubles of
+                                   such a run are generated directly
+                                   (Algorithm 3).  Combines with the other
+                                   constraints. */
 } pt2_opts;
 
 #define PT2_FLAG_PROFILE 1u   /* record per-phase device times (pt2_phase_times); a batch created

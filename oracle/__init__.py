@@ -63,7 +63,8 @@ def _load():
             P = ctypes.c_void_p
             lib.oracle_pt2.restype = ctypes.c_int64
             lib.oracle_pt2.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P, P, ctypes.c_double,
-                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                       ctypes.c_double,
                                        ctypes.POINTER(OracleResult), P, P, P, ctypes.c_int64]
             lib.oracle_diagonals.restype = None
             lib.oracle_diagonals.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P, P]
@@ -94,7 +95,7 @@ def _prep(h, eri, keys=None, coef=None):
     return out
 
 
-def pt2(h, eri, keys, coef, e0, constraint=(1, 0), include_ref=False, cutoff=0.0) -> dict:
+def pt2(h, eri, keys, coef, e0, constraint=(1, 0), include_ref=False, cutoff=0.0, top_alpha=0) -> dict:
     """E2 and the connected-set statistics (see pt2_oracle.c); contributions
     |c_i H_ai| below `cutoff` are ignored."""
     lib = _load()
@@ -102,21 +103,22 @@ def pt2(h, eri, keys, coef, e0, constraint=(1, 0), include_ref=False, cutoff=0.0
     n = h.shape[0]
     res = OracleResult()
     rc = lib.oracle_pt2(n, _p(h), _p(eri), coef.shape[0], _p(keys), _p(coef), float(e0),
-                        int(constraint[0]), int(constraint[1]), int(bool(include_ref)), float(cutoff),
+                        int(constraint[0]), int(constraint[1]), int(top_alpha), int(bool(include_ref)),
+                        float(cutoff),
                         ctypes.byref(res), None, None, None, 0)
     if rc < 0:
         raise ValueError(f"oracle_pt2 failed with code {rc}")
     return res.as_dict()
 
 
-def dump_external(h, eri, keys, coef, e0, constraint=(1, 0), cutoff=0.0):
+def dump_external(h, eri, keys, coef, e0, constraint=(1, 0), cutoff=0.0, top_alpha=0):
     """Sorted external keys (n, 2) uint64 with summed numerators and direct diagonals."""
     lib = _load()
     h, eri, keys, coef = _prep(h, eri, keys, coef)
     n = h.shape[0]
     res = OracleResult()
     rc = lib.oracle_pt2(n, _p(h), _p(eri), coef.shape[0], _p(keys), _p(coef), float(e0),
-                        int(constraint[0]), int(constraint[1]), 0, float(cutoff), ctypes.byref(res),
+                        int(constraint[0]), int(constraint[1]), int(top_alpha), 0, float(cutoff), ctypes.byref(res),
                         None, None, None, 0)
     if rc < 0:
         raise ValueError(f"oracle_pt2 failed with code {rc}")
@@ -125,7 +127,7 @@ def dump_external(h, eri, keys, coef, e0, constraint=(1, 0), cutoff=0.0):
     num = np.zeros(max(m, 1))
     haa = np.zeros(max(m, 1))
     rc = lib.oracle_pt2(n, _p(h), _p(eri), coef.shape[0], _p(keys), _p(coef), float(e0),
-                        int(constraint[0]), int(constraint[1]), 0, float(cutoff), ctypes.byref(res),
+                        int(constraint[0]), int(constraint[1]), int(top_alpha), 0, float(cutoff), ctypes.byref(res),
                         _p(k), _p(num), _p(haa), m)
     if rc != m:
         raise ValueError(f"oracle dump returned {rc}, expected {m}")

@@ -37,7 +37,10 @@
  * (pq|rs) = eri[((p*n + q)*n + r)*n + s].
  *
  * Optional constraint (Algorithm 2, one constraint class): when mod > 1 only
- * excited determinants whose alpha word satisfies alpha % mod == rem are kept.
+ * excited determinants whose alpha word satisfies alpha % mod == rem are kept;
+ * when top != 0, only those whose k = popcount(top) highest occupied alpha
+ * orbitals are exactly the orbitals of top (the triplet constraint of the
+ * "Triplet constraints" section for k = 3, the quadruplet one for k = 4).
  * The classes r = 0..mod-1 are non-overlapping and complete, so their E2 sum
  * to the unconstrained E2.  When mod exceeds every alpha word (mod > 2^n_orb
  * - 1) the class is the single alpha string rem; a single or double
@@ -240,10 +243,24 @@ typedef void (*visit_fn)(void *ctx, uint64_t a, uint64_t b, double value);
 
 typedef struct {
     uint64_t mod, rem;
+    uint64_t top;
 } constraint_t;
+
+/* The k highest occupied orbitals of word a, as a mask (fewer if a has fewer). */
+static uint64_t highest_occupied(uint64_t a, int k)
+{
+    uint64_t m = 0;
+    for (int p = 63; p >= 0 && k > 0; --p)
+        if ((a >> p) & 1ull) {
+            m |= 1ull << p;
+            --k;
+        }
+    return m;
+}
 
 static int keep_alpha(const constraint_t *c, uint64_t a)
 {
+    if (c->top && highest_occupied(a, __builtin_popcountll(c->top)) != c->top) return 0;
     return c->mod <= 1 || (a % c->mod) == c->rem;
 }
 
@@ -412,14 +429,14 @@ static int check_ref(int n_orb, int64_t n_det, const uint64_t *keys)
  */
 int64_t oracle_pt2(int n_orb, const double *h, const double *eri, int64_t n_det,
                    const uint64_t *keys, const double *coef, double e0,
-                   uint64_t cons_mod, uint64_t cons_rem, int include_ref, double cutoff,
+                   uint64_t cons_mod, uint64_t cons_rem, uint64_t top, int include_ref, double cutoff,
                    oracle_result *out, uint64_t *dump_keys, double *dump_num,
                    double *dump_haa, int64_t dump_cap)
 {
     if (check_ref(n_orb, n_det, keys)) return -1;
     if (!(cutoff >= 0.0) || isinf(cutoff)) return -1;
     sys_t s = {n_orb, h, eri};
-    constraint_t cons = {cons_mod, cons_rem};
+    constraint_t cons = {cons_mod, cons_rem, top};
     memset(out, 0, sizeof(*out));
     out->min_abs_denom = INFINITY;
 
@@ -523,7 +540,7 @@ int64_t oracle_det_terms(int n_orb, const double *h, const double *eri, uint64_t
                          double *val, double *haa, int64_t cap)
 {
     sys_t s = {n_orb, h, eri};
-    constraint_t cons = {cons_mod, cons_rem};
+    constraint_t cons = {cons_mod, cons_rem, 0};
     list_ctx l = {&s, keys, val, haa, cap, 0};
     enumerate_det(&s, wa, wb, c, &cons, visit_list, &l);
     return l.n;

@@ -151,6 +151,8 @@ GenParams gen_params(pt2_ctx *c, const SystemRes &s, const RefRes &r)
     p.cutoff = 0.0;
     p.subtract = 0;
     p.cons_mod = 1;
+    p.top_mask = 0;
+    p.top_hi = 0;
     p.err = (uint32_t *)c->err_word.ptr;
     return p;
 }

@@ -83,6 +83,9 @@ int init_job(pt2_ctx *c, Job &j, uint32_t ref_id, const pt2_opts *o)
     j.gp = gen_params(c, *j.s, *j.r);
     j.gp.cons_mod = j.o.constraint_mod > 1 ? j.o.constraint_mod : 1;
     j.gp.cons_rem = j.o.constraint_mod > 1 ? j.o.constraint_rem : 0;
+    // the highest occupied alpha orbitals of every summed excited determinant
+    j.gp.top_mask = j.o.top_alpha;
+    j.gp.top_hi = j.o.top_alpha ? ~((1ull << __builtin_ctzll(j.o.top_alpha)) - 1ull) : 0ull;
     if (j.o.flags & PT2_FLAG_SPIN_SYMMETRIC) {
         if (!j.r->flip_symmetric)
             return fail(c, PT2_ERR_INVALID,
@@ -130,7 +133,8 @@ cudaError_t job_subtract(pt2_ctx *c, const Job &j, RunAcc *acc, cudaStream_t st)
     return launch_ref_subtract(reinterpret_cast<const uint64_t *>(j.r->keys.ptr),
                                reinterpret_cast<const double *>(j.r->coef.ptr),
                                reinterpret_cast<const double *>(j.r->hii.ptr), j.r->n_det, j.r->e0, j.gp.cons_mod,
-                               j.gp.cons_rem, reinterpret_cast<const HashTables *>(c->hash.ptr), j.cls_lo, j.cls_hi,
+                               j.gp.cons_rem, j.gp.top_hi, j.gp.top_mask,
+                               reinterpret_cast<const HashTables *>(c->hash.ptr), j.cls_lo, j.cls_hi,
                                acc, reinterpret_cast<uint32_t *>(c->err_word.ptr), st);
 }
 

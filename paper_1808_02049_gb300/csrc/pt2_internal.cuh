@@ -116,6 +116,7 @@ struct GenParams {
     double cutoff;                // numerator cutoff: contributions |c_i H_ai| below it are dropped (0: none)
     uint32_t subtract;            // duplicate subtraction: reference keys stay in the sum (no reference slices)
     uint64_t cons_mod, cons_rem;  // alpha % mod == rem (mod <= 1: none)
+    uint64_t top_mask, top_hi;    // alpha & top_hi == top_mask: the highest occupied alpha orbitals are top_mask (0, 0: none)
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance
     // outputs
@@ -231,11 +232,12 @@ cudaError_t launch_pass_finish(const unsigned long long *tile_off, const unsigne
                                const unsigned long long *expected, RunAcc *const *acc, unsigned int *n_big,
                                uint32_t *err, cudaStream_t s);
 cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s);
-// acc.E2 -= sum over the reference determinants of the constraint class (alpha % cons_mod == cons_rem
-// and alpha class in [cls_lo, cls_hi)) of c_i^2 (E0 - H_ii), exactly
+// acc.E2 -= sum over the reference determinants of the constraint class (alpha % cons_mod == cons_rem,
+// the top-orbital constraint and alpha class in [cls_lo, cls_hi)) of c_i^2 (E0 - H_ii), exactly
 cudaError_t launch_ref_subtract(const uint64_t *keys, const double *coef, const double *hii, uint64_t n, double e0,
-                                uint64_t cons_mod, uint64_t cons_rem, const HashTables *hash, uint32_t cls_lo,
-                                uint32_t cls_hi, RunAcc *acc, uint32_t *err, cudaStream_t s);
+                                uint64_t cons_mod, uint64_t cons_rem, uint64_t top_hi, uint64_t top_mask,
+                                const HashTables *hash, uint32_t cls_lo, uint32_t cls_hi, RunAcc *acc, uint32_t *err,
+                                cudaStream_t s);
 cudaError_t launch_acc_finalize(RunAcc *acc, int n, cudaStream_t s);
 // num^2 / den with the tile kernels' arithmetic (den in Hartree, rounded to 2^-48)
 cudaError_t launch_eval_terms(const double *num, const double *den, uint64_t n, double *out, cudaStream_t s);

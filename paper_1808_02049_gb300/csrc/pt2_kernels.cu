@@ -49,9 +49,14 @@ namespace pt2 {
 
 __device__ __forceinline__ uint32_t class_of(uint64_t zc) { return (uint32_t)(zc >> (64 - kClassBits)); }
 
-__device__ __forceinline__ bool cons_ok(uint64_t mod, uint64_t rem, uint64_t alpha)
+// Constraint classes of Algorithm 2 on an excited alpha string: alpha % mod ==
+// rem (mod <= 1: none), and the triplet constraint of the "Triplet
+// constraints" section generalised to k orbitals: the k highest occupied
+// alpha orbitals are exactly T (tmask = T, thi = every bit at or above T's
+// lowest; both 0: none).
+__device__ __forceinline__ bool cons_ok(uint64_t mod, uint64_t rem, uint64_t thi, uint64_t tmask, uint64_t alpha)
 {
-    return mod <= 1 || (alpha % mod) == rem;
+    return (alpha & thi) == tmask && (mod <= 1 || (alpha % mod) == rem);
 }
 
 // bits strictly between orbitals x and y
@@ -649,12 +654,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         uint64_t zc = F.ZcA ^ F.zc[r] ^ F.zc[a];
         uint32_t inp;
         if constexpr (MODE == kModeClassCount) {
-            inp = cons_ok(p.cons_mod, p.cons_rem, a2);
+            inp = cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
         } else if constexpr (MODE == kModeBetaCount) {
-            inp = class_of(zc) == p.heavy_class && cons_ok(p.cons_mod, p.cons_rem, a2);
+            inp = class_of(zc) == p.heavy_class && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
         } else {
             uint32_t cl = class_of(zc);
-            inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, a2);
+            inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
         }
         if constexpr (kVal) sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
         sa_zt[s] = kCount ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
@@ -673,7 +678,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (binp << 17);
     }
     if (tid == 0) {
-        bool ok = cons_ok(p.cons_mod, p.cons_rem, A);
+        bool ok = cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, A);
         if constexpr (MODE == kModeBetaCount) {
             ok = ok && class_of(F.ZcA) == p.heavy_class;
         } else if constexpr (MODE != kModeClassCount) {
@@ -764,7 +769,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 int pv = pairs[t];
                 int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
-                if (!cons_ok(p.cons_mod, p.cons_rem, al)) continue;
+                if (!cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, al)) continue;
                 if (sym && al < B) continue;
                 atomicAdd(&hist[class_of(z12 ^ F.zc[a1] ^ F.zc[a2])], 1u);
             }
@@ -811,7 +816,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 if (class_of(z12 ^ F.zc[a1] ^ F.zc[a2]) != K) continue;
                 const uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
-                if (!cons_ok(p.cons_mod, p.cons_rem, al)) continue;
+                if (!cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, al)) continue;
                 if (sym && al < B) continue;
                 ++keepB;
             }
@@ -1065,6 +1070,79 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                       (F.gA[a2] - __ldg(WSx + r1 * N + a2) - __ldg(WSx + r2 * N + a2)) - __ldg(WSx + a1 * N + a2);
             };
             __syncthreads();  // the alpha-beta warps are done with vec
+            // list the candidates [c0, c1) that `cand` turns into items and emit
+            // them, in rounds of at most kListCap
+            auto list_and_emit = [&](uint32_t total, auto cand) {
+                for (uint32_t c0 = 0; c0 < total; c0 += kListCap) {
+                    if (tid == 0) F.n_list = 0;
+                    __syncthreads();
+                    const uint32_t c1 = min(total, c0 + kListCap);
+                    for (uint32_t cb = c0; cb < c1; cb += kGenThreads) {
+                        const uint32_t ci = cb + tid;
+                        uint32_t item = 0;
+                        const bool keep = ci < c1 && cand(ci, item);
+                        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+                        if (m) {
+                            const int leader = __ffs(m) - 1;
+                            uint32_t base = 0;
+                            if (lane == leader) base = atomicAdd(&F.n_list, (unsigned)__popc(m));
+                            base = __shfl_sync(0xffffffffu, base, leader);
+                            if (keep) clist[base + __popc(m & lt)] = item;
+                        }
+                    }
+                    __syncthreads();
+                    const int nl = (int)F.n_list;
+                    for (int k0 = tid; k0 < nl; k0 += kGenThreads * kAaBatch)
+                        emit_batch<MODE, kAaBatch>(out, k0, kGenThreads, nl, key_aa, val_aa);
+                    __syncthreads();  // the list area is reused
+                }
+            };
+            // an item of occupied pair pi and virtual pair vp (colex pair
+            // indices into occA / virA) if its alpha class lies in the pass
+            // and it meets the constraints
+            auto aa_item = [&](int pi, int vp, uint32_t &item) {
+                const int pr = pairs[pi], pv = pairs[vp];
+                const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+                const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
+                const uint32_t cl = class_of(F.ZcA ^ F.zc[r1] ^ F.zc[r2] ^ F.zc[a1] ^ F.zc[a2]);
+                const uint64_t w2 = A ^ (1ull << r1) ^ (1ull << r2) ^ (1ull << a1) ^ (1ull << a2);
+                item = ((uint32_t)pi << 16) | (uint32_t)vp;
+                return cl >= p.class_lo && cl < p.class_hi &&
+                       cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, w2) && !(sym && w2 < B);
+            };
+            if (p.top_mask) {
+                // Algorithm 3 (fast generation for a triplet constraint T): the
+                // double keeps T as the highest occupied orbitals iff it removes
+                // every occupied orbital at or above T's lowest that is not in T
+                // (R), adds the orbitals of T that are empty (Q), and takes its
+                // other orbitals below T's lowest.  Those are the first L
+                // occupied and the first Lv virtual orbitals, so the occupied
+                // pairs (and likewise the virtual ones) are: R itself (|R| = 2),
+                // R's orbital with each of the first L (|R| = 1), or every pair
+                // of the first L (|R| = 0).
+                const uint64_t T = p.top_mask;
+                const uint64_t R = A & p.top_hi & ~T, Q = T & ~A;
+                const int nr = __popcll(R), nq = __popcll(Q);
+                const int tlo = __ffsll((long long)T) - 1;
+                const int L = __popcll(A & ((1ull << tlo) - 1ull)), Lv = tlo - L;
+                const bool fits = nr <= 2 && nq <= 2 && (N >= 64 || (T >> N) == 0);
+                if (fits) {  // uniform across the CTA
+                    auto colex = [](int i, int j) { return j * (j - 1) / 2 + i; };  // pair i < j
+                    auto occ_pos = [&](uint64_t bits) { return __popcll(A & (bits - 1ull)); };
+                    auto vir_pos = [&](uint64_t bits) { return (__ffsll((long long)bits) - 1) - occ_pos(bits); };
+                    const uint64_t r1b = R & (~R + 1ull), q1b = Q & (~Q + 1ull);
+                    const int ir1 = nr ? occ_pos(r1b) : 0, ir2 = nr == 2 ? occ_pos(R ^ r1b) : 0;
+                    const int iq1 = nq ? vir_pos(q1b) : 0, iq2 = nq == 2 ? vir_pos(Q ^ q1b) : 0;
+                    const uint32_t nO = nr == 2 ? 1u : nr == 1 ? (uint32_t)L : (uint32_t)(L * (L - 1) / 2);
+                    const uint32_t nV = nq == 2 ? 1u : nq == 1 ? (uint32_t)Lv : (uint32_t)(Lv * (Lv - 1) / 2);
+                    list_and_emit(nO * nV, [&](uint32_t ci, uint32_t &item) {
+                        const int io = (int)(ci / nV), iv = (int)(ci - (uint32_t)io * nV);
+                        const int pi = nr == 2 ? colex(ir1, ir2) : nr == 1 ? colex(io, ir1) : io;
+                        const int vp = nq == 2 ? colex(iq1, iq2) : nq == 1 ? colex(iv, iq1) : iv;
+                        return aa_item(pi, vp, item);
+                    });
+                }
+            } else {
             for (int p0 = 0; p0 < npo; p0 += kPairGroup) {
                 const int np = min(kPairGroup, npo - p0);
                 for (int t = tid; t <= np; t += kGenThreads) {
@@ -1082,61 +1160,30 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 }
                 __syncthreads();
                 block_scan_excl_u32(poff, np + 1, F.wsum);
-                const uint32_t total = poff[np];
-                for (uint32_t c0 = 0; c0 < total; c0 += kListCap) {
-                    if (tid == 0) F.n_list = 0;
-                    __syncthreads();
-                    const uint32_t c1 = min(total, c0 + kListCap);
-                    for (uint32_t cb = c0; cb < c1; cb += kGenThreads) {
-                        const uint32_t ci = cb + tid;
-                        bool keep = false;
-                        uint32_t item = 0;
-                        if (ci < c1) {
-                            int lo = 0, hi = np;  // the occupied pair: last t with poff[t] <= ci
-                            while (hi - lo > 1) {
-                                const int mid = (lo + hi) >> 1;
-                                if (poff[mid] <= ci) lo = mid;
-                                else hi = mid;
-                            }
-                            const int pr = pairs[p0 + lo];
-                            const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
-                            const uint64_t zc12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
-                            const uint32_t u = vb_bucket(zc12);
-                            uint32_t i = ci - poff[lo];
-                            int vp = 0;
-                            for (int q = 0; q < F.n_blk; ++q) {
-                                const uint32_t k = F.blk_k[q];
-                                const uint32_t bb = (F.blk_g[q] ^ u) & ~((1u << k) - 1u);
-                                const uint32_t st = vb_off[bb], sz = (uint32_t)vb_off[bb + (1u << k)] - st;
-                                if (i < sz) {
-                                    vp = vb_list[st + i];
-                                    break;
-                                }
-                                i -= sz;
-                            }
-                            const int pv = pairs[vp];
-                            const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
-                            const uint32_t cl = class_of(zc12 ^ F.zc[a1] ^ F.zc[a2]);
-                            const uint64_t w2 = A ^ (1ull << r1) ^ (1ull << r2) ^ (1ull << a1) ^ (1ull << a2);
-                            keep = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, w2) &&
-                                   !(sym && w2 < B);
-                            item = ((uint32_t)(p0 + lo) << 16) | (uint32_t)vp;
-                        }
-                        const uint32_t m = __ballot_sync(0xffffffffu, keep);
-                        if (m) {
-                            const int leader = __ffs(m) - 1;
-                            uint32_t base = 0;
-                            if (lane == leader) base = atomicAdd(&F.n_list, (unsigned)__popc(m));
-                            base = __shfl_sync(0xffffffffu, base, leader);
-                            if (keep) clist[base + __popc(m & lt)] = item;
-                        }
+                list_and_emit(poff[np], [&](uint32_t ci, uint32_t &item) {
+                    int lo = 0, hi = np;  // the occupied pair: last t with poff[t] <= ci
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (poff[mid] <= ci) lo = mid;
+                        else hi = mid;
                     }
-                    __syncthreads();
-                    const int nl = (int)F.n_list;
-                    for (int k0 = tid; k0 < nl; k0 += kGenThreads * kAaBatch)
-                        emit_batch<MODE, kAaBatch>(out, k0, kGenThreads, nl, key_aa, val_aa);
-                    __syncthreads();  // the list area is reused
-                }
+                    const int pr = pairs[p0 + lo];
+                    const uint32_t u = vb_bucket(F.ZcA ^ F.zc[F.occA[pr & 0xFF]] ^ F.zc[F.occA[pr >> 8]]);
+                    uint32_t i = ci - poff[lo];
+                    int vp = 0;
+                    for (int q = 0; q < F.n_blk; ++q) {
+                        const uint32_t k = F.blk_k[q];
+                        const uint32_t bb = (F.blk_g[q] ^ u) & ~((1u << k) - 1u);
+                        const uint32_t st = vb_off[bb], sz = (uint32_t)vb_off[bb + (1u << k)] - st;
+                        if (i < sz) {
+                            vp = vb_list[st + i];
+                            break;
+                        }
+                        i -= sz;
+                    }
+                    return aa_item(p0 + lo, vp, item);
+                });
+            }
             }
         }
         // ---- beta-beta doubles (alpha string A): one occupied pair per warp,
@@ -1535,7 +1582,7 @@ __global__ void ref_tile_kernel(const RefPartParams p)
     uint32_t t = 0xFFFFFFFFu;
     // a run with duplicate subtraction keeps the reference keys in the sum
     if (!q.subtract && cl >= q.class_lo && cl < q.class_hi && bc >= q.bclass_lo && bc < q.bclass_hi &&
-        cons_ok(q.cons_mod, q.cons_rem, A)) {
+        cons_ok(q.cons_mod, q.cons_rem, q.top_hi, q.top_mask, A)) {
         t = (uint32_t)(q.tile_base + tile_of(zt, (uint32_t)q.n_tiles));
         atomicAdd(&p.ref_count[t], 1u);
     }
@@ -2438,8 +2485,9 @@ cudaError_t launch_acc_init(RunAcc *acc, int n, cudaStream_t s)
 __global__ void __launch_bounds__(256) ref_subtract_kernel(const uint64_t *__restrict__ keys,
                                                            const double *__restrict__ coef,
                                                            const double *__restrict__ hii, uint64_t n, double e0,
-                                                           uint64_t cons_mod, uint64_t cons_rem,
-                                                           const HashTables *__restrict__ hash, uint32_t cls_lo,
+                                                           uint64_t cons_mod, uint64_t cons_rem, uint64_t top_hi,
+                                                           uint64_t top_mask, const HashTables *__restrict__ hash,
+                                                           uint32_t cls_lo,
                                                            uint32_t cls_hi, RunAcc *acc, uint32_t *err)
 {
     uint64_t lo = 0;
@@ -2447,7 +2495,7 @@ __global__ void __launch_bounds__(256) ref_subtract_kernel(const uint64_t *__res
     uint32_t er = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t A = keys[2 * i];
-        if (!cons_ok(cons_mod, cons_rem, A)) continue;
+        if (!cons_ok(cons_mod, cons_rem, top_hi, top_mask, A)) continue;
         if (cls_lo > 0 || cls_hi < (uint32_t)kNumClasses) {  // a class slice: the alpha string's class
             uint64_t zc = 0;
             for (uint64_t x = A; x; x &= x - 1) zc ^= hash->zc[__ffsll((long long)x) - 1];
@@ -2489,13 +2537,14 @@ __global__ void __launch_bounds__(256) ref_subtract_kernel(const uint64_t *__res
 }
 
 cudaError_t launch_ref_subtract(const uint64_t *keys, const double *coef, const double *hii, uint64_t n, double e0,
-                                uint64_t cons_mod, uint64_t cons_rem, const HashTables *hash, uint32_t cls_lo,
-                                uint32_t cls_hi, RunAcc *acc, uint32_t *err, cudaStream_t s)
+                                uint64_t cons_mod, uint64_t cons_rem, uint64_t top_hi, uint64_t top_mask,
+                                const HashTables *hash, uint32_t cls_lo, uint32_t cls_hi, RunAcc *acc, uint32_t *err,
+                                cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const uint64_t blocks = (n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216;
-    ref_subtract_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, coef, hii, n, e0, cons_mod, cons_rem, hash, cls_lo,
-                                                         cls_hi, acc, err);
+    ref_subtract_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, coef, hii, n, e0, cons_mod, cons_rem, top_hi, top_mask,
+                                                         hash, cls_lo, cls_hi, acc, err);
     return cudaGetLastError();
 }
 

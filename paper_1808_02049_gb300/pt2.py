@@ -52,7 +52,8 @@ class pt2_opts(ctypes.Structure):
                 ("pass_budget_bytes", ctypes.c_uint64), ("tile_target", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("numerator_cutoff", ctypes.c_double),
                 ("debug_flags", ctypes.c_uint32), ("class_slices", ctypes.c_uint32),
-                ("class_slice", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("class_slice", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("top_alpha", ctypes.c_uint64)]
 
 
 class pt2_result(ctypes.Structure):
@@ -128,7 +129,7 @@ def _check(ctx, rc):
 
 def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False,
               spin_symmetric=False, cutoff=0.0, subtract_ref=False, narrow_sort_hash=False,
-              short_copy_wait=False, class_slice=(0, 1)) -> pt2_opts:
+              short_copy_wait=False, class_slice=(0, 1), top_alpha=0) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
@@ -140,6 +141,7 @@ def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=Fal
     o.debug_flags = ((PT2_DEBUG_NARROW_SORT_HASH if narrow_sort_hash else 0) |
                      (PT2_DEBUG_SHORT_COPY_WAIT if short_copy_wait else 0))
     o.class_slice, o.class_slices = int(class_slice[0]), int(class_slice[1])
+    o.top_alpha = int(top_alpha)
     return o
 
 

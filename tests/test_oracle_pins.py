@@ -323,3 +323,58 @@ def test_oracle_rejects_invalid_reference():
     bad[4] |= np.uint64(1 << 20)  # bit beyond n_orb = 16, wrong popcount
     with pytest.raises(ValueError):
         oracle.pt2(s.h, s.eri, bad, r.coef, -10.0)
+
+
+def _top_orbitals(word, k):
+    """The k highest set bits of word as a mask (a plain restatement of the
+    triplet constraint's definition, independent of the oracle's C)."""
+    bits = [p for p in range(64) if (int(word) >> p) & 1]
+    return sum(1 << p for p in bits[-k:]) if len(bits) >= k else -1
+
+
+def test_triplet_constraint_matches_brute_force(brute_cases):
+    # per triplet T: the brute-force external set and energy restricted to
+    # determinants whose three highest occupied alpha orbitals are T
+    import itertools
+
+    for c in brute_cases:
+        n = c["h"].shape[0]
+        na = bin(int(c["ref"][0][0])).count("1")
+        if na < 3:
+            continue
+        keys = keys_of(c["ref"])
+        bf = brute.pt2(c["h"], c["eri"], c["dets"], c["H"], c["ref_idx"], c["coef"], c["e0"])
+        terms = bf["num"] ** 2 / (c["e0"] - bf["haa"])
+        tops = np.array([_top_orbitals(k[0], 3) for k in bf["keys"]])
+        seen = 0
+        for trip in itertools.combinations(range(n), 3):
+            T = sum(1 << p for p in trip)
+            sel = tops == T
+            res = oracle.pt2(c["h"], c["eri"], keys, c["coef"], c["e0"], top_alpha=T)
+            assert res["n_external"] == int(sel.sum())
+            assert abs(res["e2"] - terms[sel].sum()) <= 1e-12 * max(1.0, abs(bf["e2"]))
+            seen += int(sel.sum())
+        assert seen == len(bf["keys"])
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_top_orbital_constraints_partition_the_sum(k):
+    # the triplet (k = 3) and quadruplet (k = 4) constraints are
+    # non-overlapping and complete: over every mask of k of the 16 orbitals
+    # the classes rebuild the unconstrained result exactly
+    import itertools
+
+    s, r = inputs.make_workload("small", n_det=40 if k == 3 else 15)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    base = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0)
+    tot = dict(n_terms=0, n_external=0, n_in_ref=0, digest_sum=0, digest_xor=0, e2=0.0)
+    for orbs in itertools.combinations(range(16), k):
+        p = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, top_alpha=sum(1 << q for q in orbs))
+        for f in ("n_terms", "n_external", "n_in_ref"):
+            tot[f] += p[f]
+        tot["digest_sum"] = (tot["digest_sum"] + p["digest_sum"]) % 2 ** 64
+        tot["digest_xor"] ^= p["digest_xor"]
+        tot["e2"] += p["e2"]
+    for f in ("n_terms", "n_external", "n_in_ref", "digest_sum", "digest_xor"):
+        assert tot[f] == base[f], f
+    assert abs(tot["e2"] - base["e2"]) <= 1e-12 * abs(base["e2"])
