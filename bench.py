@@ -233,6 +233,25 @@ def bench_cutoff(ctx, rid, exact, cut=1e-8):
             "delta_e2": sum(r["e2"] for r in res) - sum(exact[k][0]["e2"] for k in ks)}
 
 
+def bench_hashed_keys(ctx, rid, exact):
+    """Keys of a tile identified by a 54-bit hash (the hashing section) on two
+    slices of the headline workload, against the same slices' timed exact
+    solves: time, and whether the hash merged different keys."""
+    ks = sorted(exact)[:2]
+    t_ex = sum(exact[k][1] for k in ks)
+    t_h, res = 0.0, []
+    for k in ks:
+        ctx.run(rid, class_slice=(k, SLICES), hashed_keys=True)
+        r, dt = timed_run(ctx, rid, class_slice=(k, SLICES), hashed_keys=True)
+        res.append(r)
+        t_h += dt
+    same = all(r["e2"] == exact[k][0]["e2"] and r["n_external"] == exact[k][0]["n_external"]
+               and r["digest_sum"] == exact[k][0]["digest_sum"] for r, k in zip(res, ks))
+    return {"slices": [f"{k}/{SLICES}" for k in ks], "ms_exact": t_ex * 1e3, "ms_hashed": t_h * 1e3,
+            "speedup": t_ex / t_h, "merged_records": sum(r["n_hash_collisions"] for r in res),
+            "identical_to_exact": bool(same)}
+
+
 def bench_subtraction(ctx, rid, exact):
     """Duplicate subtraction on slices of the headline workload against the
     explicit filter (timed in the measured steps).  The synthetic reference is
@@ -411,10 +430,10 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began df854c5b
-    "kernels_sha256": "4771c9f1812831be724b0fa517518c0441955a08b149c7ae9b9a004d96a330c4",
-    "tile_kernel": (1.445603e9 + 3.888128e6) / 45_176_097,     # 32.09 B per term
-    "gen_kernel<Emit>": (0.217464e9 + 1.394030e9) / 45_176_097,  # 35.67 B per term
+    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began 62af1956
+    "kernels_sha256": "47fa7006f944aef63914c548150ed4cb71088c406836ac6830620e040b82c905",
+    "tile_kernel": (1.444859e9 + 3.687168e6) / 45_176_097,     # 32.06 B per term
+    "gen_kernel<Emit>": (0.217976e9 + 1.394653e9) / 45_176_097,  # 35.70 B per term
 }
 
 
@@ -577,6 +596,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_batch:
         extra["cutoff"] = bench_cutoff(ctx, rid, per_slice)
         extra["subtraction"] = bench_subtraction(ctx, rid, per_slice)
+        extra["hashed_keys"] = bench_hashed_keys(ctx, rid, per_slice)
         lsid, lrid, lres, lsec, extra["large"] = bench_large(ctx)
         extra["spin_symmetric"] = bench_spin_symmetric(ctx)
         extra["triplets"] = bench_triplets(ctx)

@@ -168,6 +168,17 @@ typedef struct {
  * n_in_ref is then 0 and n_external, the digest, min_abs_denom and
  * n_pos_denom cover every generated key, reference keys included. */
 #define PT2_FLAG_SUBTRACT_REF 8u
+/* Hashed keys (the section on compression with hash functions): inside each
+ * hash tile the records are grouped by a 54-bit hash of the 128-bit key (a
+ * 64-bit mix with the record's index in its low bits) instead of by the key
+ * itself, so the grouping reads no keys.  Two different keys of one tile
+ * with the same 54-bit hash would be merged; the run then still compares
+ * every merged record with its group's first key and reports the number of
+ * mismatches in pt2_result.n_hash_collisions (0: the hashed grouping was
+ * exact, so E2, the counts and the external set equal an ordinary run's).
+ * With about 450 keys per tile the expected number of such merges is about
+ * 450^2 / 2^55 per tile, 3e-3 for a 4.8e11-term solve. */
+#define PT2_FLAG_HASHED_KEYS 16u
 
 /* Test aids (pt2_opts.debug_flags).  They exercise paths that ordinary inputs
  * reach only rarely; neither changes a result.
@@ -198,7 +209,9 @@ typedef struct {
     uint32_t n_tiles;         /* hash tiles over all passes */
     uint32_t n_oversize;      /* tiles handled by the chunked path */
     uint32_t n_hash_collisions; /* comparisons inside a tile that met two different keys with
-                                   the same 32-bit sort hash (saturates at 2^32 - 1) */
+                                   the same 32-bit sort hash; with PT2_FLAG_HASHED_KEYS, records
+                                   merged into a group whose first key differs from theirs
+                                   (saturates at 2^32 - 1) */
     double seconds;           /* device time of the run (CUDA events) */
 } pt2_result;
 

@@ -152,7 +152,8 @@ int job_filt(const Job &j) { return (j.gp.sym ? kFiltSym : 0) | (j.gp.cutoff > 0
 uint32_t job_iflags(const Job &j)
 {
     return (j.gp.sym ? kInstSym : 0u) | ((j.o.debug_flags & PT2_DEBUG_NARROW_SORT_HASH) ? kInstNarrow : 0u) |
-           ((j.o.debug_flags & PT2_DEBUG_SHORT_COPY_WAIT) ? kInstShortWait : 0u);
+           ((j.o.debug_flags & PT2_DEBUG_SHORT_COPY_WAIT) ? kInstShortWait : 0u) |
+           ((j.o.flags & PT2_FLAG_HASHED_KEYS) ? kInstHashed : 0u);
 }
 
 // Terms per beta class among the terms of alpha class k of a job (one

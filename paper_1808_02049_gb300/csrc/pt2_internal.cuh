@@ -57,6 +57,7 @@ constexpr uint32_t kErrCount = 16u;          // emitted terms differ from the pl
 constexpr uint32_t kInstSym = 1u;        // spin-flip symmetric run
 constexpr uint32_t kInstNarrow = 2u;     // narrowed sort hash (test aid: most keys of a tile share hash and bucket)
 constexpr uint32_t kInstShortWait = 4u;  // bulk-copy waits give up almost at once (test aid: exercises the timeout)
+constexpr uint32_t kInstHashed = 8u;     // keys of a tile identified by a 54-bit hash (the hashing section)
 
 // One generated term: the excited determinant, its numerator H_ai c_i and
 // its denominator E0 - H_aa in units of 2^-48 Ha (from the parent's diagonal

@@ -1828,6 +1828,13 @@ struct GrpSmem {
     unsigned int nuniq, nlong;
 };
 
+// 64-bit hash of a key for the hashed-key grouping (the hashing section):
+// SplitMix64's finaliser on both words, combined by an odd multiplier.
+__device__ __forceinline__ uint64_t key_hash64(uint64_t a, uint64_t b)
+{
+    return fmix64((a * 0x9E3779B97F4A7C15ull) ^ fmix64(b));
+}
+
 // Distinct keys listed by the last grouping (its heads, then its long heads).
 __device__ __forceinline__ int group_keys(const GrpSmem &G) { return (int)(G.nuniq + G.nlong); }
 
@@ -1893,7 +1900,7 @@ struct R48 {
 // that makes most keys of a tile share their hash and bucket).  Returns how
 // often this thread met two different keys with the same hash.  Every thread
 // of the CTA must call it; it starts after and ends with a barrier.
-template <class R, class Run>
+template <class R, bool HK = false, class Run>
 __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t hmask, GrpSmem &G, uint32_t &err,
                                   Run &&run)
 {
@@ -1903,8 +1910,11 @@ __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t
         G.nuniq = 0;
         G.nlong = 0;
     }
-    // 1. hash and rank within the bucket
-    uint32_t hh[kGrpItems], rk[kGrpItems];
+    // 1. hash and rank within the bucket.  An entry is (hash << 32) | index,
+    // or with hashed keys (HK) the 64-bit key hash whose low 10 bits hold the
+    // index; either way its top 10 bits are the bucket.
+    uint64_t hh[kGrpItems];
+    uint32_t rk[kGrpItems];
 #pragma unroll
     for (int k = 0; k < kGrpItems; ++k) {
         const int i = tid + k * kGrpThreads;
@@ -1913,8 +1923,9 @@ __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t
         if (i < cnt) {
             uint64_t a, b;
             R::key(recs, i, a, b);
-            hh[k] = sort_hash(a, b) & hmask;
-            rk[k] = atomicAdd(&G.cnt[hh[k] >> kGrpBktShift], 1u);
+            if constexpr (HK) hh[k] = (key_hash64(a, b) & ~0x3FFull) | (uint64_t)i;
+            else hh[k] = ((uint64_t)(sort_hash(a, b) & hmask) << 32) | (uint64_t)i;
+            rk[k] = atomicAdd(&G.cnt[hh[k] >> 54], 1u);
         }
     }
     __syncthreads();
@@ -1939,7 +1950,7 @@ __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t
 #pragma unroll
     for (int k = 0; k < kGrpItems; ++k) {
         const int i = tid + k * kGrpThreads;
-        if (i < cnt) G.ent[G.cnt[hh[k] >> kGrpBktShift] + rk[k]] = ((uint64_t)hh[k] << 32) | (uint32_t)i;
+        if (i < cnt) G.ent[G.cnt[hh[k] >> 54] + rk[k]] = hh[k];
     }
     __syncthreads();
     // 2. one lane per record: does an earlier record of its bucket have its key?
@@ -1954,7 +1965,14 @@ __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t
             const uint32_t bk = h >> kGrpBktShift;
             const int bs = (int)G.cnt[bk];
             head = true;
-            if (bs < pos) {
+            if (HK) {
+                // with hashed keys an equal 54-bit hash stands for an equal key
+                for (int j = bs; j < pos; ++j)
+                    if (((G.ent[j] ^ e) >> 10) == 0) {
+                        head = false;
+                        break;
+                    }
+            } else if (bs < pos) {
                 uint64_t a, b;
                 R::key(recs, (int)(e & 0x3FFu), a, b);
                 for (int j = bs; j < pos; ++j) {
@@ -2003,11 +2021,16 @@ __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t
             R::key(recs, idx, a, b);
             for (int q = pos + 1; q < be; ++q) {
                 const uint64_t eq = G.ent[q];
-                if ((uint32_t)(eq >> 32) != h) continue;
+                if (HK ? ((eq ^ e) >> 10) != 0 : (uint32_t)(eq >> 32) != h) continue;
                 const int iq = (int)(eq & 0x3FFu);
                 uint64_t a2, b2;
                 R::key(recs, iq, a2, b2);
-                if (a2 != a || b2 != b) continue;
+                if (a2 != a || b2 != b) {
+                    // hashed keys: the records are merged all the same; the
+                    // count reports that the hash identified different keys
+                    if (!HK) continue;
+                    ++coll;
+                }
                 if (!multi) R::add(recs, idx, fl, fh, err);
                 multi = true;
                 R::add(recs, iq, fl, fh, err);
@@ -2033,11 +2056,15 @@ __device__ uint32_t group_records(const typename R::Rec *recs, int cnt, uint32_t
             const int q = base + lane;
             if (q < be) {
                 const uint64_t eq = G.ent[q];
-                if ((uint32_t)(eq >> 32) == h) {
+                if (HK ? ((eq ^ e) >> 10) == 0 : (uint32_t)(eq >> 32) == h) {
                     const int iq = (int)(eq & 0x3FFu);
                     uint64_t a2, b2;
                     R::key(recs, iq, a2, b2);
                     if (a2 == a && b2 == b) R::add(recs, iq, fl, fh, err);
+                    else if (HK) {
+                        R::add(recs, iq, fl, fh, err);
+                        ++coll;
+                    }
                 }
             }
         }
@@ -2182,11 +2209,11 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) tile_kernel(cons
             if (__syncthreads_or(!ok)) break;
             Rec32 *recs = M.recs;
             // the head record of each key takes the key's numerator ...
-            st.n_coll += group_records<R32>(recs, cnt, hmask, M.G, st.err,
-                                            [&](int head, bool exact, uint64_t sl, int64_t sh) {
-                                                recs[head].num =
-                                                    exact ? fx_to_double(sl, sh) : canon_num(recs[head].num, st.err);
-                                            });
+            auto run = [&](int head, bool exact, uint64_t sl, int64_t sh) {
+                recs[head].num = exact ? fx_to_double(sl, sh) : canon_num(recs[head].num, st.err);
+            };
+            if (fl & kInstHashed) st.n_coll += group_records<R32, true>(recs, cnt, hmask, M.G, st.err, run);
+            else st.n_coll += group_records<R32, false>(recs, cnt, hmask, M.G, st.err, run);
             // ... and every lane finishes one key at a time
             const int nk = group_keys(M.G);
             for (int u = threadIdx.x; u < nk; u += kTileThreads) {
@@ -2236,9 +2263,10 @@ struct BigSmem {
 size_t big_smem_bytes() { return sizeof(BigSmem); }
 
 // One chunk of records -> exact partials appended to dst (out_count of them).
-__device__ uint32_t chunk_to_partials(Rec32 *recs, int m, BigSmem &M, Rec48 *dst, uint32_t hmask, uint32_t &err)
+__device__ uint32_t chunk_to_partials(Rec32 *recs, int m, BigSmem &M, Rec48 *dst, uint32_t hmask, bool hashed,
+                                      uint32_t &err)
 {
-    return group_records<R32>(recs, m, hmask, M.G, err, [&](int head, bool exact, uint64_t sl, int64_t sh) {
+    auto put = [&](int head, bool exact, uint64_t sl, int64_t sh) {
         const Rec32 &r = recs[head];
         Rec48 o;
         o.a = r.a;
@@ -2253,7 +2281,9 @@ __device__ uint32_t chunk_to_partials(Rec32 *recs, int m, BigSmem &M, Rec48 *dst
         o.den = r.den;
         o.pad = 0;
         dst[atomicAdd(&M.out_count, 1u)] = o;
-    });
+    };
+    return hashed ? group_records<R32, true>(recs, m, hmask, M.G, err, put)
+                  : group_records<R32, false>(recs, m, hmask, M.G, err, put);
 }
 
 // Persistent over the oversize tiles of all instances, numbered in one index
@@ -2336,7 +2366,7 @@ __global__ void __launch_bounds__(kBigThreads, kTileCtasPerSm) big_tile_kernel(c
                 stop = true;
                 break;
             }
-            st.n_coll += chunk_to_partials(M.u.r32, m, M, bufA + u, hmask, st.err);
+            st.n_coll += chunk_to_partials(M.u.r32, m, M, bufA + u, hmask, (fl & kInstHashed) != 0, st.err);
             u += M.out_count;
             __syncthreads();
         }
@@ -2351,15 +2381,16 @@ __global__ void __launch_bounds__(kBigThreads, kTileCtasPerSm) big_tile_kernel(c
             for (int i = threadIdx.x; i < m; i += nt) M.u.r48[i] = src[i];
             __syncthreads();
             Rec48 *r48 = M.u.r48;
-            st.n_coll += group_records<R48>(r48, m, hmask, M.G, st.err,
-                                            [&](int head, bool exact, uint64_t sl, int64_t sh) {
-                                                Rec48 &r = r48[head];
-                                                if (!exact) {
-                                                    sl = r.fx_lo;
-                                                    sh = r.fx_hi;
-                                                }
-                                                r.pad = (uint64_t)__double_as_longlong(fx_to_double(sl, sh));
-                                            });
+            auto fin48 = [&](int head, bool exact, uint64_t sl, int64_t sh) {
+                Rec48 &r = r48[head];
+                if (!exact) {
+                    sl = r.fx_lo;
+                    sh = r.fx_hi;
+                }
+                r.pad = (uint64_t)__double_as_longlong(fx_to_double(sl, sh));
+            };
+            if (fl & kInstHashed) st.n_coll += group_records<R48, true>(r48, m, hmask, M.G, st.err, fin48);
+            else st.n_coll += group_records<R48, false>(r48, m, hmask, M.G, st.err, fin48);
             const int nk = group_keys(M.G);
             for (int q = threadIdx.x; q < nk; q += nt) {
                 const Rec48 &r = r48[M.G.uniq[q]];

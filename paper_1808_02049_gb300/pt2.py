@@ -28,6 +28,7 @@ PT2_FLAG_PROFILE = 1
 PT2_FLAG_AUTOTUNE = 2
 PT2_FLAG_SPIN_SYMMETRIC = 4
 PT2_FLAG_SUBTRACT_REF = 8
+PT2_FLAG_HASHED_KEYS = 16
 PT2_DEBUG_NARROW_SORT_HASH = 1
 PT2_DEBUG_SHORT_COPY_WAIT = 2
 
@@ -129,14 +130,14 @@ def _check(ctx, rc):
 
 def make_opts(constraint=(1, 0), pass_budget_bytes=0, tile_target=0, profile=False, autotune=False,
               spin_symmetric=False, cutoff=0.0, subtract_ref=False, narrow_sort_hash=False,
-              short_copy_wait=False, class_slice=(0, 1), top_alpha=0) -> pt2_opts:
+              short_copy_wait=False, class_slice=(0, 1), top_alpha=0, hashed_keys=False) -> pt2_opts:
     o = pt2_opts()
     o.constraint_mod, o.constraint_rem = int(constraint[0]), int(constraint[1])
     o.pass_budget_bytes = int(pass_budget_bytes)
     o.tile_target = int(tile_target)
     o.flags = ((PT2_FLAG_PROFILE if profile else 0) | (PT2_FLAG_AUTOTUNE if autotune else 0) |
                (PT2_FLAG_SPIN_SYMMETRIC if spin_symmetric else 0) |
-               (PT2_FLAG_SUBTRACT_REF if subtract_ref else 0))
+               (PT2_FLAG_SUBTRACT_REF if subtract_ref else 0) | (PT2_FLAG_HASHED_KEYS if hashed_keys else 0))
     o.numerator_cutoff = float(cutoff)
     o.debug_flags = ((PT2_DEBUG_NARROW_SORT_HASH if narrow_sort_hash else 0) |
                      (PT2_DEBUG_SHORT_COPY_WAIT if short_copy_wait else 0))

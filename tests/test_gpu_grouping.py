@@ -173,3 +173,39 @@ def test_term_arithmetic_rejects_out_of_range_denominators(ctx):
         with pytest.raises(pt2.Pt2Error) as e:
             ctx.eval_terms(np.array([0.5]), np.array([d]))
         assert e.value.code == pt2.PT2_ERR_INVALID
+
+
+@pytest.mark.parametrize("tile_target", [16, 0, 1024])
+def test_hashed_keys_equal_the_exact_grouping(ctx, small, tile_target):
+    # the hashing section's compression: keys of a tile identified by a
+    # 54-bit hash; with no merge of different keys (reported as 0) the run is
+    # the ordinary one bit for bit, and the oracle's
+    got = ctx.run(small["rid"], tile_target=tile_target, hashed_keys=True)
+    assert got["n_hash_collisions"] == 0
+    assert_same_result(got, small["ref"])
+    exact = ctx.run(small["rid"], tile_target=tile_target)
+    assert got["e2"] == exact["e2"]
+    assert (got["digest_sum"], got["digest_xor"]) == (exact["digest_sum"], exact["digest_xor"])
+    k, num, haa = ctx.dump_external(small["rid"], small["ref"]["n_external"] + 10, tile_target=tile_target,
+                                    hashed_keys=True)
+    ok, onum, ohaa, _ = small["dump"]
+    k, num, haa = sort_keys(k, num, haa)
+    assert np.array_equal(k, ok)
+    np.testing.assert_allclose(num, onum, rtol=0, atol=1e-13)
+
+
+def test_hashed_keys_on_the_large_system(ctx):
+    s, r = inputs.make_workload("large", n_det=2000)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    sid = ctx.load_system(s.h, s.eri)
+    rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    try:
+        a = ctx.run(rid)
+        b = ctx.run(rid, hashed_keys=True)
+    finally:
+        ctx.unload(rid)
+        ctx.unload(sid)
+    assert b["n_hash_collisions"] == 0
+    assert a["e2"] == b["e2"]
+    for f in ("n_terms", "n_unique", "n_in_ref", "n_external", "digest_sum", "digest_xor", "n_oversize"):
+        assert a[f] == b[f], f

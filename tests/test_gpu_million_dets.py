@@ -97,3 +97,13 @@ def test_slices_of_the_full_size_solve(million):
     assert abs(sum(p["e2"] for p in parts) - full["e2"]) <= 1e-14 * abs(full["e2"])
     # no slice is far from its share (the hash classes spread the terms)
     assert max(p["n_terms"] for p in parts) < 3 * full["n_terms"] / 20
+
+
+def test_hashed_keys_on_a_slice_of_the_full_size_solve(million):
+    c, rid = million["c"], million["rid"]
+    a = c.run(rid, class_slice=(2, 20))
+    b = c.run(rid, class_slice=(2, 20), hashed_keys=True)
+    assert b["n_hash_collisions"] == 0
+    assert a["e2"] == b["e2"]
+    for f in ("n_terms", "n_unique", "n_in_ref", "n_external", "digest_sum", "digest_xor"):
+        assert a[f] == b[f], f
