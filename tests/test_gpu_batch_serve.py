@@ -3,8 +3,14 @@ continuous batching of submitted requests.
 
 Energies and set statistics are accumulated exactly, so an instance's result
 must be bit-identical alone (pt2_run), inside a batch and inside a served
-mix; the smallest instances are also checked against the oracle.
+mix.  Every instance is also checked against the oracle, batched and served,
+on one constraint class (alpha % 11 == 5: the oracle drops the other classes'
+terms before computing their matrix elements, so it stays quick); the two
+smallest instances in full.
 """
+
+import concurrent.futures as cf
+import os
 
 import numpy as np
 import pytest
@@ -61,6 +67,46 @@ def test_batch_matches_single_runs_and_oracle(fleet):
         assert x["alone"]["n_external"] == ref["n_external"]
         assert (x["alone"]["digest_sum"], x["alone"]["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
         assert abs(x["alone"]["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
+
+
+CLASS = (11, 5)
+
+
+@pytest.fixture(scope="module")
+def oracle_class(fleet):
+    # the oracle on one constraint class of every instance, on the host cores
+    _, refs = fleet
+    oracle.build()
+    with cf.ThreadPoolExecutor(max_workers=min(len(refs), os.cpu_count() or 1)) as ex:
+        return list(ex.map(lambda x: oracle.pt2(x["s"].h, x["s"].eri, x["r"].keys, x["r"].coef, x["e0"],
+                                                constraint=CLASS), refs))
+
+
+def same_as_oracle(got, ref):
+    assert got["n_terms"] == ref["n_terms"]
+    assert got["n_external"] == ref["n_external"]
+    assert got["n_in_ref"] == ref["n_in_ref"]
+    assert (got["digest_sum"], got["digest_xor"]) == (ref["digest_sum"], ref["digest_xor"])
+    assert abs(got["e2"] - ref["e2"]) <= max(1e-10, 1e-10 * abs(ref["e2"]))
+
+
+def test_every_batched_instance_matches_oracle_on_a_class(fleet, oracle_class):
+    c, refs = fleet
+    bid = c.batch_create([x["rid"] for x in refs], constraint=CLASS)
+    try:
+        res = c.batch_run(bid, len(refs))
+    finally:
+        c.batch_destroy(bid)
+    for got, ref in zip(res, oracle_class):
+        assert ref["n_terms"] > 0
+        same_as_oracle(got, ref)
+
+
+def test_every_served_instance_matches_oracle_on_a_class(fleet, oracle_class):
+    c, refs = fleet
+    tickets = [c.submit(x["rid"], constraint=CLASS) for x in refs]
+    for t, ref in zip(tickets, oracle_class):
+        same_as_oracle(c.wait(t, timeout_s=600), ref)
 
 
 def test_profiled_batch_matches_graph_replay(fleet):
