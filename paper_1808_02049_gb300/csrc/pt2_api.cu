@@ -78,7 +78,7 @@ int ensure(pt2_ctx *c, DevBuf &b, size_t bytes, const char *what)
 
 void free_system(pt2_ctx *c, SystemRes &s)
 {
-    DevBuf *b[] = {&s.h, &s.eri, &s.J, &s.WS, &s.Jx, &s.WSx, &s.hdx};
+    DevBuf *b[] = {&s.h, &s.eri, &s.J, &s.WS, &s.Jx, &s.WSx, &s.hdx, &s.dpair};
     for (DevBuf *x : b) dev_free(c, *x);
 }
 
@@ -123,6 +123,7 @@ SysDev sys_dev(const SystemRes &s)
     d.Jx = (const int64_t *)s.Jx.ptr;
     d.WSx = (const int64_t *)s.WSx.ptr;
     d.hdx = (const int64_t *)s.hdx.ptr;
+    d.dpair = (const double *)s.dpair.ptr;
     return d;
 }
 
@@ -323,13 +324,23 @@ int pt2_load_system(pt2_ctx *c, int n_orb, const double *h, const double *eri, u
         return fail(c, PT2_ERR_UNSUPPORTED,
                     "orbital energy bound %.1f Ha exceeds the %.0f Ha range of the fixed-point diagonal", gbound,
                     kDenRange);
+    // same-spin double elements (a1 r1|a2 r2) - (a1 r2|a2 r1) by colex pairs
+    // r1 < r2, a1 < a2, from the canonical integrals: the same two doubles and
+    // the same subtraction as a direct evaluation, so the same value
+    const size_t np = n * (n - 1) / 2;
+    std::vector<double> dp(np * np);
+    for (size_t r2 = 1, P = 0; r2 < n; ++r2)
+        for (size_t r1 = 0; r1 < r2; ++r1, ++P)
+            for (size_t a2 = 1, Q = 0; a2 < n; ++a2)
+                for (size_t a1 = 0; a1 < a2; ++a1, ++Q)
+                    dp[P * np + Q] = eri[((r2 * n + a2) * n + r1) * n + a1] - eri[((r1 * n + a2) * n + r2) * n + a1];
     auto s = std::make_unique<SystemRes>();
     s->n = n_orb;
     int rc;
     if ((rc = dev_alloc(c, s->h, n2 * 8, "h")) || (rc = dev_alloc(c, s->eri, n4 * 8, "eri")) ||
         (rc = dev_alloc(c, s->J, n2 * 8, "J")) || (rc = dev_alloc(c, s->WS, n2 * 8, "WS")) ||
         (rc = dev_alloc(c, s->Jx, n2 * 8, "Jx")) || (rc = dev_alloc(c, s->WSx, n2 * 8, "WSx")) ||
-        (rc = dev_alloc(c, s->hdx, n * 8, "hdx"))) {
+        (rc = dev_alloc(c, s->hdx, n * 8, "hdx")) || (rc = dev_alloc(c, s->dpair, np * np * 8, "pair integrals"))) {
         free_system(c, *s);
         return rc;
     }
@@ -340,6 +351,7 @@ int pt2_load_system(pt2_ctx *c, int n_orb, const double *h, const double *eri, u
     CK(cudaMemcpy(s->Jx.ptr, Jx.data(), n2 * 8, cudaMemcpyHostToDevice), "copy Jx");
     CK(cudaMemcpy(s->WSx.ptr, WSx.data(), n2 * 8, cudaMemcpyHostToDevice), "copy WSx");
     CK(cudaMemcpy(s->hdx.ptr, hdx.data(), n * 8, cudaMemcpyHostToDevice), "copy hdx");
+    CK(cudaMemcpy(s->dpair.ptr, dp.data(), np * np * 8, cudaMemcpyHostToDevice), "copy pair integrals");
     uint32_t id = c->next_id++;
     c->systems[id] = std::move(s);
     *system_id = id;

@@ -198,8 +198,8 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
     for (size_t i = 0; i < n; ++i) {
         filt |= job_filt(*jobs[i]);
         GenParams g = jobs[i]->gp;
-        g.class_lo = 0;
-        g.class_hi = kNumClasses;
+        g.class_lo = jobs[i]->cls_lo;  // the job's class slice only
+        g.class_hi = jobs[i]->cls_hi;
         g.det_begin = 0;
         g.class_counts = reinterpret_cast<unsigned long long *>(c->class_counts.ptr) + i * kNumClasses;
         gen_layout(g, kModeClassCount);
@@ -250,11 +250,15 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
                 }
                 std::vector<unsigned long long> bh;
                 if ((rc = beta_counts(c, j, (uint32_t)k, bh))) return rc;
+                // the beta counts are of every term: in a run with a numerator
+                // cutoff they bound what the beta-class passes keep
+                const bool cutting = j.gp.cutoff > 0.0;
                 unsigned long long sum = 0;
                 Pass bp;
                 bp.c_lo = k;
                 bp.c_hi = k + 1;
                 bp.b_lo = 0;
+                bp.at_most = cutting;
                 for (int b = 0; b < kNumClasses; ++b) {
                     sum += bh[b];
                     if (bh[b] > cap)
@@ -267,12 +271,13 @@ int plan_jobs(pt2_ctx *c, const std::vector<Job *> &jobs, bool split_large, uint
                         j.passes.push_back(bp);
                         bp.b_lo = b;
                         bp.records = 0;
+                        bp.at_most = cutting;
                     }
                     bp.records += bh[b];
                 }
                 bp.b_hi = kNumClasses;
                 if (bp.records > 0) j.passes.push_back(bp);
-                if (sum != cl[k])
+                if (cutting ? sum < cl[k] : sum != cl[k])
                     return fail(c, PT2_ERR_CUDA, "beta counts of alpha class %d sum to %llu, not %llu", k, sum,
                                 (unsigned long long)cl[k]);
                 cur = Pass();
@@ -391,7 +396,7 @@ void fill_step(pt2_ctx *c, const StepPlan &sp, StepDev &h)
         h.tile_base[i] = tb;
         h.e0[i] = j.r->e0;
         h.iflags[i] = job_iflags(j);
-        h.expected[i] = P.records | (j.gp.cutoff > 0.0 ? kExpectAtMost : 0ull);
+        h.expected[i] = P.records | (P.at_most ? kExpectAtMost : 0ull);
         h.acc[i] = j.acc;
         h.n_big[i] = 0;
         cta += j.r->n_det;

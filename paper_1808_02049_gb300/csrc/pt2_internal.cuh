@@ -86,6 +86,10 @@ struct SysDev {
     const int64_t *hdx;  // n: h_pp * 2^48
     const double *J;     // n*n (direct diagonal kernel)
     const double *WS;    // n*n
+    // same-spin double elements by colex pair: dpair[P(r1, r2) * np + P(a1, a2)] =
+    // (a1 r1|a2 r2) - (a1 r2|a2 r1) for r1 < r2, a1 < a2, P(i, j) = j (j - 1) / 2 + i,
+    // np = n (n - 1) / 2 (one load per element instead of two)
+    const double *dpair;
 };
 
 struct HashTables {
@@ -121,14 +125,14 @@ struct GenParams {
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance
     // outputs
-    unsigned long long *class_counts;  // kNumClasses (this instance's slice)
+    unsigned long long *class_counts;  // kNumClasses per instance; the class-count mode fills [class_lo, class_hi)
     uint32_t *tile_counts;             // n_tiles
     unsigned int *cursor;              // n_tiles: next free slot of each tile (a pass holds < 2^32 records)
     Rec32 *recs;
     unsigned long long rec_cap;        // records the launch may write (emit and det-terms modes)
     uint32_t *err;
     // dynamic shared memory layout (byte offsets)
-    int smem_sa, smem_sb, smem_pairs, smem_vec, smem_hist, smem_bytes;
+    int smem_sa, smem_sb, smem_pairs, smem_vec, smem_hist, smem_vbk, smem_bytes;
     int n_sa, n_sb;                    // singles per determinant: na*(n-na), nb*(n-nb)
 };
 

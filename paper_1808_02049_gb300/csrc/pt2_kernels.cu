@@ -389,6 +389,7 @@ struct GenFixed {
     double c;
     int64_t d0;
     int n_sa_pass, a_in_pass, n_sb_pass, b_in_pass;
+    uint32_t chunk_a[32], chunk_b[32];  // pass flags of singles 32c .. 32c + 31 (n_sa, n_sb <= 1024)
     uint32_t wsum[kGenThreads / 32];
     // the pass's alpha classes as aligned blocks of bucket groups (see above)
     uint16_t blk_g[2 * kVbkBitsMax];
@@ -421,12 +422,12 @@ __device__ __forceinline__ double single_value(const double *__restrict__ ht, co
     return v;
 }
 
-// Same-spin double r1 r2 -> a1 a2: (a1 r1|a2 r2) - (a1 r2|a2 r1), read as
-// (r2 a2|r1 a1) - (r1 a2|r2 a1) so that a1 varies fastest in memory.
-__device__ __forceinline__ double same_double_value(const double *__restrict__ eri, int N, int r1, int r2, int a1,
+// Same-spin double r1 r2 -> a1 a2 (r1 < r2, a1 < a2): (a1 r1|a2 r2) - (a1 r2|a2 r1),
+// one load from the table of these elements by colex pair (SysDev::dpair).
+__device__ __forceinline__ double same_double_value(const double *__restrict__ dpair, int np, int r1, int r2, int a1,
                                                     int a2)
 {
-    return __ldg(eri + (((size_t)r2 * N + a2) * N + r1) * N + a1) - __ldg(eri + (((size_t)r1 * N + a2) * N + r2) * N + a1);
+    return __ldg(dpair + (size_t)(r2 * (r2 - 1) / 2 + r1) * np + (a2 * (a2 - 1) / 2 + a1));
 }
 
 // Kept by the numerator cutoff: |c v| >= cut (the sign of the element does not matter).
@@ -538,6 +539,70 @@ __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, i
     }
 }
 
+// Bucket table of a determinant's virtual alpha pairs (entries vb_off[b] ..
+// vb_off[b + 1] of vb_list are the indices, in the pair list, of the pairs
+// whose class hash has top bits b), and the class range [class_lo, class_hi)
+// as aligned blocks of bucket groups (F.blk_g, F.blk_k, F.n_blk).  Called by
+// the whole CTA.
+__device__ __forceinline__ void build_vbk(GenFixed &F, const uint16_t *pairs, int n_vir_pairs_a, uint32_t class_lo,
+                                          uint32_t class_hi, uint32_t *vb_cnt, uint16_t *vb_off, uint16_t *vb_list)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nw = kGenThreads / 32;
+    if (tid == 0) {
+        constexpr int gs = kClassBits - kVbkBits;
+        uint32_t g = class_lo >> gs;
+        const uint32_t g1 = ((class_hi - 1) >> gs) + 1;
+        int nb = 0;
+        while (g < g1) {
+            int k = kVbkBits;
+            while (k > 0 && ((g & ((1u << k) - 1u)) != 0 || g + (1u << k) > g1)) --k;
+            F.blk_g[nb] = (uint16_t)g;
+            F.blk_k[nb] = (uint8_t)k;
+            ++nb;
+            g += 1u << k;
+        }
+        F.n_blk = nb;
+    }
+    for (int b = tid; b < kVbkBuckets; b += kGenThreads) vb_cnt[b] = 0;
+    __syncthreads();
+    for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
+        const int pv = pairs[t];
+        atomicAdd(&vb_cnt[vb_bucket(F.zc[F.virA[pv & 0xFF]] ^ F.zc[F.virA[pv >> 8]])], 1u);
+    }
+    __syncthreads();
+    {
+        const uint4 c4 = reinterpret_cast<const uint4 *>(vb_cnt)[tid];
+        const uint32_t sum = c4.x + c4.y + c4.z + c4.w;
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) F.wsum[warp] = incl;
+        __syncthreads();
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int k = 0; k < nw; ++k) run += k < warp ? F.wsum[k] : 0u;
+        const uint32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            vb_off[4 * tid + k] = (uint16_t)run;
+            vb_cnt[4 * tid + k] = run;  // scatter cursor
+            run += c[k];
+        }
+        if (tid == kGenThreads - 1) vb_off[kVbkBuckets] = (uint16_t)run;
+    }
+    __syncthreads();
+    for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
+        const int pv = pairs[t];
+        const uint32_t b = vb_bucket(F.zc[F.virA[pv & 0xFF]] ^ F.zc[F.virA[pv >> 8]]);
+        vb_list[atomicAdd(&vb_cnt[b], 1u)] = (uint16_t)t;
+    }
+    __syncthreads();
+}
+
 // All singles and doubles of determinant `det` of one instance (the body of
 // both generator kernels).  FILT (kFiltSym | kFiltCut): the instance may be a
 // spin-flip symmetric run, or have a numerator cutoff (the checks cost
@@ -579,6 +644,8 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     const int N = p.sys.n;
     const int na = p.na, nb = p.nb, nva = N - na, nvb = N - nb;
     const double *__restrict__ eri = p.sys.eri;
+    const double *__restrict__ dpair = p.sys.dpair;
+    const int NP = N * (N - 1) / 2;
     const int64_t *__restrict__ Jx = p.sys.Jx;
     const int64_t *__restrict__ WSx = p.sys.WSx;
     const double *__restrict__ ht = p.sys.h;
@@ -591,8 +658,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         F.ztb[i] = p.hash->ztb[i];
     }
     for (int t = tid; t < N * (N - 1) / 2; t += kGenThreads) pairs[t] = p.hash->pairs[t];
+    // the class-count mode histograms the classes [class_lo, class_hi) only
+    const uint32_t n_hist = MODE == kModeClassCount ? p.class_hi - p.class_lo : (uint32_t)kNumClasses;
     if constexpr (kCount)
-        for (int i = tid; i < kNumClasses; i += kGenThreads) hist[i] = 0;
+        for (int i = tid; i < (int)n_hist; i += kGenThreads) hist[i] = 0;
     {
         // occupied and virtual lists, one orbital per thread: its rank among
         // the occupied (virtual) orbitals below it is a population count
@@ -645,43 +714,56 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     const double c = F.c;
     const int64_t d0 = F.d0;
 
-    // singles lists; delta = H_aa - H_ii of the single, exact
-    for (int s = tid; s < p.n_sa; s += kGenThreads) {
-        int i = s / nva, j = s - (s / nva) * nva;
-        int r = F.occA[i], a = F.virA[j];
-        uint32_t sg = __popcll(A & between_mask(r, a)) & 1;
-        uint64_t a2 = A ^ (1ull << r) ^ (1ull << a);
-        uint64_t zc = F.ZcA ^ F.zc[r] ^ F.zc[a];
-        uint32_t inp;
-        if constexpr (MODE == kModeClassCount) {
-            inp = cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
-        } else if constexpr (MODE == kModeBetaCount) {
-            inp = class_of(zc) == p.heavy_class && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
-        } else {
-            uint32_t cl = class_of(zc);
-            inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
+    // singles lists; delta = H_aa - H_ii of the single, exact.  Single s is
+    // lane s % 32 of its warp, so the warp's ballot of the pass flags is the
+    // flag word of the 32 singles from 32 (s / 32) (compacted below)
+    const uint32_t mva = nva ? (uint32_t)((0x100000000ull + nva - 1) / nva) : 0u;  // s / nva = umulhi(s, mva)
+    const uint32_t mvb = nvb ? (uint32_t)((0x100000000ull + nvb - 1) / nvb) : 0u;  // exact while s * nv < 2^32
+    for (int s0 = 0; s0 < p.n_sa; s0 += kGenThreads) {
+        const int s = s0 + tid;
+        uint32_t inp = 0;
+        if (s < p.n_sa) {
+            const int i = (int)__umulhi((uint32_t)s, mva), j = s - i * nva;
+            const int r = F.occA[i], a = F.virA[j];
+            const uint32_t sg = __popcll(A & between_mask(r, a)) & 1;
+            const uint64_t a2 = A ^ (1ull << r) ^ (1ull << a);
+            const uint64_t zc = F.ZcA ^ F.zc[r] ^ F.zc[a];
+            if constexpr (MODE == kModeBetaCount) {
+                inp = class_of(zc) == p.heavy_class && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
+            } else {
+                const uint32_t cl = class_of(zc);
+                inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
+            }
+            if constexpr (kVal) sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
+            sa_zt[s] = kCount ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
+            sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17);
         }
-        if constexpr (kVal) sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
-        sa_zt[s] = kCount ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
-        sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17);
+        const uint32_t m = __ballot_sync(0xffffffffu, inp != 0);
+        if (lane == 0) F.chunk_a[(s0 >> 5) + warp] = m;
     }
-    for (int s = tid; s < p.n_sb; s += kGenThreads) {
-        int i = s / nvb, j = s - (s / nvb) * nvb;
-        int r = F.occB[i], a = F.virB[j];
-        uint32_t sg = __popcll(B & between_mask(r, a)) & 1;
-        if constexpr (kVal) sb_delta[s] = F.gB[a] - F.gB[r] - WSx[r * N + a];
-        const uint64_t zcb = F.ZcbB ^ F.zcb[r] ^ F.zcb[a];  // beta class hash of the excited beta string
-        // the beta-count mode histograms beta classes, so it keeps that hash here
-        sb_zt[s] = MODE == kModeBetaCount ? zcb : (F.ZtbB ^ F.ztb[r] ^ F.ztb[a]);
-        const uint32_t bc = bclass_of(zcb);
-        const uint32_t binp = bfull || (bc >= blo && bc < bhi);
-        sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (binp << 17);
+    for (int s0 = 0; s0 < p.n_sb; s0 += kGenThreads) {
+        const int s = s0 + tid;
+        uint32_t binp = 0;
+        if (s < p.n_sb) {
+            const int i = (int)__umulhi((uint32_t)s, mvb), j = s - i * nvb;
+            const int r = F.occB[i], a = F.virB[j];
+            const uint32_t sg = __popcll(B & between_mask(r, a)) & 1;
+            if constexpr (kVal) sb_delta[s] = F.gB[a] - F.gB[r] - WSx[r * N + a];
+            const uint64_t zcb = F.ZcbB ^ F.zcb[r] ^ F.zcb[a];  // beta class hash of the excited beta string
+            // the beta-count mode histograms beta classes, so it keeps that hash here
+            sb_zt[s] = MODE == kModeBetaCount ? zcb : (F.ZtbB ^ F.ztb[r] ^ F.ztb[a]);
+            const uint32_t bc = bclass_of(zcb);
+            binp = bfull || (bc >= blo && bc < bhi);
+            sb_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (binp << 17);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, binp != 0);
+        if (lane == 0) F.chunk_b[(s0 >> 5) + warp] = m;
     }
     if (tid == 0) {
         bool ok = cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, A);
         if constexpr (MODE == kModeBetaCount) {
             ok = ok && class_of(F.ZcA) == p.heavy_class;
-        } else if constexpr (MODE != kModeClassCount) {
+        } else {
             uint32_t cl = class_of(F.ZcA);
             ok = ok && cl >= p.class_lo && cl < p.class_hi;
         }
@@ -690,28 +772,35 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         F.b_in_pass = bfull || (bc >= blo && bc < bhi);
     }
     __syncthreads();
-    // compact the alpha singles of the pass (warp 0, ballot + popc)
-    if (warp == 0) {
-        int base = 0;
-        for (int s0 = 0; s0 < p.n_sa; s0 += 32) {
-            int s = s0 + lane;
-            bool f = s < p.n_sa && ((sa_info[s] >> 17) & 1u);
-            uint32_t m = __ballot_sync(0xffffffffu, f);
-            if (f) sa_pass[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)s;
-            base += __popc(m);
+    // compact the alpha singles of the pass, and the beta singles whose beta
+    // class belongs to it, in ascending order: every warp scans the chunk
+    // counts (one chunk per lane) and writes the singles of its own chunks
+    {
+        const int nca = (p.n_sa + 31) >> 5, ncb = bfull ? 0 : (p.n_sb + 31) >> 5;
+        const uint32_t ma = lane < nca ? F.chunk_a[lane] : 0u, mb = lane < ncb ? F.chunk_b[lane] : 0u;
+        uint32_t ia = __popc(ma), ib = __popc(mb);  // inclusive prefix counts over the chunks
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t va = __shfl_up_sync(0xffffffffu, ia, off), vb = __shfl_up_sync(0xffffffffu, ib, off);
+            if (lane >= off) {
+                ia += va;
+                ib += vb;
+            }
         }
-        if (lane == 0) F.n_sa_pass = base;
-    } else if (warp == 1 && !bfull) {
-        // and the beta singles whose beta class belongs to the pass
-        int base = 0;
-        for (int s0 = 0; s0 < p.n_sb; s0 += 32) {
-            int s = s0 + lane;
-            bool f = s < p.n_sb && ((sb_info[s] >> 17) & 1u);
-            uint32_t m = __ballot_sync(0xffffffffu, f);
-            if (f) sb_pass[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)s;
-            base += __popc(m);
+        const uint32_t lt = (1u << lane) - 1u;
+        for (int ch = warp; ch < nca; ch += nw) {
+            const uint32_t m = __shfl_sync(0xffffffffu, ma, ch), base = __shfl_sync(0xffffffffu, ia, ch) - __popc(m);
+            if ((m >> lane) & 1u) sa_pass[base + __popc(m & lt)] = (uint16_t)(ch * 32 + lane);
         }
-        if (lane == 0) F.n_sb_pass = base;
+        for (int ch = warp; ch < ncb; ch += nw) {
+            const uint32_t m = __shfl_sync(0xffffffffu, mb, ch), base = __shfl_sync(0xffffffffu, ib, ch) - __popc(m);
+            if ((m >> lane) & 1u) sb_pass[base + __popc(m & lt)] = (uint16_t)(ch * 32 + lane);
+        }
+        const uint32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+        if (tid == 0) {
+            F.n_sa_pass = (int)ta;
+            if (!bfull) F.n_sb_pass = (int)tb;
+        }
     }
     __syncthreads();
     const int n_sa_pass = F.n_sa_pass;
@@ -723,15 +812,60 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
     if constexpr (MODE == kModeClassCount) {
         // work list (the paper's first pass over the wavefunction): terms per
-        // class.  A run with a numerator cutoff plans from these counts of all
-        // terms, an upper bound of what it keeps (the counting modes never
-        // evaluate matrix elements)
-        if (!sym) {
+        // class of [class_lo, class_hi).  A run with a numerator cutoff counts
+        // the contributions it keeps: it evaluates every matrix element with
+        // the functions the emission uses, so both take the same decisions
+        const uint32_t lo = p.class_lo;
+        if (cutting) {
+            // an alpha single (beta string B) and its alpha-beta doubles, one
+            // alpha single per warp
+            for (int k = warp; k < n_sa_pass; k += nw) {
+                const int s = sa_pass[k];
+                const uint32_t ia = sa_info[s];
+                const uint64_t a2 = single_word(A, ia);
+                const int rA = ia & 0xFF, aA = (ia >> 8) & 0xFF;
+                uint32_t cnt = 0;
+                for (int sb = lane; sb < p.n_sb; sb += 32) {
+                    const uint32_t bi = sb_info[sb];
+                    if (sym && single_word(B, bi) > a2) continue;
+                    cnt += above_cut(c, __ldg(eri + (((size_t)rA * N + aA) * N + (bi & 0xFF)) * N + ((bi >> 8) & 0xFF)),
+                                     cut);
+                }
+                cnt = __reduce_add_sync(0xffffffffu, cnt);
+                if (lane == 0) {
+                    if ((!sym || a2 >= B) && above_cut(c, single_value(ht, eri, N, F.occA, na, F.occB, nb, rA, aA), cut))
+                        ++cnt;
+                    if (cnt) atomicAdd(&hist[class_of(sa_zt[s]) - lo], cnt);
+                }
+            }
+            if (a_in) {  // beta singles and beta-beta doubles keep alpha string A
+                uint32_t cnt = 0;
+                for (int sb = tid; sb < p.n_sb; sb += kGenThreads) {
+                    const uint32_t bi = sb_info[sb];
+                    if (sym && single_word(B, bi) > A) continue;
+                    cnt += above_cut(c, single_value(ht, eri, N, F.occB, nb, F.occA, na, bi & 0xFF, (bi >> 8) & 0xFF),
+                                     cut);
+                }
+                for (int pi = warp; pi < n_occ_pairs_b; pi += nw) {
+                    const int pr = pairs[pi];
+                    const int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
+                    const uint64_t b12 = B ^ (1ull << r1) ^ (1ull << r2);
+                    for (int t = lane; t < n_vir_pairs_b; t += 32) {
+                        const int pv = pairs[t];
+                        const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
+                        if (sym && (b12 ^ (1ull << a1) ^ (1ull << a2)) > A) continue;
+                        cnt += above_cut(c, same_double_value(dpair, NP, r1, r2, a1, a2), cut);
+                    }
+                }
+                cnt = __reduce_add_sync(0xffffffffu, cnt);
+                if (lane == 0 && cnt) atomicAdd(&hist[class_of(F.ZcA) - lo], cnt);
+            }
+        } else if (!sym) {
             if (tid == 0 && a_in)
-                atomicAdd(&hist[class_of(F.ZcA)], (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
+                atomicAdd(&hist[class_of(F.ZcA) - lo], (uint32_t)(p.n_sb + n_occ_pairs_b * n_vir_pairs_b));
             for (int k = tid; k < n_sa_pass; k += kGenThreads) {
                 int s = sa_pass[k];
-                atomicAdd(&hist[class_of(sa_zt[s])], (uint32_t)(1 + p.n_sb));
+                atomicAdd(&hist[class_of(sa_zt[s]) - lo], (uint32_t)(1 + p.n_sb));
             }
         } else {
             // kept terms only (the drop rule of a symmetric run): an alpha
@@ -743,7 +877,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 uint32_t cnt = 0;
                 for (int sb = lane; sb < p.n_sb; sb += 32) cnt += single_word(B, sb_info[sb]) <= a2;
                 cnt = __reduce_add_sync(0xffffffffu, cnt);
-                if (lane == 0) atomicAdd(&hist[class_of(sa_zt[s])], cnt + (a2 >= B ? 1u : 0u));
+                if (lane == 0) atomicAdd(&hist[class_of(sa_zt[s]) - lo], cnt + (a2 >= B ? 1u : 0u));
             }
             if (a_in) {  // beta singles and beta-beta doubles keep alpha string A
                 uint32_t cnt = 0;
@@ -757,26 +891,53 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                     }
                 }
                 cnt = __reduce_add_sync(0xffffffffu, cnt);
-                if (lane == 0 && cnt) atomicAdd(&hist[class_of(F.ZcA)], cnt);
+                if (lane == 0 && cnt) atomicAdd(&hist[class_of(F.ZcA) - lo], cnt);
             }
         }
-        for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
-            int pr = pairs[pi];
-            int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
-            uint64_t z12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
-            uint64_t a12 = A ^ (1ull << r1) ^ (1ull << r2);
-            for (int t = lane; t < n_vir_pairs_a; t += 32) {
-                int pv = pairs[t];
-                int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
-                uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
-                if (!cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, al)) continue;
-                if (sym && al < B) continue;
-                atomicAdd(&hist[class_of(z12 ^ F.zc[a1] ^ F.zc[a2])], 1u);
+        // alpha-alpha doubles (beta string B): every candidate when all classes
+        // are counted; for a narrower range only those of the bucket ranges
+        // the range maps to (as the emission finds them), each checked class
+        // by class
+        auto count_aa = [&](uint64_t z12, uint64_t a12, int r1, int r2, int pv) {
+            const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
+            const uint32_t h = class_of(z12 ^ F.zc[a1] ^ F.zc[a2]) - lo;
+            if (h >= n_hist) return;
+            const uint64_t al = a12 ^ (1ull << a1) ^ (1ull << a2);
+            if (!cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, al)) return;
+            if (sym && al < B) return;
+            if (cutting && !above_cut(c, same_double_value(dpair, NP, r1, r2, a1, a2), cut)) return;
+            atomicAdd(&hist[h], 1u);
+        };
+        if (n_hist == (uint32_t)kNumClasses) {
+            for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
+                const int pr = pairs[pi];
+                const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+                const uint64_t z12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
+                const uint64_t a12 = A ^ (1ull << r1) ^ (1ull << r2);
+                for (int t = lane; t < n_vir_pairs_a; t += 32) count_aa(z12, a12, r1, r2, pairs[t]);
+            }
+        } else {
+            uint32_t *vb_cnt = reinterpret_cast<uint32_t *>(smem + p.smem_vbk);
+            uint16_t *vb_off = reinterpret_cast<uint16_t *>(vb_cnt + kVbkBuckets);
+            uint16_t *vb_list = vb_off + kVbkBuckets + 1;
+            build_vbk(F, pairs, n_vir_pairs_a, p.class_lo, p.class_hi, vb_cnt, vb_off, vb_list);
+            for (int pi = warp; pi < n_occ_pairs_a; pi += nw) {
+                const int pr = pairs[pi];
+                const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
+                const uint64_t z12 = F.ZcA ^ F.zc[r1] ^ F.zc[r2];
+                const uint64_t a12 = A ^ (1ull << r1) ^ (1ull << r2);
+                const uint32_t u = vb_bucket(z12);
+                for (int q = 0; q < F.n_blk; ++q) {
+                    const uint32_t k = F.blk_k[q];
+                    const uint32_t bb = (F.blk_g[q] ^ u) & ~((1u << k) - 1u);
+                    const int st = vb_off[bb], en = vb_off[bb + (1u << k)];
+                    for (int i = st + lane; i < en; i += 32) count_aa(z12, a12, r1, r2, pairs[vb_list[i]]);
+                }
             }
         }
         __syncthreads();
-        for (int i = tid; i < kNumClasses; i += kGenThreads)
-            if (hist[i]) atomicAdd(&p.class_counts[i], (unsigned long long)hist[i]);
+        for (int i = tid; i < (int)n_hist; i += kGenThreads)
+            if (hist[i]) atomicAdd(&p.class_counts[lo + i], (unsigned long long)hist[i]);
         return;
     } else if constexpr (MODE == kModeBetaCount) {
         // beta classes of the terms whose alpha class is the heavy class K:
@@ -857,63 +1018,10 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
 
         // bucket table of the virtual alpha pairs, and the pass's classes as
         // aligned blocks of bucket groups
-        uint32_t *vb_cnt = reinterpret_cast<uint32_t *>(smem + p.smem_hist);
+        uint32_t *vb_cnt = reinterpret_cast<uint32_t *>(smem + p.smem_vbk);
         uint16_t *vb_off = reinterpret_cast<uint16_t *>(vb_cnt + kVbkBuckets);
         uint16_t *vb_list = vb_off + kVbkBuckets + 1;
-        if (b_in) {  // uniform across the CTA
-            if (tid == 0) {
-                constexpr int gs = kClassBits - kVbkBits;
-                uint32_t g = class_lo >> gs;
-                const uint32_t g1 = ((class_hi - 1) >> gs) + 1;
-                int nb = 0;
-                while (g < g1) {
-                    int k = kVbkBits;
-                    while (k > 0 && ((g & ((1u << k) - 1u)) != 0 || g + (1u << k) > g1)) --k;
-                    F.blk_g[nb] = (uint16_t)g;
-                    F.blk_k[nb] = (uint8_t)k;
-                    ++nb;
-                    g += 1u << k;
-                }
-                F.n_blk = nb;
-            }
-            for (int b = tid; b < kVbkBuckets; b += kGenThreads) vb_cnt[b] = 0;
-            __syncthreads();
-            for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
-                const int pv = pairs[t];
-                atomicAdd(&vb_cnt[vb_bucket(F.zc[F.virA[pv & 0xFF]] ^ F.zc[F.virA[pv >> 8]])], 1u);
-            }
-            __syncthreads();
-            {
-                const uint4 c4 = reinterpret_cast<const uint4 *>(vb_cnt)[tid];
-                const uint32_t sum = c4.x + c4.y + c4.z + c4.w;
-                uint32_t incl = sum;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += v;
-                }
-                if (lane == 31) F.wsum[warp] = incl;
-                __syncthreads();
-                uint32_t run = incl - sum;
-#pragma unroll
-                for (int k = 0; k < nw; ++k) run += k < warp ? F.wsum[k] : 0u;
-                const uint32_t c[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    vb_off[4 * tid + k] = (uint16_t)run;
-                    vb_cnt[4 * tid + k] = run;  // scatter cursor
-                    run += c[k];
-                }
-                if (tid == kGenThreads - 1) vb_off[kVbkBuckets] = (uint16_t)run;
-            }
-            __syncthreads();
-            for (int t = tid; t < n_vir_pairs_a; t += kGenThreads) {
-                const int pv = pairs[t];
-                const uint32_t b = vb_bucket(F.zc[F.virA[pv & 0xFF]] ^ F.zc[F.virA[pv >> 8]]);
-                vb_list[atomicAdd(&vb_cnt[b], 1u)] = (uint16_t)t;
-            }
-            __syncthreads();
-        }
+        if (b_in) build_vbk(F, pairs, n_vir_pairs_a, class_lo, class_hi, vb_cnt, vb_off, vb_list);  // uniform
 
         // ---- alpha singles (few per determinant: O(n) element each); beta string B
         if (b_in)
@@ -1046,7 +1154,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
                 const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 if (cutting) {
-                    el = same_double_value(eri, N, r1, r2, a1, a2);
+                    el = same_double_value(dpair, NP, r1, r2, a1, a2);
                     if (!above_cut(c, el, cut)) return false;
                 }
                 zt = ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2] ^ F.zta[a1] ^ F.zta[a2];
@@ -1061,7 +1169,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 ka = w1 ^ (1ull << r2) ^ (1ull << a2);
                 kb = B;
                 const uint32_t par = __popcll(A & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                const double v = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
+                const double v = cutting ? el : same_double_value(dpair, NP, r1, r2, a1, a2);
                 num = flip_sign(c * v, par);
                 // H_aa - H_ii = -g(r1) - g(r2) + W(r1,r2) + v(a1) + v(a2) + W(a1,a2),
                 // v(x) = g(x) - W(r1,x) - W(r2,x)
@@ -1212,7 +1320,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                             const int r1 = F.occB[pr & 0xFF], r2 = F.occB[pr >> 8];
                             const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
                             if (cutting) {
-                                el = same_double_value(eri, N, r1, r2, a1, a2);
+                                el = same_double_value(dpair, NP, r1, r2, a1, a2);
                                 if (!above_cut(c, el, cut)) return false;
                             }
                             zt = ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2] ^ F.ztb[a1] ^ F.ztb[a2];
@@ -1228,7 +1336,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                             kb = w1 ^ (1ull << r2) ^ (1ull << a2);
                             const uint32_t par =
                                 __popcll(B & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
-                            const double v = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
+                            const double v = cutting ? el : same_double_value(dpair, NP, r1, r2, a1, a2);
                             num = flip_sign(c * v, par);
                             den = d0 + F.gB[r1] + F.gB[r2] - __ldg(WSx + r1 * N + r2) -
                                   (F.gB[a1] - __ldg(WSx + r1 * N + a1) - __ldg(WSx + r2 * N + a1)) -
@@ -1261,7 +1369,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 const int pv = pairs[t];
                                 const int a1 = F.virB[pv & 0xFF], a2 = F.virB[pv >> 8];
                                 if (cutting) {
-                                    el = same_double_value(eri, N, r1, r2, a1, a2);
+                                    el = same_double_value(dpair, NP, r1, r2, a1, a2);
                                     if (!above_cut(c, el, cut)) return false;
                                 }
                                 zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
@@ -1277,7 +1385,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 const uint32_t par =
                                     __popcll(B & between_mask(r1, a1)) + __popcll(w1 & between_mask(r2, a2));
                                 // a1 is the fastest-varying index across lanes
-                                const double v = cutting ? el : same_double_value(eri, N, r1, r2, a1, a2);
+                                const double v = cutting ? el : same_double_value(dpair, NP, r1, r2, a1, a2);
                                 num = flip_sign(c * v, par);
                                 den = base - vec[j1] - vec[j2] - __ldg(WSx + a1 * N + a2);
                             });
@@ -2609,8 +2717,19 @@ void gen_layout(GenParams &p, GenMode mode)
     p.smem_vec = (int)off;
     off = al(off + (size_t)(kGenThreads / 32) * kMaxOrb * 8);
     p.smem_hist = (int)off;
-    if (mode == kModeClassCount || mode == kModeBetaCount) off = al(off + (size_t)kNumClasses * 4);
-    else off = al(off + kVbkBytes);
+    p.smem_vbk = (int)off;
+    if (mode == kModeClassCount) {
+        // a histogram of the counted class range; a range narrower than all
+        // classes is counted through the bucket table of the virtual alpha pairs
+        const uint32_t w = p.class_hi - p.class_lo;
+        off = al(off + (size_t)w * 4);
+        p.smem_vbk = (int)off;
+        if (w < (uint32_t)kNumClasses) off = al(off + kVbkBytes);
+    } else if (mode == kModeBetaCount) {
+        off = al(off + (size_t)kNumClasses * 4);
+    } else {
+        off = al(off + kVbkBytes);
+    }
     p.smem_bytes = (int)off;
 }
 
@@ -2618,11 +2737,15 @@ cudaError_t launch_gen(GenMode mode, const GenBatch &b, uint64_t n_ctas, int sme
 {
     if (n_ctas == 0) return cudaSuccess;
     // the counting modes always carry the symmetry check (they have registers
-    // to spare) and never the cutoff (they count every term)
+    // to spare); the class count carries the cutoff for runs that have one,
+    // the beta count never (it counts every term of a heavy class)
     const unsigned g = (unsigned)n_ctas;
     constexpr int S = kFiltSym, C = kFiltCut;
     switch (mode) {
-    case kModeClassCount: gen_kernel<kModeClassCount, S><<<g, kGenThreads, smem_bytes, s>>>(b); break;
+    case kModeClassCount:  // a run with a numerator cutoff counts what it keeps
+        if (b.filt & C) gen_kernel<kModeClassCount, S | C><<<g, kGenThreads, smem_bytes, s>>>(b);
+        else gen_kernel<kModeClassCount, S><<<g, kGenThreads, smem_bytes, s>>>(b);
+        break;
     case kModeBetaCount: gen_kernel<kModeBetaCount, S><<<g, kGenThreads, smem_bytes, s>>>(b); break;
     case kModeTileCount:
         switch (b.filt & (S | C)) {
@@ -2658,8 +2781,15 @@ static int gen_smem_max()
     GenParams p;
     p.n_sa = 32 * 32;
     p.n_sb = 32 * 32;
+    p.class_lo = 0;
+    p.class_hi = kNumClasses - 1;  // the widest partial range: histogram and bucket table
     gen_layout(p, kModeClassCount);
-    return p.smem_bytes;
+    int m = p.smem_bytes;
+    for (GenMode mode : {kModeBetaCount, kModeEmit}) {
+        gen_layout(p, mode);
+        m = m > p.smem_bytes ? m : p.smem_bytes;
+    }
+    return m;
 }
 
 cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm)
@@ -2667,7 +2797,8 @@ cudaError_t init_kernel_attributes(int *tile_per_sm, int *big_per_sm)
     const int g = gen_smem_max();
     cudaError_t e;
     constexpr int S = kFiltSym, C = kFiltCut;
-    const void *gens[] = {(const void *)gen_kernel<kModeClassCount, S>, (const void *)gen_kernel<kModeBetaCount, S>,
+    const void *gens[] = {(const void *)gen_kernel<kModeClassCount, S>, (const void *)gen_kernel<kModeClassCount, S | C>,
+                          (const void *)gen_kernel<kModeBetaCount, S>,
                           (const void *)gen_kernel<kModeTileCount, 0>,  (const void *)gen_kernel<kModeTileCount, S>,
                           (const void *)gen_kernel<kModeTileCount, C>,  (const void *)gen_kernel<kModeTileCount, S | C>,
                           (const void *)gen_kernel<kModeEmit, 0>,       (const void *)gen_kernel<kModeEmit, S>,

@@ -24,7 +24,7 @@ struct DevBuf {
 
 struct SystemRes {
     int n = 0;
-    DevBuf h, eri, J, WS, Jx, WSx, hdx;
+    DevBuf h, eri, J, WS, Jx, WSx, hdx, dpair;
     int refs = 0;  // references using this system
 };
 
@@ -50,6 +50,7 @@ struct Pass {
     uint32_t b_lo = 0, b_hi = kNumClasses;
     uint64_t records = 0;
     uint64_t n_tiles = 0;
+    bool at_most = false;  // records is an upper bound (beta classes of a heavy class in a cutoff run)
 };
 
 // One PT2 solve scheduled by the engine.

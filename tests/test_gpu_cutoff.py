@@ -95,6 +95,23 @@ def test_cutoff_bit_identical_across_tilings_pass_plans_and_heavy_split(ctx, sma
     assert got["n_passes"] > 30
 
 
+def test_cutoff_passes_are_planned_from_kept_counts(ctx, small):
+    # the work list of a cutoff run counts the contributions it keeps (the
+    # same decisions as the emission: each pass's record count is then checked
+    # for equality), so its tiles hold the target and its passes run full
+    s, r, e0 = small["s"], small["r"], small["e0"]
+    cut, tt = 1e-5, 64
+    ref = oracle.pt2(s.h, s.eri, r.keys, r.coef, e0, cutoff=cut)
+    for budget in (12 << 20, 3 << 20):
+        got = ctx.run(small["rid"], cutoff=cut, tile_target=tt, pass_budget_bytes=budget)
+        exact = ctx.run(small["rid"], tile_target=tt, pass_budget_bytes=budget)
+        assert_matches_oracle(got, ref)
+        kept = got["n_terms"]
+        assert kept < 0.6 * exact["n_terms"]
+        assert kept / tt <= got["n_tiles"] <= kept / tt + got["n_passes"]
+        assert got["n_passes"] <= 0.7 * exact["n_passes"] + 1, (got["n_passes"], exact["n_passes"])
+
+
 def test_cutoff_with_constraint_classes(ctx, small):
     s, r, e0 = small["s"], small["r"], small["e0"]
     cut = 1e-5
