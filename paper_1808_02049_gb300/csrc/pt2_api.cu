@@ -249,7 +249,7 @@ void pt2_destroy(pt2_ctx *c)
                       &c->scan_tmp, &c->recs,         &c->ref_tile,    &c->ref_count,  &c->ref_off,
                       &c->ref_cursor, &c->ref_keys,   &c->big_list,    &c->big_max,    &c->scratch,
                       &c->acc,      &c->err_word,     &c->steps,       &c->gen_tab,    &c->dump_keys,
-                      &c->dump_num, &c->dump_haa,     &c->dump_count};
+                      &c->dump_num, &c->dump_haa,     &c->dump_count,  &c->grp_counts, &c->grp_tab};
     for (DevBuf *b : bufs) dev_free(c, *b);
     if (c->steps_pinned) cudaFreeHost(c->steps_pinned);
     for (auto &ev : c->ev)

@@ -414,24 +414,28 @@ struct DumpTarget {
 };
 
 // Enqueue one step on the context stream (no host synchronisation unless
-// profiling).  d is the step's device table.
-int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *dump, bool prof)
+// profiling).  d is the step's device table.  pre: the step's tile counts,
+// already counted by a grouped count (null: the step counts them itself).
+int enqueue_step(pt2_ctx *c, const StepPlan &sp, StepDev *d, const DumpTarget *dump, bool prof,
+                 const uint32_t *pre = nullptr)
 {
     cudaStream_t st = c->stream;
     const int n = (int)sp.items.size();
     cudaEvent_t *E = &c->ev[2];
     if (prof) CK(cudaEventRecord(E[0], st), "event");
-    CK(cudaMemsetAsync(c->tile_counts.ptr, 0, sp.n_tiles * 4, st), "memset");
     GenBatch gb{d->params, d->det_base, n, 0, {}, 0};
     for (const StepItem &it : sp.items) gb.filt |= job_filt(*it.job);
     if (n == 1) gb.one = step_item_params(c, sp, 0, 0);
     const int smem = step_smem(sp);
-    CK(gen_launch(c, kModeTileCount, gb, sp.n_ctas, smem), "tile count kernel");
+    if (!pre) {
+        CK(cudaMemsetAsync(c->tile_counts.ptr, 0, sp.n_tiles * 4, st), "memset");
+        CK(gen_launch(c, kModeTileCount, gb, sp.n_ctas, smem), "tile count kernel");
+    }
     if (prof) CK(cudaEventRecord(E[1], st), "event");
     unsigned long long *tile_off = reinterpret_cast<unsigned long long *>(c->tile_off.ptr);
     unsigned long long *tmp = reinterpret_cast<unsigned long long *>(c->scan_tmp.ptr);
     // tile offsets, and the same offsets as the 32-bit slot cursors of the emission
-    CK(launch_scan_u32_to_u64(reinterpret_cast<uint32_t *>(c->tile_counts.ptr), tile_off,
+    CK(launch_scan_u32_to_u64(pre ? pre : reinterpret_cast<const uint32_t *>(c->tile_counts.ptr), tile_off,
                               reinterpret_cast<uint32_t *>(c->cursor.ptr), sp.n_tiles, tmp, st),
        "scan");
     c->launches += 3;
@@ -525,6 +529,84 @@ void result_of(const RunAcc &h, const Job &j, pt2_result *out)
 }
 
 // Upload the device tables of a list of steps (one pinned staging copy).
+// Consecutive passes of one run over whole alpha classes (every beta class)
+// counted by one tile-count launch: each determinant's set-up (its singles,
+// their classes, the bucket table) is then done once per group instead of
+// once per pass.  A group's counts are kept until its passes have run.
+constexpr uint64_t kGrpMaxTiles = 1ull << 28;  // 1 GiB of counts
+struct CountGroup {
+    size_t k0 = 0, n = 0;  // steps k0 .. k0 + n - 1, one pass each
+    uint64_t tiles = 0;
+    uint32_t tab[kGrpTab] = {};
+};
+
+std::vector<CountGroup> count_groups(const Job &j, const std::vector<StepPlan> &steps)
+{
+    std::vector<CountGroup> out;
+    if (j.gp.top_mask) return out;  // triplet runs list their alpha-alpha doubles by Algorithm 3
+    auto plain = [&](size_t k) {
+        if (steps[k].items.size() != 1 || steps[k].items[0].job != &j) return false;
+        const Pass &P = j.passes[steps[k].items[0].pass];
+        return P.b_lo == 0 && P.b_hi >= (uint32_t)kNumClasses;
+    };
+    size_t k = 0;
+    while (k < steps.size()) {
+        if (!plain(k)) {
+            ++k;
+            continue;
+        }
+        CountGroup g;
+        g.k0 = k;
+        uint32_t hi = 0;
+        while (k < steps.size() && plain(k) && g.n < (size_t)kMaxGrp) {
+            const Pass &P = j.passes[steps[k].items[0].pass];
+            if (g.n > 0 && (P.c_lo != hi || g.tiles + P.n_tiles > kGrpMaxTiles)) break;
+            g.tab[g.n] = P.c_lo;
+            g.tab[kMaxGrp + 1 + g.n] = (uint32_t)g.tiles;
+            g.tab[2 * kMaxGrp + 1 + g.n] = (uint32_t)P.n_tiles;
+            g.tiles += P.n_tiles;
+            hi = P.c_hi;
+            ++g.n;
+            ++k;
+        }
+        g.tab[g.n] = hi;
+        if (g.n >= 2) out.push_back(g);
+    }
+    return out;
+}
+
+// One tile-count launch over the passes of group g (its table at dtab).
+int enqueue_group_count(pt2_ctx *c, const Job &j, const CountGroup &g, const uint32_t *dtab, bool prof)
+{
+    cudaStream_t st = c->stream;
+    cudaEvent_t *E = &c->ev[2];
+    if (prof) CK(cudaEventRecord(E[0], st), "event");
+    GenParams p = j.gp;
+    p.class_lo = g.tab[0];
+    p.class_hi = g.tab[g.n];
+    p.bclass_lo = 0;
+    p.bclass_hi = kNumClasses;
+    p.n_tiles = g.tiles;
+    p.tile_base = 0;
+    p.det_begin = 0;
+    p.class_counts = nullptr;
+    p.tile_counts = reinterpret_cast<uint32_t *>(c->grp_counts.ptr);
+    p.n_grp = (uint32_t)g.n;
+    p.grp = dtab;
+    gen_layout(p, kModeEmit);
+    CK(cudaMemsetAsync(c->grp_counts.ptr, 0, g.tiles * 4, st), "memset");
+    GenBatch gb{nullptr, nullptr, 1, 0, p, job_filt(j)};
+    CK(gen_launch(c, kModeTileCount, gb, j.r->n_det, p.smem_bytes), "grouped tile count kernel");
+    if (prof) {
+        CK(cudaEventRecord(E[1], st), "event");
+        CK(cudaEventSynchronize(E[1]), "sync");
+        float ms;
+        cudaEventElapsedTime(&ms, E[0], E[1]);
+        c->phase_ms[1] += ms;
+    }
+    return PT2_OK;
+}
+
 int upload_steps(pt2_ctx *c, const std::vector<StepPlan> &steps, DevBuf &dst)
 {
     const size_t bytes = steps.size() * sizeof(StepDev);
@@ -575,9 +657,34 @@ int run_single(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, pt2_result *ou
     CK(cudaMemsetAsync(c->err_word.ptr, 0, 4, st), "memset");
     CK(launch_acc_init(j.acc, 1, st), "acc init");
     CK(job_subtract(c, j, j.acc, st), "duplicate subtraction");
+    // passes whose tiles are counted in groups
+    const std::vector<CountGroup> groups = count_groups(j, steps);
+    if (!groups.empty()) {
+        uint64_t mt = 0;
+        std::vector<uint32_t> tabs;
+        for (const CountGroup &g : groups) {
+            mt = std::max(mt, g.tiles);
+            tabs.insert(tabs.end(), g.tab, g.tab + kGrpTab);
+        }
+        if ((rc = ensure(c, c->grp_counts, mt * 4, "grouped tile counts"))) return rc;
+        if ((rc = ensure(c, c->grp_tab, tabs.size() * 4, "pass tables"))) return rc;
+        CK(cudaMemcpyAsync(c->grp_tab.ptr, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice, st), "copy");
+    }
     StepDev *d = reinterpret_cast<StepDev *>(c->steps.ptr);
-    for (size_t k = 0; k < steps.size(); ++k)
-        if ((rc = enqueue_step(c, steps[k], d + k, dump, prof))) return rc;
+    size_t gi = 0;
+    for (size_t k = 0; k < steps.size(); ++k) {
+        while (gi < groups.size() && k >= groups[gi].k0 + groups[gi].n) ++gi;
+        const uint32_t *pre = nullptr;
+        if (gi < groups.size() && k >= groups[gi].k0) {
+            const CountGroup &g = groups[gi];
+            if (k == g.k0 &&
+                (rc = enqueue_group_count(c, j, g, reinterpret_cast<const uint32_t *>(c->grp_tab.ptr) + gi * kGrpTab,
+                                          prof)))
+                return rc;
+            pre = reinterpret_cast<const uint32_t *>(c->grp_counts.ptr) + g.tab[kMaxGrp + 1 + (k - g.k0)];
+        }
+        if ((rc = enqueue_step(c, steps[k], d + k, dump, prof, pre))) return rc;
+    }
     CK(launch_acc_finalize(j.acc, 1, st), "finalize");
     c->launches += 2;
     RunAcc h;

@@ -36,6 +36,12 @@ constexpr int kBigBuckets = 256;             // most hash buckets the partials o
 static_assert(kBigBuckets * kBigCap >= 2 * kBigScratch, "the hash split can always make buckets fit a chunk");
 static_assert(kBigScratch <= 65535, "bucket starts of the hash split are 16-bit");
 constexpr int kMaxBatch = 256;               // instances in one step
+// Passes whose tiles one tile-count launch counts together (a group of
+// consecutive passes of one run); the pass table has kGrpTab entries:
+// class boundaries lo[0..kMaxGrp], tile bases base[kMaxGrp], tile counts nt[kMaxGrp]
+constexpr int kMaxGrp = 64;
+constexpr int kGrpTab = 3 * kMaxGrp + 1;
+static_assert(kMaxGrp <= 64, "a pass index of a grouped count takes 6 bits");
 
 // Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is
 // assembled from) are int64 multiples of 2^-48 Ha; numerator and energy sums
@@ -124,6 +130,12 @@ struct GenParams {
     uint64_t top_mask, top_hi;    // alpha & top_hi == top_mask: the highest occupied alpha orbitals are top_mask (0, 0: none)
     uint64_t n_tiles;                  // tiles of this instance in the pass
     uint64_t tile_base;                // first global tile index of this instance
+    // tile-count mode over a group of n_grp > 0 passes (classes [class_lo,
+    // class_hi) = the union of theirs): a term of class cl belongs to pass
+    // q = the last with grp[q] <= cl and counts in tile grp[kMaxGrp + 1 + q] +
+    // tile_of(zt, grp[2 kMaxGrp + 1 + q]); 0: one pass, n_tiles tiles
+    uint32_t n_grp;
+    const uint32_t *grp;               // kGrpTab entries
     // outputs
     unsigned long long *class_counts;  // kNumClasses per instance; the class-count mode fills [class_lo, class_hi)
     uint32_t *tile_counts;             // n_tiles

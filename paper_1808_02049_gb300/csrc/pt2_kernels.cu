@@ -390,6 +390,8 @@ struct GenFixed {
     int64_t d0;
     int n_sa_pass, a_in_pass, n_sb_pass, b_in_pass;
     uint32_t chunk_a[32], chunk_b[32];  // pass flags of singles 32c .. 32c + 31 (n_sa, n_sb <= 1024)
+    uint32_t grp[kGrpTab];              // pass table of a grouped tile count (GenParams::grp)
+    uint32_t q_a;                       // its pass of the alpha string A
     uint32_t wsum[kGenThreads / 32];
     // the pass's alpha classes as aligned blocks of bucket groups (see above)
     uint16_t blk_g[2 * kVbkBitsMax];
@@ -480,6 +482,10 @@ struct EmitOut {
     uint32_t rec_cap;       // record slots of the step (< 2^32)
     uint32_t *err;
     double e0;              // DetTerms only
+    // TileCount over a group of passes: tile bases then tile counts of the
+    // passes (shared memory); the pass of a term rides in the low 6 bits of
+    // its tile hash, which tile_of does not read.  Null: one pass.
+    const uint32_t *gtab;
 };
 
 // Tile of a term from the high word of its tile hash: floor(zt_hi n_tiles / 2^32)
@@ -510,7 +516,14 @@ __device__ __forceinline__ void emit_batch(const EmitOut &p, int i0, int step, i
             if (i < n && key(i, zt, el[u])) {
                 ok |= 1u << u;
                 if constexpr (MODE == kModeTileCount) {
-                    red_add_global(&p.ctr[tile_of(zt, p.n_tiles)], 1u);
+                    uint32_t t;
+                    if (p.gtab) {
+                        const uint32_t q = (uint32_t)zt & 63u;
+                        t = p.gtab[q] + tile_of(zt, p.gtab[kMaxGrp + q]);
+                    } else {
+                        t = tile_of(zt, p.n_tiles);
+                    }
+                    red_add_global(&p.ctr[t], 1u);
                 } else if constexpr (MODE == kModeEmit) {
                     slot[u] = atom_add_global(&p.ctr[tile_of(zt, p.n_tiles)], 1u);
                 } else {
@@ -658,6 +671,22 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         F.ztb[i] = p.hash->ztb[i];
     }
     for (int t = tid; t < N * (N - 1) / 2; t += kGenThreads) pairs[t] = p.hash->pairs[t];
+    // a tile count over a group of passes: the pass of a class is the last q
+    // with grp[q] <= class
+    const bool grouped = MODE == kModeTileCount && p.n_grp != 0;
+    if (grouped)
+        for (int i = tid; i < kGrpTab; i += kGenThreads) F.grp[i] = p.grp[i];
+    auto grp_of = [&](uint32_t cl) {
+        int lo = 0, hi = (int)p.n_grp;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (F.grp[mid] <= cl) lo = mid;
+            else hi = mid;
+        }
+        return (uint32_t)lo;
+    };
+    // the tile hash of a term with its pass in the low 6 bits (grouped count)
+    auto with_pass = [&](uint64_t zt, uint32_t q) { return grouped ? ((zt & ~63ull) | q) : zt; };
     // the class-count mode histograms the classes [class_lo, class_hi) only
     const uint32_t n_hist = MODE == kModeClassCount ? p.class_hi - p.class_lo : (uint32_t)kNumClasses;
     if constexpr (kCount)
@@ -721,7 +750,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
     const uint32_t mvb = nvb ? (uint32_t)((0x100000000ull + nvb - 1) / nvb) : 0u;  // exact while s * nv < 2^32
     for (int s0 = 0; s0 < p.n_sa; s0 += kGenThreads) {
         const int s = s0 + tid;
-        uint32_t inp = 0;
+        uint32_t inp = 0, qs = 0;
         if (s < p.n_sa) {
             const int i = (int)__umulhi((uint32_t)s, mva), j = s - i * nva;
             const int r = F.occA[i], a = F.virA[j];
@@ -733,10 +762,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             } else {
                 const uint32_t cl = class_of(zc);
                 inp = cl >= p.class_lo && cl < p.class_hi && cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, a2);
+                if (grouped && inp) qs = grp_of(cl);
             }
             if constexpr (kVal) sa_delta[s] = F.gA[a] - F.gA[r] - WSx[r * N + a];
             sa_zt[s] = kCount ? zc : (F.ZtaA ^ F.zta[r] ^ F.zta[a]);
-            sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17);
+            // bits 0-7 r, 8-15 a, 16 sign, 17 in the pass, 18-23 pass of a grouped count
+            sa_info[s] = (uint32_t)r | ((uint32_t)a << 8) | (sg << 16) | (inp << 17) | (qs << 18);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, inp != 0);
         if (lane == 0) F.chunk_a[(s0 >> 5) + warp] = m;
@@ -766,6 +797,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         } else {
             uint32_t cl = class_of(F.ZcA);
             ok = ok && cl >= p.class_lo && cl < p.class_hi;
+            F.q_a = grouped && ok ? grp_of(cl) : 0u;
         }
         F.a_in_pass = ok;
         const uint32_t bc = bclass_of(F.ZcbB);
@@ -1011,6 +1043,8 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         out.rec_cap = (uint32_t)min(p.rec_cap, (unsigned long long)0xFFFFFFFFull);
         out.err = p.err;
         out.e0 = p.e0;
+        out.gtab = grouped ? F.grp + kMaxGrp + 1 : nullptr;
+        const uint32_t q_a = F.q_a;  // pass of A (grouped count)
         const uint32_t class_lo = p.class_lo, class_hi = p.class_hi;
         // beta singles of the pass: all of them, or the compacted list
         const int n_sb = bfull ? p.n_sb : F.n_sb_pass;
@@ -1036,7 +1070,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                         el = single_value(ht, eri, N, F.occA, na, F.occB, nb, info & 0xFF, (info >> 8) & 0xFF);
                         if (!above_cut(c, el, cut)) return false;
                     }
-                    zt = sa_zt[s] ^ ZtbB;
+                    zt = with_pass(sa_zt[s] ^ ZtbB, sa_info[s] >> 18);
                     return true;
                 },
                 [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
@@ -1062,7 +1096,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                             el = single_value(ht, eri, N, F.occB, nb, F.occA, na, info & 0xFF, (info >> 8) & 0xFF);
                             if (!above_cut(c, el, cut)) return false;
                         }
-                        zt = ZtaA ^ sb_zt[s];
+                        zt = with_pass(ZtaA ^ sb_zt[s], q_a);
                         return true;
                     },
                     [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
@@ -1114,7 +1148,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                            ((bi >> 8) & 0xFF));
                                 if (!above_cut(c, el, cut)) return false;
                             }
-                            zt = sa_zt[s] ^ sb_zt[sb];
+                            zt = with_pass(sa_zt[s] ^ sb_zt[sb], ia >> 18);
                             return true;
                         },
                         [&](int i, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
@@ -1150,19 +1184,19 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
             const uint32_t lt = (1u << lane) - 1u;
             auto key_aa = [&](int k, uint64_t &zt, double &el) {
                 const uint32_t e = clist[k];
-                const int pr = pairs[e >> 16], pv = pairs[e & 0xFFFFu];
+                const int pr = pairs[(e >> 16) & 0x3FFu], pv = pairs[e & 0xFFFFu];
                 const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
                 const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 if (cutting) {
                     el = same_double_value(dpair, NP, r1, r2, a1, a2);
                     if (!above_cut(c, el, cut)) return false;
                 }
-                zt = ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2] ^ F.zta[a1] ^ F.zta[a2];
+                zt = with_pass(ZtaA ^ ZtbB ^ F.zta[r1] ^ F.zta[r2] ^ F.zta[a1] ^ F.zta[a2], e >> 26);
                 return true;
             };
             auto val_aa = [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
                 const uint32_t e = clist[k];
-                const int pr = pairs[e >> 16], pv = pairs[e & 0xFFFFu];
+                const int pr = pairs[(e >> 16) & 0x3FFu], pv = pairs[e & 0xFFFFu];
                 const int r1 = F.occA[pr & 0xFF], r2 = F.occA[pr >> 8];
                 const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 const uint64_t w1 = A ^ (1ull << r1) ^ (1ull << a1);
@@ -1214,9 +1248,12 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                 const int a1 = F.virA[pv & 0xFF], a2 = F.virA[pv >> 8];
                 const uint32_t cl = class_of(F.ZcA ^ F.zc[r1] ^ F.zc[r2] ^ F.zc[a1] ^ F.zc[a2]);
                 const uint64_t w2 = A ^ (1ull << r1) ^ (1ull << r2) ^ (1ull << a1) ^ (1ull << a2);
-                item = ((uint32_t)pi << 16) | (uint32_t)vp;
-                return cl >= p.class_lo && cl < p.class_hi &&
-                       cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, w2) && !(sym && w2 < B);
+                const bool in = cl >= p.class_lo && cl < p.class_hi &&
+                                cons_ok(p.cons_mod, p.cons_rem, p.top_hi, p.top_mask, w2) && !(sym && w2 < B);
+                // bits 0-15 the virtual pair, 16-25 the occupied pair (< 1024
+                // for 64 orbitals), 26-31 the pass of a grouped count
+                item = ((grouped && in ? grp_of(cl) : 0u) << 26) | ((uint32_t)pi << 16) | (uint32_t)vp;
+                return in;
             };
             if (p.top_mask) {
                 // Algorithm 3 (fast generation for a triplet constraint T): the
@@ -1323,7 +1360,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                 el = same_double_value(dpair, NP, r1, r2, a1, a2);
                                 if (!above_cut(c, el, cut)) return false;
                             }
-                            zt = ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2] ^ F.ztb[a1] ^ F.ztb[a2];
+                            zt = with_pass(ZtaA ^ ZtbB ^ F.ztb[r1] ^ F.ztb[r2] ^ F.ztb[a1] ^ F.ztb[a2], q_a);
                             return true;
                         },
                         [&](int k, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {
@@ -1372,7 +1409,7 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
                                     el = same_double_value(dpair, NP, r1, r2, a1, a2);
                                     if (!above_cut(c, el, cut)) return false;
                                 }
-                                zt = zt12 ^ F.ztb[a1] ^ F.ztb[a2];
+                                zt = with_pass(zt12 ^ F.ztb[a1] ^ F.ztb[a2], q_a);
                                 return true;
                             },
                             [&](int t, uint64_t &ka, uint64_t &kb, double &num, int64_t &den, double el) {

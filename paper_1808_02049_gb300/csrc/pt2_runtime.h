@@ -117,6 +117,7 @@ struct pt2_ctx {
     pt2::DevBuf class_counts, tile_counts, tile_off, cursor, scan_tmp, recs, ref_tile, ref_count, ref_off,
         ref_cursor, ref_keys, big_list, big_max, scratch, acc, err_word, steps, gen_tab, dump_keys, dump_num,
         dump_haa, dump_count;
+    pt2::DevBuf grp_counts, grp_tab;  // tile counts of a group of passes counted by one launch, and its pass tables
     uint64_t ws_gen = 0;  // bumped whenever a device buffer is reallocated
     void *steps_pinned = nullptr;  // staging of the step tables (pinned)
     size_t steps_pinned_bytes = 0;

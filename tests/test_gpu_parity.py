@@ -167,6 +167,25 @@ def test_many_passes(ctx, small):
     assert_same_result(got, small["ref"])
 
 
+def test_grouped_tile_counts(ctx, small):
+    # consecutive passes over whole alpha classes are counted by one launch
+    # per group of at most 64 passes; a 1 MB budget makes about 100 passes,
+    # so more than one group, and splits the heavy alpha class by beta class
+    # between them.  The run must equal the oracle and, bit for bit, the same
+    # plan run as a batch, whose steps count their own tiles
+    kw = dict(pass_budget_bytes=1 << 20, tile_target=256)
+    got = ctx.run(small["rid"], **kw)
+    assert got["n_passes"] > 90
+    assert_same_result(got, small["ref"])
+    bid = ctx.batch_create([small["rid"]], **kw)
+    try:
+        (b,) = ctx.batch_run(bid, 1)
+    finally:
+        ctx.batch_destroy(bid)
+    for f in ("e2", "n_terms", "n_unique", "n_external", "digest_sum", "digest_xor", "n_tiles", "n_passes"):
+        assert b[f] == got[f], f
+
+
 def test_constraint_classes(ctx, small):
     s, r, e0 = small["s"], small["r"], small["e0"]
     m = 5
