@@ -430,10 +430,10 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began 62af1956
-    "kernels_sha256": "47fa7006f944aef63914c548150ed4cb71088c406836ac6830620e040b82c905",
-    "tile_kernel": (1.444859e9 + 3.687168e6) / 45_176_097,     # 32.06 B per term
-    "gen_kernel<Emit>": (0.217976e9 + 1.394653e9) / 45_176_097,  # 35.70 B per term
+    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began bc6ca55c
+    "kernels_sha256": "3f26a02c05e9068acc7c21e04d5474b0259370720865d6484ba5ae0e8aac068a",
+    "tile_kernel": (1.444887e9 + 3.213568e6) / 45_176_097,     # 32.05 B per term
+    "gen_kernel<Emit>": (0.173164e9 + 1.392590e9) / 45_176_097,  # 34.66 B per term
 }
 
 
@@ -648,7 +648,7 @@ def run_gpu(args):
                            "e2_complete_solve": sum(per_slice[k][0]["e2"] for k in range(M)) if covered else None,
                            "terms_complete_solve": sum(per_slice[k][0]["n_terms"] for k in range(M)) if covered
                            else None,
-                           "l2": "inputs larger than L2 (32-byte records, up to 96 GB per pass, stream through "
+                           "l2": "inputs larger than L2 (32-byte records, up to 64 GiB per pass, stream through "
                                  "HBM) and a 256 MB L2 flush between steps",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roof,
