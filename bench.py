@@ -430,10 +430,10 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began bc6ca55c
-    "kernels_sha256": "3f26a02c05e9068acc7c21e04d5474b0259370720865d6484ba5ae0e8aac068a",
-    "tile_kernel": (1.444887e9 + 3.213568e6) / 45_176_097,     # 32.05 B per term
-    "gen_kernel<Emit>": (0.173164e9 + 1.392590e9) / 45_176_097,  # 34.66 B per term
+    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began 75947701
+    "kernels_sha256": "6d15b0f14066b677cfa4e5803fcce36324ac9cc3052c021b1647517f28ae4f05",
+    "tile_kernel": (1.444991e9 + 3.737088e6) / 45_176_097,     # 32.07 B per term
+    "gen_kernel<Emit>": (0.172486e9 + 1.392777e9) / 45_176_097,  # 34.65 B per term
 }
 
 

@@ -537,7 +537,7 @@ constexpr uint64_t kGrpMaxTiles = 1ull << 28;  // 1 GiB of counts
 struct CountGroup {
     size_t k0 = 0, n = 0;  // steps k0 .. k0 + n - 1, one pass each
     uint64_t tiles = 0;
-    uint32_t tab[kGrpTab] = {};
+    uint32_t tab[kGrpStride] = {};  // pass table, then the pass of each class (bytes)
 };
 
 std::vector<CountGroup> count_groups(const Job &j, const std::vector<StepPlan> &steps)
@@ -570,6 +570,9 @@ std::vector<CountGroup> count_groups(const Job &j, const std::vector<StepPlan> &
             ++k;
         }
         g.tab[g.n] = hi;
+        uint8_t *cls = reinterpret_cast<uint8_t *>(g.tab + kGrpClsOff);
+        for (size_t q = 0; q < g.n; ++q)
+            for (uint32_t c = g.tab[q]; c < g.tab[q + 1]; ++c) cls[c] = (uint8_t)q;
         if (g.n >= 2) out.push_back(g);
     }
     return out;
@@ -593,7 +596,7 @@ int enqueue_group_count(pt2_ctx *c, const Job &j, const CountGroup &g, const uin
     p.tile_counts = reinterpret_cast<uint32_t *>(c->grp_counts.ptr);
     p.n_grp = (uint32_t)g.n;
     p.grp = dtab;
-    gen_layout(p, kModeEmit);
+    gen_layout(p, kModeTileCount);
     CK(cudaMemsetAsync(c->grp_counts.ptr, 0, g.tiles * 4, st), "memset");
     GenBatch gb{nullptr, nullptr, 1, 0, p, job_filt(j)};
     CK(gen_launch(c, kModeTileCount, gb, j.r->n_det, p.smem_bytes), "grouped tile count kernel");
@@ -664,7 +667,7 @@ int run_single(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, pt2_result *ou
         std::vector<uint32_t> tabs;
         for (const CountGroup &g : groups) {
             mt = std::max(mt, g.tiles);
-            tabs.insert(tabs.end(), g.tab, g.tab + kGrpTab);
+            tabs.insert(tabs.end(), g.tab, g.tab + kGrpStride);
         }
         if ((rc = ensure(c, c->grp_counts, mt * 4, "grouped tile counts"))) return rc;
         if ((rc = ensure(c, c->grp_tab, tabs.size() * 4, "pass tables"))) return rc;
@@ -678,7 +681,7 @@ int run_single(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, pt2_result *ou
         if (gi < groups.size() && k >= groups[gi].k0) {
             const CountGroup &g = groups[gi];
             if (k == g.k0 &&
-                (rc = enqueue_group_count(c, j, g, reinterpret_cast<const uint32_t *>(c->grp_tab.ptr) + gi * kGrpTab,
+                (rc = enqueue_group_count(c, j, g, reinterpret_cast<const uint32_t *>(c->grp_tab.ptr) + gi * kGrpStride,
                                           prof)))
                 return rc;
             pre = reinterpret_cast<const uint32_t *>(c->grp_counts.ptr) + g.tab[kMaxGrp + 1 + (k - g.k0)];

@@ -37,11 +37,15 @@ static_assert(kBigBuckets * kBigCap >= 2 * kBigScratch, "the hash split can alwa
 static_assert(kBigScratch <= 65535, "bucket starts of the hash split are 16-bit");
 constexpr int kMaxBatch = 256;               // instances in one step
 // Passes whose tiles one tile-count launch counts together (a group of
-// consecutive passes of one run); the pass table has kGrpTab entries:
-// class boundaries lo[0..kMaxGrp], tile bases base[kMaxGrp], tile counts nt[kMaxGrp]
+// consecutive passes of one run).  A group's table: kGrpTab u32 entries (class
+// boundaries lo[0..kMaxGrp], tile bases base[kMaxGrp], tile counts nt[kMaxGrp]),
+// then from u32 entry kGrpClsOff on the pass of every class, one byte per class
 constexpr int kMaxGrp = 64;
 constexpr int kGrpTab = 3 * kMaxGrp + 1;
+constexpr int kGrpClsOff = 196;                           // 16-byte aligned
+constexpr int kGrpStride = kGrpClsOff + kNumClasses / 4;  // u32 entries of one group's table
 static_assert(kMaxGrp <= 64, "a pass index of a grouped count takes 6 bits");
+static_assert(kGrpClsOff >= kGrpTab && kGrpClsOff % 4 == 0, "the class table follows the pass table, aligned");
 
 // Fixed-point scales.  Diagonal quantities (E0 - H_aa and the pieces it is
 // assembled from) are int64 multiples of 2^-48 Ha; numerator and energy sums
@@ -132,10 +136,11 @@ struct GenParams {
     uint64_t tile_base;                // first global tile index of this instance
     // tile-count mode over a group of n_grp > 0 passes (classes [class_lo,
     // class_hi) = the union of theirs): a term of class cl belongs to pass
-    // q = the last with grp[q] <= cl and counts in tile grp[kMaxGrp + 1 + q] +
-    // tile_of(zt, grp[2 kMaxGrp + 1 + q]); 0: one pass, n_tiles tiles
+    // q = byte cl of the class table (the last q with grp[q] <= cl) and counts
+    // in tile grp[kMaxGrp + 1 + q] + tile_of(zt, grp[2 kMaxGrp + 1 + q]);
+    // 0: one pass, n_tiles tiles
     uint32_t n_grp;
-    const uint32_t *grp;               // kGrpTab entries
+    const uint32_t *grp;               // kGrpStride entries (16-byte aligned)
     // outputs
     unsigned long long *class_counts;  // kNumClasses per instance; the class-count mode fills [class_lo, class_hi)
     uint32_t *tile_counts;             // n_tiles
@@ -144,7 +149,7 @@ struct GenParams {
     unsigned long long rec_cap;        // records the launch may write (emit and det-terms modes)
     uint32_t *err;
     // dynamic shared memory layout (byte offsets)
-    int smem_sa, smem_sb, smem_pairs, smem_vec, smem_hist, smem_vbk, smem_bytes;
+    int smem_sa, smem_sb, smem_pairs, smem_vec, smem_hist, smem_vbk, smem_gcls, smem_bytes;
     int n_sa, n_sb;                    // singles per determinant: na*(n-na), nb*(n-nb)
 };
 

@@ -671,20 +671,16 @@ __device__ __forceinline__ void gen_body(const GenParams &p, const uint64_t det)
         F.ztb[i] = p.hash->ztb[i];
     }
     for (int t = tid; t < N * (N - 1) / 2; t += kGenThreads) pairs[t] = p.hash->pairs[t];
-    // a tile count over a group of passes: the pass of a class is the last q
-    // with grp[q] <= class
+    // a tile count over a group of passes: its pass table, and the pass of
+    // each class (one byte per class, copied 16 bytes per thread)
     const bool grouped = MODE == kModeTileCount && p.n_grp != 0;
-    if (grouped)
+    uint8_t *gcls = smem + p.smem_gcls;
+    if (grouped) {
         for (int i = tid; i < kGrpTab; i += kGenThreads) F.grp[i] = p.grp[i];
-    auto grp_of = [&](uint32_t cl) {
-        int lo = 0, hi = (int)p.n_grp;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (F.grp[mid] <= cl) lo = mid;
-            else hi = mid;
-        }
-        return (uint32_t)lo;
-    };
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.grp + kGrpClsOff);
+        for (int i = tid; i < kNumClasses / 16; i += kGenThreads) reinterpret_cast<uint4 *>(gcls)[i] = src[i];
+    }
+    auto grp_of = [&](uint32_t cl) { return (uint32_t)gcls[cl]; };
     // the tile hash of a term with its pass in the low 6 bits (grouped count)
     auto with_pass = [&](uint64_t zt, uint32_t q) { return grouped ? ((zt & ~63ull) | q) : zt; };
     // the class-count mode histograms the classes [class_lo, class_hi) only
@@ -2767,6 +2763,8 @@ void gen_layout(GenParams &p, GenMode mode)
     } else {
         off = al(off + kVbkBytes);
     }
+    p.smem_gcls = (int)off;
+    if (mode == kModeTileCount && p.n_grp) off = al(off + kNumClasses);  // pass of each class
     p.smem_bytes = (int)off;
 }
 
@@ -2822,7 +2820,8 @@ static int gen_smem_max()
     p.class_hi = kNumClasses - 1;  // the widest partial range: histogram and bucket table
     gen_layout(p, kModeClassCount);
     int m = p.smem_bytes;
-    for (GenMode mode : {kModeBetaCount, kModeEmit}) {
+    p.n_grp = 1;  // a grouped tile count: the emission's layout and a class table
+    for (GenMode mode : {kModeBetaCount, kModeEmit, kModeTileCount}) {
         gen_layout(p, mode);
         m = m > p.smem_bytes ? m : p.smem_bytes;
     }

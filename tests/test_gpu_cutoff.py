@@ -148,6 +148,40 @@ def test_cutoff_with_spin_symmetry(ctx):
         ctx.unload(sid)
 
 
+def test_grouped_counts_with_cutoff_symmetry_and_slices(ctx):
+    # a cutoff run on a symmetric reference, one class slice, many passes:
+    # the single run counts its tiles in groups of passes, a batch of the same
+    # run counts them per step; both must give the same result bit for bit,
+    # and the slices must add up to the whole run
+    w = inputs.WORKLOADS["small"]
+    seed = inputs.workload_seed(w["seed_index"])
+    s = inputs.make_integrals(w["n_orb"], seed)
+    r = inputs.make_symmetric_reference(w["n_orb"], w["n_elec_per_spin"], w["n_det"], w["max_level"], seed + 1)
+    e0 = oracle.e0_of(s.h, s.eri, r.keys)
+    sid = ctx.load_system(s.h, s.eri)
+    rid = ctx.load_reference(sid, r.keys, r.coef, e0)
+    try:
+        kw = dict(cutoff=1e-5, spin_symmetric=True, pass_budget_bytes=1 << 19, tile_target=128)
+        whole = ctx.run(rid, cutoff=1e-5, spin_symmetric=True)
+        parts = []
+        for k in range(3):
+            got = ctx.run(rid, class_slice=(k, 3), **kw)
+            bid = ctx.batch_create([rid], class_slice=(k, 3), **kw)
+            try:
+                (b,) = ctx.batch_run(bid, 1)
+            finally:
+                ctx.batch_destroy(bid)
+            assert same(got, b), k
+            assert got["n_passes"] > 5
+            parts.append(got)
+        assert sum(p["n_terms"] for p in parts) == whole["n_terms"]
+        assert sum(p["n_external"] for p in parts) == whole["n_external"]
+        assert e2_close(sum(p["e2"] for p in parts), whole["e2"], 1e-13)
+    finally:
+        ctx.unload(rid)
+        ctx.unload(sid)
+
+
 def test_invalid_cutoff_is_rejected(ctx, small):
     for bad in (-1e-8, float("nan"), float("inf")):
         with pytest.raises(pt2.Pt2Error) as e:
