@@ -9,6 +9,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pt2_runtime.h"
@@ -104,6 +105,18 @@ bool finite_all(const double *x, size_t n)
 }
 
 uint64_t comb2(uint64_t m) { return m * (m - 1) / 2; }
+
+// f(lo, hi) over [0, n) in contiguous chunks, one per host thread (at most 16).
+template <class F>
+void parallel_chunks(size_t n, F &&f)
+{
+    const size_t hw = std::thread::hardware_concurrency();
+    const size_t nt = std::max<size_t>(1, std::min<size_t>(n, std::min<size_t>(16, hw ? hw : 1)));
+    std::vector<std::thread> th;
+    for (size_t t = 1; t < nt; ++t) th.emplace_back([&f, n, nt, t] { f(n * t / nt, n * (t + 1) / nt); });
+    f(0, n / nt);
+    for (auto &x : th) x.join();
+}
 
 uint64_t terms_per_det(int n, int na, int nb)
 {
@@ -272,34 +285,47 @@ int pt2_load_system(pt2_ctx *c, int n_orb, const double *h, const double *eri, u
             if (std::fabs(h[p * n + q] - h[q * n + p]) > 1e-12 * std::max(1.0, std::fabs(h[p * n + q])))
                 return fail(c, PT2_ERR_INVALID, "h is not symmetric at (%zu, %zu)", p, q);
     auto E = [&](size_t p, size_t q, size_t r, size_t s) { return eri[((p * n + q) * n + r) * n + s]; };
-    for (size_t p = 0; p < n; ++p)
-        for (size_t q = 0; q < n; ++q)
-            for (size_t r = 0; r < n; ++r)
-                for (size_t s = 0; s < n; ++s) {
-                    double v = E(p, q, r, s), tol = 1e-12 * std::max(1.0, std::fabs(v));
-                    if (std::fabs(v - E(q, p, r, s)) > tol || std::fabs(v - E(p, q, s, r)) > tol ||
-                        std::fabs(v - E(r, s, p, q)) > tol)
-                        return fail(c, PT2_ERR_INVALID, "eri lacks 8-fold symmetry at (%zu %zu|%zu %zu)", p, q, r, s);
-                }
+    // the first element (in index order) that differs from a symmetry partner;
+    // rows p are checked in parallel, each chunk keeps its first failure
+    std::vector<size_t> first(n, n4);
+    parallel_chunks(n, [&](size_t p0, size_t p1) {
+        for (size_t p = p0; p < p1; ++p)
+            for (size_t q = 0; q < n; ++q)
+                for (size_t r = 0; r < n; ++r)
+                    for (size_t s = 0; s < n; ++s) {
+                        const double v = E(p, q, r, s), tol = 1e-12 * std::max(1.0, std::fabs(v));
+                        if (std::fabs(v - E(q, p, r, s)) > tol || std::fabs(v - E(p, q, s, r)) > tol ||
+                            std::fabs(v - E(r, s, p, q)) > tol) {
+                            first[p0] = ((p * n + q) * n + r) * n + s;
+                            return;
+                        }
+                    }
+    });
+    const size_t bad = *std::min_element(first.begin(), first.end());
+    if (bad < n4)
+        return fail(c, PT2_ERR_INVALID, "eri lacks 8-fold symmetry at (%zu %zu|%zu %zu)", bad / (n2 * n),
+                    bad / n2 % n, bad / n % n, bad % n);
     // Canonical copies: every symmetry-equivalent element takes the value at one
     // canonical index, so the kernels may read whichever permutation gives them
     // contiguous addresses and still see bit-identical integrals.
     std::vector<double> hc(n2), ec(n4);
     for (size_t p = 0; p < n; ++p)
         for (size_t q = 0; q < n; ++q) hc[p * n + q] = p >= q ? h[p * n + q] : h[q * n + p];
-    for (size_t p = 0; p < n; ++p)
-        for (size_t q = 0; q < n; ++q)
-            for (size_t r = 0; r < n; ++r)
-                for (size_t t = 0; t < n; ++t) {
-                    size_t a = p, b = q, x = r, y = t;
-                    if (a < b) std::swap(a, b);
-                    if (x < y) std::swap(x, y);
-                    if (a * n + b < x * n + y) {
-                        std::swap(a, x);
-                        std::swap(b, y);
+    parallel_chunks(n, [&](size_t p0, size_t p1) {
+        for (size_t p = p0; p < p1; ++p)
+            for (size_t q = 0; q < n; ++q)
+                for (size_t r = 0; r < n; ++r)
+                    for (size_t t = 0; t < n; ++t) {
+                        size_t a = p, b = q, x = r, y = t;
+                        if (a < b) std::swap(a, b);
+                        if (x < y) std::swap(x, y);
+                        if (a * n + b < x * n + y) {
+                            std::swap(a, x);
+                            std::swap(b, y);
+                        }
+                        ec[((p * n + q) * n + r) * n + t] = E(a, b, x, y);
                     }
-                    ec[((p * n + q) * n + r) * n + t] = E(a, b, x, y);
-                }
+    });
     h = hc.data();
     eri = ec.data();
     cudaSetDevice(c->device);

@@ -330,6 +330,15 @@ def test_invalid_inputs_are_rejected(ctx, small):
     with pytest.raises(pt2.Pt2Error) as e:
         ctx.load_system(hb, s.eri)
     assert e.value.code == pt2.PT2_ERR_INVALID
+    # the integral check runs over rows in parallel and reports the first
+    # element (in index order) that breaks the 8-fold symmetry
+    eb = s.eri.copy()
+    eb[7, 3, 9, 5] += 1e-6
+    eb[2, 11, 4, 6] += 1e-6
+    with pytest.raises(pt2.Pt2Error) as e:
+        ctx.load_system(s.h, eb)
+    assert e.value.code == pt2.PT2_ERR_INVALID
+    assert "(2 11|4 6)" in str(e.value), str(e.value)
     with pytest.raises(pt2.Pt2Error) as e:
         ctx.load_system(np.eye(65), np.zeros((65,) * 4))
     assert e.value.code == pt2.PT2_ERR_UNSUPPORTED
