@@ -247,8 +247,7 @@ int pt2_batch_create(pt2_ctx *ctx, uint32_t n, const uint32_t *ref_ids, const pt
 int pt2_batch_run(pt2_ctx *ctx, uint32_t batch_id, pt2_result *results);
 
 /* Steps, total generated terms and kernel launches of one batch run (with a
- * numerator cutoff, n_terms is the planned upper bound: every term counted
- * before the cutoff). */
+ * numerator cutoff, n_terms is the work list's count of the kept terms). */
 int pt2_batch_info(pt2_ctx *ctx, uint32_t batch_id, uint32_t *n_steps, uint64_t *n_terms, uint64_t *launches);
 
 /* Release a batch and its device memory. */

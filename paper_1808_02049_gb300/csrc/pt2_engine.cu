@@ -138,8 +138,10 @@ cudaError_t job_subtract(pt2_ctx *c, const Job &j, RunAcc *acc, cudaStream_t st)
                                acc, reinterpret_cast<uint32_t *>(c->err_word.ptr), st);
 }
 
-// Whether a job generated the terms its plan counted: exactly, or at most
-// the plan's count for a run with a numerator cutoff (planned from all terms).
+// Whether a job generated the terms its plan counted: exactly, or for a run
+// with a numerator cutoff at most the plan's count (its work list counts the
+// kept terms, but the passes of a heavy alpha class are planned from bounds,
+// so the check stays the bound those passes are held to).
 bool terms_as_planned(const Job &j, uint64_t n_terms)
 {
     return j.gp.cutoff > 0.0 ? n_terms <= j.total : n_terms == j.total;

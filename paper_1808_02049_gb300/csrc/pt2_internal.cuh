@@ -160,8 +160,9 @@ struct GenParams {
 // Checks a generator variant carries (template argument): the spin-flip
 // drop rule and the numerator cutoff.
 constexpr int kFiltSym = 1, kFiltCut = 2;
-// Top bit of a pass's expected record count: the count is an upper bound
-// (a run with a numerator cutoff plans from the counts of all terms).
+// Top bit of a pass's expected record count: the count is an upper bound (a
+// beta-class pass of a heavy alpha class in a run with a numerator cutoff is
+// planned from the counts of all terms).
 constexpr unsigned long long kExpectAtMost = 1ull << 63;
 
 struct GenBatch {

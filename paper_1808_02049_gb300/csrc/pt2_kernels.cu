@@ -2611,7 +2611,8 @@ __global__ void pass_finish_kernel(const unsigned long long *__restrict__ tile_o
     const unsigned long long got = tile_off[tile_base[i + 1]] - tile_off[tile_base[i]];
     acc[i]->n_terms += got;
     acc[i]->n_big += n_big[i];
-    // exact count, or (flag kExpectAtMost, a run with a numerator cutoff) an upper bound
+    // exact count, or (flag kExpectAtMost: a beta-class pass of a heavy alpha
+    // class in a run with a numerator cutoff) an upper bound
     const unsigned long long e = expected[i] & ~kExpectAtMost;
     if ((expected[i] & kExpectAtMost) ? got > e : got != e) atomicOr(err, kErrCount);
     n_big[i] = 0;
