@@ -430,8 +430,8 @@ def bench_served(ctx, fleet, big, n_req, load, seed=20185000):
 # captured launch; summaries under profiles/), valid only for the kernel
 # source they were taken on.
 PROFILED_TRAFFIC = {
-    # code hash (kernel_code_sha256) of the captured source; its file sha256 at capture began 75947701
-    "kernels_sha256": "6d15b0f14066b677cfa4e5803fcce36324ac9cc3052c021b1647517f28ae4f05",
+    # code hash (kernel_sources_sha256) of the captured source; pt2_kernels.cu's file sha256 at capture began 75947701
+    "kernels_sha256": "96533fcab6611371da770b2a79168fbacaec410796a262b37371bde2b538fe83",
     "tile_kernel": (1.444991e9 + 3.737088e6) / 45_176_097,     # 32.07 B per term
     "gen_kernel<Emit>": (0.172486e9 + 1.392777e9) / 45_176_097,  # 34.65 B per term
 }
@@ -447,11 +447,17 @@ def kernel_code_sha256(text):
     return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
+def kernel_sources_sha256():
+    """kernel_code_sha256 of the kernels and the header of their constants."""
+    csrc = os.path.join(ROOT, "paper_1808_02049_gb300", "csrc")
+    text = "\n".join(open(os.path.join(csrc, f)).read() for f in ("pt2_kernels.cu", "pt2_internal.cuh"))
+    return kernel_code_sha256(text)
+
+
 def profiled_traffic_per_term(kernel):
     """Bytes per term from the capture, or None if the kernel code changed since."""
-    src = os.path.join(ROOT, "paper_1808_02049_gb300", "csrc", "pt2_kernels.cu")
     try:
-        sha = kernel_code_sha256(open(src).read())
+        sha = kernel_sources_sha256()
     except OSError:
         return None
     if sha != PROFILED_TRAFFIC["kernels_sha256"]:

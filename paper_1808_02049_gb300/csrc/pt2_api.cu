@@ -470,6 +470,15 @@ int pt2_unload(pt2_ctx *c, uint32_t id)
 {
     if (!c) return PT2_ERR_INVALID;
     cudaSetDevice(c->device);
+    {
+        // a reference with requests in the serving engine is refused before
+        // waiting for the stream, so the answer does not depend on how far
+        // the engine's queued steps have run
+        std::lock_guard<std::recursive_mutex> lock(c->exec);
+        auto ri = c->refs.find(id);
+        if (ri != c->refs.end() && ri->second->busy)
+            return fail(c, PT2_ERR_BUSY, "reference %u has requests in the serving engine", id);
+    }
     cudaStreamSynchronize(c->stream);
     std::lock_guard<std::recursive_mutex> lock(c->exec);
     auto ri = c->refs.find(id);

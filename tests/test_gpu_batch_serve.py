@@ -164,11 +164,14 @@ def test_served_request_timeout_and_busy_reference():
         e0 = float(c.diagonal(sid, r.keys).min() - 0.1)
         rid = c.load_reference(sid, r.keys, r.coef, e0)
         t = c.submit(rid)
+        try:
+            early = pt2.pt2_wait(c.handle, t, 0.0)
+        except pt2.Pt2Error as e:
+            assert e.code == pt2.PT2_ERR_TIMEOUT, str(e)
+        else:
+            pytest.fail(f"the request was done at once: {early}")
         with pytest.raises(pt2.Pt2Error) as e:
             c.unload(rid)  # still in flight
         assert e.value.code == pt2.PT2_ERR_BUSY
-        with pytest.raises(pt2.Pt2Error) as e:
-            pt2.pt2_wait(c.handle, t, 0.0)
-        assert e.value.code == pt2.PT2_ERR_TIMEOUT
         got = c.wait(t, timeout_s=600)
         assert same(got, c.run(rid))
