@@ -87,7 +87,9 @@ int pt2_load_reference(pt2_ctx *ctx, uint32_t system_id, uint64_t n_det, const u
                        const double *coef, double e0, uint32_t *ref_id);
 
 /* Free a loaded system or reference (a system may only be unloaded once no
- * reference uses it). */
+ * reference uses it; PT2_ERR_INVALID otherwise).  A reference with submitted
+ * requests that have not finished is refused at once with PT2_ERR_BUSY, also
+ * while the serving engine is running a step. */
 int pt2_unload(pt2_ctx *ctx, uint32_t id);
 
 /* Direct diagonal H_kk (Slater-Condon, the denominator term of Eq. 3) of n

@@ -471,12 +471,13 @@ int pt2_unload(pt2_ctx *c, uint32_t id)
     if (!c) return PT2_ERR_INVALID;
     cudaSetDevice(c->device);
     {
-        // a reference with requests in the serving engine is refused before
-        // waiting for the stream, so the answer does not depend on how far
-        // the engine's queued steps have run
-        std::lock_guard<std::recursive_mutex> lock(c->exec);
-        auto ri = c->refs.find(id);
-        if (ri != c->refs.end() && ri->second->busy)
+        // a reference with unfinished requests in the serving engine is
+        // refused at once: not after waiting for the engine's current step
+        // (which holds the execution lock) or for the stream, by which time
+        // they may have finished
+        std::lock_guard<std::mutex> sl(c->served_mu);
+        auto si = c->served.find(id);
+        if (si != c->served.end() && si->second > 0)
             return fail(c, PT2_ERR_BUSY, "reference %u has requests in the serving engine", id);
     }
     cudaStreamSynchronize(c->stream);

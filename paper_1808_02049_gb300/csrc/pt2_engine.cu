@@ -805,6 +805,14 @@ struct Server {
 
 namespace {
 
+// A served request of reference ref_id is finished (done or failed).
+void served_done(pt2_ctx *c, uint32_t ref_id)
+{
+    std::lock_guard<std::mutex> sl(c->served_mu);
+    auto it = c->served.find(ref_id);
+    if (it != c->served.end() && --it->second <= 0) c->served.erase(it);
+}
+
 void server_fail_jobs(pt2_ctx *c, std::vector<Job *> &js, int rc)
 {
     Server &S = *c->server;
@@ -812,6 +820,7 @@ void server_fail_jobs(pt2_ctx *c, std::vector<Job *> &js, int rc)
         j->status = rc;
         j->t_done = now_s();
         j->r->busy--;
+        served_done(c, j->ref_id);
         S.inflight_bytes -= std::min(S.inflight_bytes, j->footprint);
         if (j->acc) S.free_slots.push_back((int)(j->acc - reinterpret_cast<RunAcc *>(S.acc_pool.ptr)));
     }
@@ -923,6 +932,7 @@ void server_iteration(pt2_ctx *c)
         j->result.seconds = t - j->t_submit;
         j->status = terms_as_planned(*j, h[i].n_terms) ? PT2_OK : PT2_ERR_CUDA;
         j->r->busy--;
+        served_done(c, j->ref_id);
         S.inflight_bytes -= std::min(S.inflight_bytes, j->footprint);
         S.free_slots.push_back((int)(j->acc - reinterpret_cast<RunAcc *>(S.acc_pool.ptr)));
         S.active.erase(std::find(S.active.begin(), S.active.end(), j));
@@ -1174,6 +1184,8 @@ int pt2_submit(pt2_ctx *c, uint32_t ref_id, const pt2_opts *opts, uint64_t *tick
         if ((rc = init_job(c, *j, ref_id, opts))) return rc;
         if ((rc = server_start(c))) return rc;
         j->r->busy++;
+        std::lock_guard<std::mutex> sl(c->served_mu);
+        c->served[ref_id]++;
     }
     Server &S = *c->server;
     std::lock_guard<std::mutex> lk(S.mu);

@@ -128,6 +128,11 @@ struct pt2_ctx {
     uint32_t tuned_tile[8] = {};
     // serialises GPU work of pt2_run, batches and the serving engine
     std::recursive_mutex exec;
+    // unfinished requests of the serving engine per reference id; its own
+    // (innermost) lock, so an unload can refuse a busy reference without
+    // waiting for a step that holds `exec`
+    std::mutex served_mu;
+    std::map<uint32_t, int> served;
     std::map<uint32_t, std::unique_ptr<pt2::Batch>> batches;
     std::unique_ptr<pt2::Server> server;
     pt2_ctx();
